@@ -214,7 +214,11 @@ T d2(const Stencils& S, const Grid& G, const double* u, long long p, int d) {
 }
 
 // mixed derivative d_{d1} d_{d2} as the tensor product of the 1D centered
-// first-derivative stencils
+// first-derivative stencils. Each term is grouped as a difference of two
+// first differences, (u_{a,b} - u_{-a,b}) - (u_{a,-b} - u_{-a,-b}), so that
+// on data which varies strongly along one axis only every subtraction is
+// between nearby values and is exact (Sterbenz); the left-to-right sum of
+// the four values would instead round an O(|u|) intermediate.
 template <typename T>
 T dmix(const Stencils& S, const Grid& G, const double* u, long long p, int da, int db) {
   const long long sa = G.st[da], sb = G.st[db];
@@ -222,8 +226,8 @@ T dmix(const Stencils& S, const Grid& G, const double* u, long long p, int da, i
   bool first = true;
   for (int a = 1; a <= S.half; ++a) {
     for (int b = 1; b <= S.half; ++b) {
-      T q = T(u[p + a * sa + b * sb]) - T(u[p - a * sa + b * sb]) - T(u[p + a * sa - b * sb]) +
-            T(u[p - a * sa - b * sb]);
+      T q = (T(u[p + a * sa + b * sb]) - T(u[p - a * sa + b * sb])) -
+            (T(u[p + a * sa - b * sb]) - T(u[p - a * sa - b * sb]));
       T term = (T(S.c1[a]) * T(S.c1[b])) * q;
       acc = first ? term : acc + term;
       first = false;
