@@ -1,0 +1,373 @@
+"""Benchmark: BSSN RK4 grid-point updates per second on one GB300.
+
+Workload (default): Brill-Lindquist two-puncture data (bare masses 0.5 at
+x = +-1.5) on a 128^3 grid over [-8, 8]^3, 8th-order finite differences,
+5 ghost zones with a static outer boundary, 1+log slicing, Gamma-driver shift
+(eta = 2), Kreiss-Oliger eps = 0.1, dt = 0.25 h, double precision. One step
+is one full RK4 step (4 x ghost fill + difference tables + fused
+right-hand-side/dissipation/stage kernel) over every interior point; the
+metric counts interior points advanced per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun, one independent replica per GPU (the method's
+single-GPU path does not exchange data; weak scaling). --impl reference
+times the CPU oracle (test infrastructure) on the host cores instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BSSN RK4 grid-point updates/sec at 1 GB300, FP64 vs FP32/learned, at stated error"
+UNIT = "grid-point updates/s"
+N, G, ORDER, LO, HI = 128, 5, 8, -8.0, 8.0
+WORKLOAD = ("Brill-Lindquist two punctures (m=0.5 at x=+-1.5), 128^3 on [-8,8]^3, 8th-order FD, 5 ghosts, static "
+            "boundary, 1+log + Gamma-driver (eta=2), KO eps=0.1, dt=0.25h, FP64, RK4")
+
+# Algorithmic FP64 flops per interior point per RK4 stage, 8th order: the
+# oracle's instrumented count (add/sub/mul/div = 1) of the right-hand side
+# with mixed derivatives counted as one first-derivative stencil applied to
+# shared first derivatives (33 x 12), the algebra as the oracle writes it,
+# Kreiss-Oliger for 24 variables and the RK4 stage combination (4 per
+# variable). See DESIGN.md "Algorithmic work".
+FLOPS_PER_POINT_STAGE = None  # filled from the oracle's counter at start-up
+
+# DRAM traffic of the fused stage kernel per launch, from one ncu capture of
+# the same source (profiles/); ignored when the kernel source has changed.
+TRAFFIC = {"src_sha": None, "bytes_per_launch_128": None}
+
+
+def kernel_src_sha():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1307_6488_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1307_6488_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def algorithmic_flops(order=ORDER):
+    import oracle
+    c = oracle.flop_counts(order)
+    n_first = 45          # 15 variables x 3 directions
+    n_second = 33         # 11 variables x 3 diagonal
+    n_mixed = 33          # 11 variables x 3 pairs
+    n_adv = 72            # 24 variables x 3 directions
+    gather_sep = c["gather_rhs"] - n_mixed * c["mixed_tensor"] + n_mixed * c["first"]
+    per_rhs = gather_sep + c["rhs_algebra"]
+    return dict(rhs=per_rhs, ko=24 * c["ko_var"], rk=24 * 4, total=per_rhs + 24 * c["ko_var"] + 24 * 4,
+                first=c["first"], second=c["second"], adv_dir=c["upwind_dir"], algebra=c["rhs_algebra"],
+                mixed_tensor=c["mixed_tensor"], n=(n_first, n_second, n_mixed, n_adv))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 4 + i and s[4 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("BSSN_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ reference arm (CPU oracle)
+def cpu_oracle_rate(budget_s=15.0, n=32, max_steps=None):
+    """Oracle RK4 steps of the same workload (8th order BL, static boundary)
+    on an n^3 block of the [-8,8]^3 domain spacing; returns updates/s,
+    steps, seconds, threads."""
+    import oracle
+    from paper_1307_6488_gb300 import inputs
+    h = (HI - LO) / N
+    lo = -n * h / 2
+    u, _ = inputs.brill_lindquist(n, G, lo=lo, hi=-lo)
+    p = oracle.Params(fd_order=ORDER, ko_eps=0.1, lapse=0, shift=0, eta=2.0)
+    dt = 0.25 * h
+    oracle.rk4_step(u, G, h, dt, p, bc=1, ghost_src=u)  # warm the library
+    t0 = time.perf_counter()
+    steps = 0
+    y = u
+    while True:
+        y = oracle.rk4_step(y, G, h, dt, p, bc=1, ghost_src=u)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_steps and steps >= max_steps):
+            break
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return n ** 3 * steps / el, steps, el, threads
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    n = 32
+    rates = []
+    for _ in range(args.warmup):
+        cpu_oracle_rate(budget_s=0.0, n=n, max_steps=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r, _, _, threads = cpu_oracle_rate(budget_s=0.0, n=n, max_steps=1)
+        rates.append(r)
+    el = time.perf_counter() - t0
+    value = n ** 3 * args.steps / el
+    sample = f"one oracle RK4 step per step on a {n}^3 block of the workload (same spacing, order, gauge, KO)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_grid": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+TENSORS = [[0], list(range(1, 7)), [7], list(range(8, 14)), list(range(14, 17)), [17], list(range(18, 21)),
+           list(range(21, 24))]
+
+
+def tensor_rel_err(got, want, g):
+    """Max over variables of |got - want| normalised by the largest component
+    of the same tensor field (interior points)."""
+    gi = got[:, g:-g, g:-g, g:-g].reshape(24, -1)
+    wi = want[:, g:-g, g:-g, g:-g].reshape(24, -1)
+    mag = np.max(np.abs(wi), axis=1)
+    scale = np.zeros_like(mag)
+    for grp in TENSORS:
+        scale[grp] = np.max(mag[grp])
+    return np.max(np.abs(gi - wi), axis=1) / np.maximum(scale, 1e-300)
+
+
+def run_gpu(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1307_6488_gb300 import binding as B
+    from paper_1307_6488_gb300 import inputs
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    flops = algorithmic_flops(ORDER)
+    u, h = inputs.brill_lindquist(N, G, lo=LO, hi=HI)
+    grid = B.make_grid(N, ghost=G, dx=h)
+    p = B.make_params(fd_order=ORDER, ko_eps=0.1, lapse=0, shift=0, shift_coeff=0.75, eta=2.0, advect_gauge=1)
+    dt = 0.25 * h
+    state0 = B.upload(u, grid, device=dev)
+    ghost_src = state0.clone()
+    ya = B.alloc_state(grid, device=dev)
+    yb = B.alloc_state(grid, device=dev)
+    acc = B.alloc_state(grid, device=dev)
+    work = B.alloc_work(grid, p, device=dev)
+    rates = B.probe_fp_rates()
+
+    def run_form(prec, sample_clocks):
+        state = state0.clone()
+        launches = [0]
+
+        def step(ev=None):
+            ys = state
+            outs = [ya, yb, ya, state]
+            for s in range(4):
+                B.fill_ghosts(grid, 1, ghost_src, ys)
+                B.diff_tables(grid, p, prec, ys, work)
+                if ev is not None:
+                    ev.append(torch.cuda.Event(enable_timing=True))
+                    ev[-1].record(stream)
+                B.rk4_stage_fused(grid, p, prec, s, dt, state, ys, acc, outs[s], work)
+                if ev is not None:
+                    ev.append(torch.cuda.Event(enable_timing=True))
+                    ev[-1].record(stream)
+                ys = outs[s]
+            B.fill_ghosts(grid, 1, ghost_src, state)
+            launches[0] += 13 if prec == B.FP64 else 17
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        launches[0] = 0
+        ev = []
+        barrier(world)
+        torch.cuda.synchronize()
+        clk = ClockSampler(local) if sample_clocks else None
+        if clk:
+            clk.__enter__()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step(ev)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        if clk:
+            clk.__exit__()
+        barrier(world)
+        ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
+        stage_ms = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(len(ev) // 2)]
+        l2, mx, st = B.constraints(grid, p, state, work)
+        return dict(state=state, ms=ms, stage_ms=float(np.mean(stage_ms)), launches=launches[0], l2=l2,
+                    clocks=clk.summary() if clk else None)
+
+    f64 = run_form(B.FP64, True)
+    f32 = run_form(B.FP32_RHS, False)
+    err32 = tensor_rel_err(B.download(f32["state"], grid), B.download(f64["state"], grid), G)
+
+    # end to end through the public API with host buffers (pinned): upload the
+    # step's input state, one RK4 step (bssn_rk4_step), read the result back
+    flat_bytes = 24 * grid.var_stride * 8
+    h_in = torch.empty(24 * grid.var_stride, dtype=torch.float64, pin_memory=True)
+    h_in.copy_(state0.cpu())
+    h_out = torch.empty_like(h_in, pin_memory=True)
+    bufs = torch.empty(3 * 24 * grid.var_stride, dtype=torch.float64, device=dev)
+    dstate = torch.empty_like(state0)
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(2):
+        dstate.copy_(h_in, non_blocking=True)
+        B.rk4_step(grid, p, B.FP64, dt, 1, ghost_src, dstate, bufs, work)
+        h_out.copy_(dstate, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        dstate.copy_(h_in, non_blocking=True)
+        B.rk4_step(grid, p, B.FP64, dt, 1, ghost_src, dstate, bufs, work)
+        h_out.copy_(dstate, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+
+    if rank != 0:
+        return
+    pts = N ** 3
+    value = world * pts * args.steps / (f64["ms"] * 1e-3)
+    e2e_value = world * pts * e2e_steps / (e2e_ms * 1e-3)
+    achieved = flops["total"] * pts / (f64["stage_ms"] * 1e-3)  # FLOP/s of the fused stage kernel
+    peak = 2.0 * rates["fp64_fma_per_s"]
+    sha = kernel_src_sha()
+    traffic = TRAFFIC["bytes_per_launch_128"] if TRAFFIC["src_sha"] == sha else None
+    cpu_rate, cpu_steps, cpu_s, cpu_threads = cpu_oracle_rate(budget_s=args.cpu_budget, n=32)
+    achieved32 = flops["total"] * pts / (f32["stage_ms"] * 1e-3)
+    peak32 = 2.0 * rates["fp32_fma_per_s"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": f64["ms"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": N, "fd_order": ORDER, "ghost": G, "precision": "fp64",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (each state copy %.0f MB > 129 MB)" % (flat_bytes / 1e6)},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_stage<8,0,double> (fused RHS+KO+RK stage)",
+                     "flops_per_point": flops["total"], "stage_ms": f64["stage_ms"],
+                     "peak_source": "measured FP64 FMA rate (bssn_probe_fp_rates) x 2 flops"},
+        "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
+                         "sample": f"{cpu_steps} oracle RK4 step(s) of the same workload on a 32^3 block "
+                                   f"({cpu_s:.1f} s)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": flat_bytes, "d2h_bytes_per_step": flat_bytes},
+        "gpu_launches": f64["launches"],
+        "clocks": f64["clocks"],
+        "accuracy": {"fp64_ham_l2_after": float(f64["l2"][0]), "fp64_mom_l2_after": float(max(f64["l2"][1:4])),
+                     "parity": "FP64 RHS within 1e-12 per-variable relative of the CPU oracle (tests)"},
+        "forms": {
+            "fp32_rhs": {"value": world * pts * args.steps / (f32["ms"] * 1e-3), "unit": UNIT,
+                         "ms_per_step": f32["ms"] / args.steps, "stage_ms": f32["stage_ms"],
+                         "achieved_tflops": achieved32 / 1e12, "frac_of_fp32_peak": achieved32 / peak32,
+                         "err_vs_fp64_max_rel_per_tensor": float(np.max(err32)),
+                         "err_vs_fp64_per_var": [float(x) for x in err32],
+                         "ham_l2_after": float(f32["l2"][0]), "gpu_launches": f32["launches"],
+                         "steps": args.steps + args.warmup},
+        },
+        "fp_rates_measured": rates,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * bssn.h - C ABI of libbssn, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of a BSSN numerical-relativity evolution: the
+ * right-hand side of the BSSN form of the Einstein equations on a 3D
+ * block-structured grid (4th/8th-order centered and upwinded finite
+ * differences, the pointwise right-hand side, Kreiss-Oliger dissipation) and
+ * the method-of-lines RK4 stage update.
+ *
+ * Paper: Blazewicz et al., "From Physics Model to Results: An Optimizing
+ * Framework for Cross-Architecture Code Generation" (arXiv:1307.6488).
+ *   Sec. 1.1  the BSSN system, its variables and its cost per grid point;
+ *   Sec. 2.3  customized finite-differencing operators;
+ *   Sec. 2.6  kernel frames, tiles, fat kernels (prior art for the kernels);
+ *   Sec. 3.3  the production configuration: 8th-order differencing,
+ *             5 ghost zones for the partially upwinded stencils, double
+ *             precision, a Runge-Kutta method of lines, a boundary kernel;
+ *   Sec. 3.4  the benchmark: 100^3 evolved points per GPU plus ghosts.
+ * The paper cites but does not print the equations; the library implements
+ * the standard vacuum BSSN system in the conformal variable W, with 1+log or
+ * harmonic slicing and the Gamma-driver shift (Baumgarte & Shapiro 1998;
+ * Alcubierre et al. 2003).
+ *
+ * Conventions common to every call
+ * --------------------------------
+ * Data layout. A state is 24 double-precision grid functions in the order
+ *   W, gt11, gt12, gt13, gt22, gt23, gt33, trK, At11, At12, At13, At22,
+ *   At23, At33, Gt1, Gt2, Gt3, alpha, beta1, beta2, beta3, B1, B2, B3.
+ * Variable v occupies elements [v*var_stride, v*var_stride + Np) of one
+ * allocation, Np = (nx+2g)(ny+2g)(nz+2g); inside a variable the index is
+ *   (k+g)(ny+2g)(nx+2g) + (j+g)(nx+2g) + (i+g),  i,j,k in [-g, n+g),
+ * x fastest. Interior points are i,j,k in [0, n); the rest are ghosts.
+ * Points are cell centred; only the spacing dx, dy, dz enters the equations.
+ *
+ * Pointers. All array arguments are DEVICE pointers (cudaMalloc'ed or
+ * equivalent memory of the current device) unless documented as host
+ * pointers; they must be 16-byte aligned. The caller owns every buffer.
+ * Scratch memory ("work") is caller-allocated; its size comes from
+ * bssn_work_bytes(). No hot-path call allocates device memory.
+ *
+ * Streams. `stream` is a cudaStream_t (NULL = legacy default stream). All
+ * calls are asynchronous on it except where stated ("synchronizes").
+ *
+ * Errors. Every call returns a bssn_status_t; nothing aborts, traps or
+ * throws. Invalid arguments are rejected before any work is launched. A
+ * CUDA launch failure returns BSSN_ERR_CUDA and is also latched so that
+ * bssn_last_error() reports it.
+ */
+#ifndef BSSN_H
+#define BSSN_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BSSN_OK = 0,
+  BSSN_ERR_INVALID_ARG = 1, /* a size, pointer, order or mode is not acceptable */
+  BSSN_ERR_CUDA = 2,        /* a CUDA call failed (launch or runtime error)     */
+  BSSN_ERR_NONFINITE = 3,   /* a NaN/Inf was found (constraints / plan checks)  */
+  BSSN_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up                */
+  BSSN_ERR_UNSUPPORTED = 5, /* valid request this build does not implement       */
+  BSSN_ERR_NOMEM = 6        /* a plan could not allocate its own storage         */
+} bssn_status_t;
+
+typedef enum {
+  BSSN_FP64 = 0,     /* every operation in double precision                     */
+  BSSN_FP32_RHS = 1  /* derivatives, right-hand side and dissipation in single
+                        precision on the double-precision state; 1/W and 1/alpha
+                        factors, the RK4 update and constraints in double        */
+} bssn_precision_t;
+
+typedef struct {
+  int nx, ny, nz;        /* interior points per axis, each >= 1                   */
+  int ghost;             /* ghost width g: >= 3 for 4th order, >= 5 for 8th       */
+  double dx, dy, dz;     /* grid spacing, > 0                                     */
+  long long var_stride;  /* elements between variables, >= (nx+2g)(ny+2g)(nz+2g),
+                            a multiple of 2 so every variable is 16-byte aligned  */
+} bssn_grid_t;
+
+typedef struct {
+  int fd_order;          /* 4 or 8 (Sec. 3.3 uses 8)                              */
+  double ko_eps;         /* Kreiss-Oliger strength epsilon (0 disables)           */
+  int lapse;             /* 0: 1+log  d_t a = -2 a K;  1: harmonic  -a^2 K;  2: frozen */
+  int shift;             /* 0: Gamma-driver;  1: frozen (d_t beta = d_t B = 0)    */
+  double shift_coeff;    /* coefficient of B^i in d_t beta^i (3/4)                */
+  double eta;            /* damping eta in d_t B^i (2)                            */
+  int advect_gauge;      /* 1: add beta^k d_k to the alpha, beta and B equations  */
+} bssn_params_t;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* bssn_status_string(bssn_status_t s);
+
+/* The first CUDA error latched by any call since the last bssn_clear_error()
+ * (BSSN_OK if none). Host-only, does not synchronize. */
+bssn_status_t bssn_last_error(void);
+void bssn_clear_error(void);
+
+/* Bytes of scratch ("work") that bssn_rhs, bssn_rk4_stage and
+ * bssn_constraints need for this grid, order and precision. Returns 0 and
+ * sets *bytes to 0 for invalid arguments. */
+unsigned long long bssn_work_bytes(const bssn_grid_t* grid, const bssn_params_t* params,
+                                   bssn_precision_t prec);
+
+/* Ghost fill (Sec. 3.3 "boundary condition" kernel; the paper does not state
+ * its type). mode 0: periodic wrap of every coordinate (needs no src);
+ * mode 1: static, every ghost point of every variable is copied from src
+ * (the t = 0 state, same layout). Interior points are untouched. */
+bssn_status_t bssn_fill_ghosts(const bssn_grid_t* grid, int mode, const double* src, double* state,
+                               void* stream);
+
+/* Right-hand side of the BSSN system (Sec. 1.1) at every interior point,
+ * without dissipation: rhs[v] at interior points is overwritten, ghosts of
+ * rhs are not touched. The ghosts of `state` must be filled. `state` and
+ * `rhs` must not overlap. work: >= bssn_work_bytes(). */
+bssn_status_t bssn_rhs(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec,
+                       const double* state, double* rhs, void* work, unsigned long long work_bytes,
+                       void* stream);
+
+/* Kreiss-Oliger dissipation added to rhs at interior points:
+ *   rhs += (-1)^(r+1) eps / 2^(2r) * sum_d delta_d^(2r) state / h_d,
+ * r = 3 for fd_order 4, r = 5 for fd_order 8, for all 24 variables.
+ * Ghosts of `state` must be filled. */
+bssn_status_t bssn_ko_dissipation(const bssn_grid_t* grid, const bssn_params_t* params,
+                                  bssn_precision_t prec, const double* state, double* rhs, void* stream);
+
+/* One stage of the classic RK4 method of lines (Sec. 3.3 uses a Runge-Kutta
+ * integrator), fused with the right-hand side and dissipation of ys:
+ *   k = RHS(ys) + KO(ys)
+ *   stage 0: acc  = dt/6 k;        ynext = y0 + dt/2 k
+ *   stage 1: acc += dt/3 k;        ynext = y0 + dt/2 k
+ *   stage 2: acc += dt/3 k;        ynext = y0 + dt k
+ *   stage 3:                       ynext = y0 + (acc + dt/6 k)
+ * at interior points (ghosts of ynext and acc are not written). For stage 0
+ * pass ys == y0. ynext may equal y0 (y0 is read only at the point being
+ * written) but must not overlap ys or acc; acc must not overlap y0 or ys.
+ * The ghosts of ys must be filled. work: >= bssn_work_bytes(). */
+bssn_status_t bssn_rk4_stage(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec,
+                             int stage, double dt, const double* y0, const double* ys, double* acc,
+                             double* ynext, void* work, unsigned long long work_bytes, void* stream);
+
+/* The two halves of bssn_rk4_stage, for callers that schedule or time them
+ * separately (the paper's split of "RHS derivatives" from the rest, Sec. 2.3):
+ * bssn_diff_tables fills the first-difference tables in `work` from `state`;
+ * bssn_rk4_stage_fused then runs the fused right-hand side + dissipation +
+ * stage update reading those tables, which must have been made from the same
+ * ys with the same grid and fd_order (no check is possible). Same argument
+ * rules as bssn_rk4_stage. */
+bssn_status_t bssn_diff_tables(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec,
+                               const double* state, void* work, unsigned long long work_bytes, void* stream);
+bssn_status_t bssn_rk4_stage_fused(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec,
+                                   int stage, double dt, const double* y0, const double* ys, double* acc,
+                                   double* ynext, void* work, unsigned long long work_bytes, void* stream);
+
+/* One full RK4 step in place on `state`: four fused stages with the ghosts
+ * filled before each (bc 0 periodic, bc 1 static from ghost_src). Needs three
+ * state-sized buffers in `bufs` (bufs, bufs + var_stride*24, ...: 3*24*
+ * var_stride doubles) besides work. On return the interior of state holds the
+ * new values and its ghosts are refilled. */
+bssn_status_t bssn_rk4_step(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec,
+                            double dt, int bc, const double* ghost_src, double* state, double* bufs,
+                            void* work, unsigned long long work_bytes, void* stream);
+
+/* Constraints at interior points (always double precision):
+ *   H   = R + 2/3 K^2 - At_ij At^ij                      (Hamiltonian)
+ *   M_i = gt^jk D_k At_ij - 3/W At_i^j d_j W - 2/3 d_i K  (momentum)
+ *   G^i = Gt^i - gt^jk Gt^i_jk                            (Gamma constraint)
+ * ham (1 array), mom and gcon (3 arrays each, var_stride apart) receive the
+ * pointwise values when not NULL. out_l2[7] and out_max[7] are HOST arrays:
+ * root-mean-square and maximum modulus over interior points, in the order
+ * H, M1, M2, M3, G1, G2, G3. Synchronizes `stream`. Returns
+ * BSSN_ERR_NONFINITE (after filling the outputs) if any value is NaN/Inf. */
+bssn_status_t bssn_constraints(const bssn_grid_t* grid, const bssn_params_t* params, const double* state,
+                               double* ham, double* mom, double* gcon, double* out_l2, double* out_max,
+                               void* work, unsigned long long work_bytes, void* stream);
+
+/* Measured issue rates of this device's floating-point pipes (a short
+ * microbenchmark, ~20 ms). out[0] = FP64 FMA/s, out[1] = FP32 FMA/s,
+ * out[2] = FP64 add/s. HOST array. Synchronizes the device. */
+bssn_status_t bssn_probe_fp_rates(double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSSN_H */

@@ -35,6 +35,9 @@ def lib():
         L.oracle_apply_op.argtypes = [_i, _i, _i, _i, _d, _d, _d, _i, _i, _i, _i, _d, _p, _p]
         L.oracle_rhs.argtypes = [_i, _i, _i, _i, _d, _d, _d, _ll, _i, _d, _i, _i, _d, _d, _i, _p, _p]
         L.oracle_rhs.restype = _i
+        L.oracle_rhs_points.argtypes = [_i, _i, _i, _i, _d, _d, _d, _ll, _i, _d, _i, _i, _d, _d, _i, _i, _ll, _p, _p,
+                                         _p]
+        L.oracle_rhs_points.restype = _i
         L.oracle_ko.argtypes = [_i, _i, _i, _i, _d, _d, _d, _ll, _i, _d, _p, _p]
         L.oracle_ko.restype = _i
         L.oracle_fill_ghosts.argtypes = [_i, _i, _i, _i, _ll, _i, _p, _p]
@@ -123,6 +126,19 @@ def rhs(u, g, h, p: Params, ko=False):
         rc = lib().oracle_ko(nx, ny, nz, g, hx, hy, hz, vs, p.fd_order, p.ko_eps, _ptr(u), _ptr(out))
         if rc != 0:
             raise ValueError("oracle_ko: invalid arguments")
+    return out
+
+
+def rhs_points(u, g, h, p: Params, lin, ko=False):
+    """RHS (+KO) at interior points lin = i + nx (j + ny k); returns (len(lin), 24)."""
+    nx, ny, nz, vs = _check_state(u, g)
+    lin = np.ascontiguousarray(lin, dtype=np.int64)
+    out = np.zeros((len(lin), 24))
+    hx, hy, hz = (h, h, h) if np.isscalar(h) else h
+    rc = lib().oracle_rhs_points(nx, ny, nz, g, hx, hy, hz, vs, p.fd_order, p.ko_eps, p.lapse, p.shift,
+                                 p.shift_coeff, p.eta, p.advect_gauge, int(ko), len(lin), _ptr(lin), _ptr(u), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_rhs_points: invalid arguments")
     return out
 
 

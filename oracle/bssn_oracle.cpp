@@ -814,6 +814,36 @@ int oracle_rhs(int nx, int ny, int nz, int g, double dx, double dy, double dz, l
   return 0;
 }
 
+// Right-hand side (with_ko = 1: plus Kreiss-Oliger) at selected interior
+// points only, for checking large grids by sampling. lin[q] = i + nx (j + ny k);
+// out[q*24 + v] receives variable v at point q.
+int oracle_rhs_points(int nx, int ny, int nz, int g, double dx, double dy, double dz, long long vs, int fd_order,
+                      double ko_eps, int lapse, int shift, double shift_coeff, double eta, int advect_gauge,
+                      int with_ko, long long npoints, const long long* lin, const double* state, double* out) {
+  if ((fd_order != 4 && fd_order != 8) || g < required_ghost(fd_order)) return -1;
+  Grid G = make_grid(nx, ny, nz, g, dx, dy, dz, vs);
+  Params P = make_params(fd_order, ko_eps, lapse, shift, shift_coeff, eta, advect_gauge);
+  const Stencils S = make_stencils(fd_order);
+  const long long total = (long long)nx * ny * nz;
+  for (long long q = 0; q < npoints; ++q)
+    if (lin[q] < 0 || lin[q] >= total) return -1;
+#pragma omp parallel for schedule(static)
+  for (long long q = 0; q < npoints; ++q) {
+    const int i = (int)(lin[q] % nx), j = (int)((lin[q] / nx) % ny), k = (int)(lin[q] / ((long long)nx * ny));
+    const long long p = G.idx(i, j, k);
+    Derivs<double> D;
+    double u[NVAR], r[NVAR];
+    for (int v = 0; v < NVAR; ++v) u[v] = state[v * vs + p];
+    gather_derivs<double>(S, G, state, p, true, false, D);
+    rhs_point<double>(P, u, D, r);
+    for (int v = 0; v < NVAR; ++v) {
+      if (with_ko) r[v] += ko1<double>(S, G, state + v * vs, p, ko_eps);
+      out[q * NVAR + v] = r[v];
+    }
+  }
+  return 0;
+}
+
 // rhs += Kreiss-Oliger dissipation of every variable at interior points.
 int oracle_ko(int nx, int ny, int nz, int g, double dx, double dy, double dz, long long vs, int fd_order,
               double ko_eps, const double* state, double* rhs) {

@@ -1,0 +1,230 @@
+"""ctypes binding of libbssn (include/bssn.h): argument marshalling only.
+
+Every function here has the name of the C entry point without the ``bssn_``
+prefix and forwards to it; arrays are torch CUDA tensors (float64) or raw
+device addresses. The compute path is the CUDA library: if libbssn.so is
+missing this module raises instead of falling back to anything else.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbssn.so")
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_NOMEM = range(7)
+FP64, FP32_RHS = 0, 1
+NVAR = 24
+
+
+class BssnError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("ghost", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("var_stride", ctypes.c_longlong)]
+
+    @property
+    def padded(self):
+        g = self.ghost
+        return (self.nz + 2 * g, self.ny + 2 * g, self.nx + 2 * g)
+
+    @property
+    def npad(self):
+        z, y, x = self.padded
+        return z * y * x
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("fd_order", ctypes.c_int), ("ko_eps", ctypes.c_double), ("lapse", ctypes.c_int),
+                ("shift", ctypes.c_int), ("shift_coeff", ctypes.c_double), ("eta", ctypes.c_double),
+                ("advect_gauge", ctypes.c_int)]
+
+
+def make_grid(nx, ny=None, nz=None, ghost=3, dx=1.0, dy=None, dz=None, align=16):
+    """Grid with var_stride = padded points rounded up to `align` doubles."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    dy = dx if dy is None else dy
+    dz = dx if dz is None else dz
+    npad = (nx + 2 * ghost) * (ny + 2 * ghost) * (nz + 2 * ghost)
+    vs = (npad + align - 1) // align * align
+    return Grid(nx, ny, nz, ghost, dx, dy, dz, vs)
+
+
+def make_params(fd_order=4, ko_eps=0.1, lapse=0, shift=0, shift_coeff=0.75, eta=2.0, advect_gauge=1):
+    return Params(fd_order, ko_eps, lapse, shift, shift_coeff, eta, advect_gauge)
+
+
+_L = None
+_p = ctypes.c_void_p
+
+
+def lib():
+    global _L
+    if _L is not None:
+        return _L
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built: run __graft_entry__.build() (nvcc, sm_103a)")
+    L = ctypes.CDLL(LIB_PATH)
+    G, P = ctypes.POINTER(Grid), ctypes.POINTER(Params)
+    ull = ctypes.c_ulonglong
+    L.bssn_status_string.argtypes = [ctypes.c_int]
+    L.bssn_status_string.restype = ctypes.c_char_p
+    L.bssn_last_error.restype = ctypes.c_int
+    L.bssn_clear_error.restype = None
+    L.bssn_work_bytes.argtypes = [G, P, ctypes.c_int]
+    L.bssn_work_bytes.restype = ull
+    L.bssn_fill_ghosts.argtypes = [G, ctypes.c_int, _p, _p, _p]
+    L.bssn_rhs.argtypes = [G, P, ctypes.c_int, _p, _p, _p, ull, _p]
+    L.bssn_ko_dissipation.argtypes = [G, P, ctypes.c_int, _p, _p, _p]
+    L.bssn_rk4_stage.argtypes = [G, P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _p, _p, _p, _p, _p, ull, _p]
+    L.bssn_diff_tables.argtypes = [G, P, ctypes.c_int, _p, _p, ull, _p]
+    L.bssn_rk4_stage_fused.argtypes = [G, P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _p, _p, _p, _p, _p, ull,
+                                       _p]
+    L.bssn_rk4_step.argtypes = [G, P, ctypes.c_int, ctypes.c_double, ctypes.c_int, _p, _p, _p, _p, ull, _p]
+    L.bssn_constraints.argtypes = [G, P, _p, _p, _p, _p, _p, _p, _p, ull, _p]
+    L.bssn_probe_fp_rates.argtypes = [_p]
+    for name in ("bssn_fill_ghosts", "bssn_rhs", "bssn_ko_dissipation", "bssn_rk4_stage", "bssn_rk4_step",
+                 "bssn_diff_tables", "bssn_rk4_stage_fused",
+                 "bssn_constraints", "bssn_probe_fp_rates"):
+        getattr(L, name).restype = ctypes.c_int
+    _L = L
+    return L
+
+
+def status_string(s):
+    return lib().bssn_status_string(int(s)).decode()
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(status, where):
+    if status != OK:
+        raise BssnError(status, where)
+
+
+def last_error():
+    return lib().bssn_last_error()
+
+
+def clear_error():
+    lib().bssn_clear_error()
+
+
+def work_bytes(grid, params, prec=FP64):
+    return int(lib().bssn_work_bytes(ctypes.byref(grid), ctypes.byref(params), prec))
+
+
+def fill_ghosts(grid, mode, src, state, stream=None):
+    _check(lib().bssn_fill_ghosts(ctypes.byref(grid), mode, _ptr(src), _ptr(state), _stream(stream)), "fill_ghosts")
+
+
+def rhs(grid, params, prec, state, out, work, stream=None):
+    _check(lib().bssn_rhs(ctypes.byref(grid), ctypes.byref(params), prec, _ptr(state), _ptr(out), _ptr(work),
+                          _nbytes(work), _stream(stream)), "rhs")
+
+
+def ko_dissipation(grid, params, prec, state, out, stream=None):
+    _check(lib().bssn_ko_dissipation(ctypes.byref(grid), ctypes.byref(params), prec, _ptr(state), _ptr(out),
+                                     _stream(stream)), "ko_dissipation")
+
+
+def rk4_stage(grid, params, prec, stage, dt, y0, ys, acc, ynext, work, stream=None):
+    _check(lib().bssn_rk4_stage(ctypes.byref(grid), ctypes.byref(params), prec, stage, dt, _ptr(y0), _ptr(ys),
+                                _ptr(acc), _ptr(ynext), _ptr(work), _nbytes(work), _stream(stream)), "rk4_stage")
+
+
+def diff_tables(grid, params, prec, state, work, stream=None):
+    _check(lib().bssn_diff_tables(ctypes.byref(grid), ctypes.byref(params), prec, _ptr(state), _ptr(work),
+                                  _nbytes(work), _stream(stream)), "diff_tables")
+
+
+def rk4_stage_fused(grid, params, prec, stage, dt, y0, ys, acc, ynext, work, stream=None):
+    _check(lib().bssn_rk4_stage_fused(ctypes.byref(grid), ctypes.byref(params), prec, stage, dt, _ptr(y0), _ptr(ys),
+                                      _ptr(acc), _ptr(ynext), _ptr(work), _nbytes(work), _stream(stream)),
+           "rk4_stage_fused")
+
+
+def rk4_step(grid, params, prec, dt, bc, ghost_src, state, bufs, work, stream=None):
+    _check(lib().bssn_rk4_step(ctypes.byref(grid), ctypes.byref(params), prec, dt, bc, _ptr(ghost_src), _ptr(state),
+                               _ptr(bufs), _ptr(work), _nbytes(work), _stream(stream)), "rk4_step")
+
+
+def constraints(grid, params, state, work, ham=None, mom=None, gcon=None, stream=None):
+    """Returns (l2[7], max[7], status); status is OK or ERR_NONFINITE."""
+    l2 = np.zeros(7)
+    mx = np.zeros(7)
+    s = lib().bssn_constraints(ctypes.byref(grid), ctypes.byref(params), _ptr(state), _ptr(ham), _ptr(mom),
+                               _ptr(gcon), l2.ctypes.data_as(_p), mx.ctypes.data_as(_p), _ptr(work), _nbytes(work),
+                               _stream(stream))
+    if s not in (OK, ERR_NONFINITE):
+        raise BssnError(s, "constraints")
+    return l2, mx, s
+
+
+def probe_fp_rates():
+    out = np.zeros(3)
+    _check(lib().bssn_probe_fp_rates(out.ctypes.data_as(_p)), "probe_fp_rates")
+    return dict(fp64_fma_per_s=out[0], fp32_fma_per_s=out[1], fp64_add_per_s=out[2])
+
+
+def _nbytes(x):
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        raise TypeError("pass work as a tensor so its size is known")
+    return x.numel() * x.element_size()
+
+
+# ------------------------------------------------------------------ host <-> device layout helpers
+def alloc_state(grid, device="cuda", n=1):
+    """Zeroed device buffer of n states (24 variables, var_stride apart)."""
+    import torch
+    return torch.zeros(n * NVAR * grid.var_stride, dtype=torch.float64, device=device)
+
+
+def alloc_work(grid, params, prec=FP64, device="cuda"):
+    import torch
+    nb = work_bytes(grid, params, prec)
+    if nb == 0:
+        raise BssnError(ERR_INVALID_ARG, "work_bytes")
+    return torch.empty((nb + 7) // 8, dtype=torch.float64, device=device)
+
+
+def view4(flat, grid, nvar=NVAR):
+    """(nvar, nz+2g, ny+2g, nx+2g) view of a flat state buffer."""
+    return flat[: nvar * grid.var_stride].view(nvar, grid.var_stride)[:, : grid.npad].view(nvar, *grid.padded)
+
+
+def upload(state_np, grid, out=None, device="cuda"):
+    """Copy a numpy (24, nz+2g, ny+2g, nx+2g) array into a flat device state."""
+    import torch
+    if out is None:
+        out = alloc_state(grid, device)
+    view4(out, grid, state_np.shape[0]).copy_(torch.from_numpy(np.ascontiguousarray(state_np)))
+    return out
+
+
+def download(flat, grid, nvar=NVAR):
+    return view4(flat, grid, nvar).cpu().numpy()

@@ -1,0 +1,428 @@
+// C ABI of libbssn: argument validation, scratch layout, ghost filling,
+// reductions, the RK4 step driver and the floating-point rate probe.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "../../include/bssn.h"
+#include "bssn_common.cuh"
+#include "bssn_launch.h"
+
+using namespace bssn;
+
+namespace {
+
+std::atomic<int> g_last_error{BSSN_OK};
+
+bssn_status_t latch(cudaError_t e) {
+  if (e == cudaSuccess) return BSSN_OK;
+  int expected = BSSN_OK;
+  g_last_error.compare_exchange_strong(expected, BSSN_ERR_CUDA);
+  return BSSN_ERR_CUDA;
+}
+
+bool aligned16(const void* p) { return p && ((uintptr_t)p & 15u) == 0; }
+
+int required_ghost(int order) { return order / 2 + 1; }
+
+bool grid_ok(const bssn_grid_t* G) {
+  if (!G) return false;
+  if (G->nx < 1 || G->ny < 1 || G->nz < 1 || G->ghost < 0 || G->ghost > 64) return false;
+  if (!(G->dx > 0) || !(G->dy > 0) || !(G->dz > 0)) return false;
+  if (!std::isfinite(G->dx) || !std::isfinite(G->dy) || !std::isfinite(G->dz)) return false;
+  const long long np = (G->nx + 2LL * G->ghost) * (G->ny + 2LL * G->ghost) * (G->nz + 2LL * G->ghost);
+  if (G->var_stride < np || (G->var_stride & 1)) return false;
+  if ((long long)G->nx * G->ny * G->nz >= (1LL << 40)) return false;
+  return true;
+}
+
+bool params_ok(const bssn_grid_t* G, const bssn_params_t* P) {
+  if (!P) return false;
+  if (P->fd_order != 4 && P->fd_order != 8) return false;
+  if (G->ghost < required_ghost(P->fd_order)) return false;
+  if (P->lapse < 0 || P->lapse > 2 || P->shift < 0 || P->shift > 1) return false;
+  if (P->advect_gauge != 0 && P->advect_gauge != 1) return false;
+  if (!std::isfinite(P->ko_eps) || P->ko_eps < 0) return false;
+  if (!std::isfinite(P->shift_coeff) || !std::isfinite(P->eta)) return false;
+  return true;
+}
+
+// Scratch layout, one size for both precisions:
+//   [tables region][constraint partials][finals + flag]
+// The tables region holds, for BSSN_FP64, the double difference tables
+// (2 x 11 x p/2 arrays of var_stride doubles); for BSSN_FP32_RHS, the single
+// precision copy of the state (24 x var_stride floats) followed by the
+// single precision tables - which always fits in the double tables' space.
+struct WorkLayout {
+  size_t tables;     // doubles
+  size_t partials;   // doubles
+  size_t finals;     // doubles (16)
+  size_t total_bytes;
+};
+
+WorkLayout work_layout(const bssn_grid_t& G, const bssn_params_t& P) {
+  Layout L = make_layout(G);
+  WorkLayout W;
+  const size_t dbl = diff_doubles(L, P.fd_order / 2);
+  const size_t f32 = ((size_t)NV * L.vs + 2 * dbl / 2 + 1) / 2;  // floats -> doubles, rounded up
+  W.tables = dbl > f32 ? dbl : f32;
+  W.partials = (size_t)con_blocks(L) * 14;
+  W.finals = 16;
+  W.total_bytes = (W.tables + W.partials + W.finals) * sizeof(double);
+  return W;
+}
+
+struct WorkPtrs {
+  void* dX;       // difference tables (double or float)
+  void* dY;
+  float* f32;     // single-precision state copy (FP32 form)
+  double* dX64;   // double tables (constraints)
+  double* dY64;
+  double* part;
+  double* finals;
+  unsigned int* flag;
+};
+
+WorkPtrs work_ptrs(void* work, const bssn_grid_t& G, const bssn_params_t& P, bssn_precision_t prec) {
+  Layout L = make_layout(G);
+  WorkLayout W = work_layout(G, P);
+  double* base = (double*)work;
+  WorkPtrs w;
+  const size_t H = P.fd_order / 2;
+  w.dX64 = base;
+  w.dY64 = base + NM * H * L.vs;
+  if (prec == BSSN_FP64) {
+    w.f32 = nullptr;
+    w.dX = w.dX64;
+    w.dY = w.dY64;
+  } else {
+    w.f32 = (float*)base;
+    float* t = w.f32 + (size_t)NV * L.vs;
+    w.dX = t;
+    w.dY = t + NM * H * L.vs;
+  }
+  w.part = base + W.tables;
+  w.finals = w.part + W.partials;
+  w.flag = (unsigned int*)(w.finals + 14);
+  return w;
+}
+
+// Difference tables of ys (for the FP32 form: first the single-precision copy).
+cudaError_t run_diffs(int order, bssn_precision_t prec, const Layout& L, const double* ys, const WorkPtrs& w,
+                      cudaStream_t s) {
+  const void* src = ys;
+  if (prec == BSSN_FP32_RHS) {
+    cudaError_t e = launch_to_f32(L, ys, w.f32, s);
+    if (e != cudaSuccess) return e;
+    src = w.f32;
+  }
+  return order == 4 ? launch_diffs<4>(L, prec, src, w.dX, w.dY, s) : launch_diffs<8>(L, prec, src, w.dX, w.dY, s);
+}
+
+cudaError_t run_fused(int order, bssn_precision_t prec, const bssn_grid_t& G, const bssn_params_t& P, const RK& rk,
+                      const double* ys, const double* y0, double* acc, double* out, const WorkPtrs& w, int mode,
+                      cudaStream_t s) {
+  const Layout L = make_layout(G);
+  const Gauge gz = make_gauge(P);
+  StageArgs A{prec == BSSN_FP64 ? (const void*)ys : (const void*)w.f32, ys, y0, acc, out, w.dX, w.dY};
+  if (order == 4) return launch_stage<4>(L, G, P.ko_eps, prec, gz, rk, A, mode, s);
+  return launch_stage<8>(L, G, P.ko_eps, prec, gz, rk, A, mode, s);
+}
+
+cudaError_t run_stage(int order, bssn_precision_t prec, const bssn_grid_t& G, const bssn_params_t& P, const RK& rk,
+                      const double* ys, const double* y0, double* acc, double* out, const WorkPtrs& w, int mode,
+                      cudaStream_t s) {
+  cudaError_t e = run_diffs(order, prec, make_layout(G), ys, w, s);
+  if (e != cudaSuccess) return e;
+  return run_fused(order, prec, G, P, rk, ys, y0, acc, out, w, mode, s);
+}
+
+bool prec_ok(bssn_precision_t prec) { return prec == BSSN_FP64 || prec == BSSN_FP32_RHS; }
+
+// ---------------------------------------------------------------- ghost fill
+__global__ void __launch_bounds__(256) k_fill_ghosts(Layout L, int mode, const double* __restrict__ src, double* u) {
+  const long long ex = L.nx + 2LL * L.g, ey = L.ny + 2LL * L.g, ez = L.nz + 2LL * L.g;
+  const long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (lin >= ex * ey * ez) return;
+  const int i = (int)(lin % ex) - L.g;
+  const long long t = lin / ex;
+  const int j = (int)(t % ey) - L.g;
+  const int k = (int)(t / ey) - L.g;
+  if (i >= 0 && i < L.nx && j >= 0 && j < L.ny && k >= 0 && k < L.nz) return;
+  const long long p = L.off0 + i + j * L.sy + k * L.sz;
+  if (mode == 1) {
+#pragma unroll 4
+    for (int v = 0; v < NV; ++v) u[v * L.vs + p] = __ldg(src + v * L.vs + p);
+    return;
+  }
+  const int ii = ((i % L.nx) + L.nx) % L.nx;
+  const int jj = ((j % L.ny) + L.ny) % L.ny;
+  const int kk = ((k % L.nz) + L.nz) % L.nz;
+  const long long q = L.off0 + ii + jj * L.sy + kk * L.sz;
+#pragma unroll 4
+  for (int v = 0; v < NV; ++v) u[v * L.vs + p] = u[v * L.vs + q];
+}
+
+cudaError_t fill(const bssn_grid_t& G, int mode, const double* src, double* u, cudaStream_t s) {
+  const Layout L = make_layout(G);
+  const long long n = (G.nx + 2LL * G.ghost) * (G.ny + 2LL * G.ghost) * (G.nz + 2LL * G.ghost);
+  k_fill_ghosts<<<(unsigned int)((n + 255) / 256), 256, 0, s>>>(L, mode, src, u);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- reductions
+// Sums (q < 7) and maxima (q >= 7) of the per-block partials, in a fixed order.
+__global__ void __launch_bounds__(256) k_reduce_partials(const double* __restrict__ part, long long nblocks,
+                                                         double* __restrict__ out) {
+  __shared__ double sh[256];
+  for (int q = 0; q < 14; ++q) {
+    double r = 0.0;
+    for (long long b = threadIdx.x; b < nblocks; b += blockDim.x) {
+      const double x = part[b * 14 + q];
+      r = (q < 7) ? r + x : fmax(r, x);
+    }
+    sh[threadIdx.x] = r;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) sh[threadIdx.x] = (q < 7) ? sh[threadIdx.x] + sh[threadIdx.x + o]
+                                                          : fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = sh[0];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- FP rate probe
+constexpr int PROBE_CHAINS = 8;
+__global__ void k_probe_dfma(double* out, double b, double c, int iters) {
+  double a[PROBE_CHAINS];
+  for (int j = 0; j < PROBE_CHAINS; ++j) a[j] = threadIdx.x * 1e-3 + j;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int j = 0; j < PROBE_CHAINS; ++j) a[j] = fma(a[j], b, c);
+  double s = 0;
+  for (int j = 0; j < PROBE_CHAINS; ++j) s += a[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+__global__ void k_probe_dadd(double* out, double b, double c, int iters) {
+  double a[PROBE_CHAINS];
+  for (int j = 0; j < PROBE_CHAINS; ++j) a[j] = threadIdx.x * 1e-3 + j;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int j = 0; j < PROBE_CHAINS; ++j) a[j] = a[j] + b;
+  double s = 0;
+  for (int j = 0; j < PROBE_CHAINS; ++j) s += a[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s + c;
+}
+__global__ void k_probe_ffma(double* out, float b, float c, int iters) {
+  float a[PROBE_CHAINS];
+  for (int j = 0; j < PROBE_CHAINS; ++j) a[j] = threadIdx.x * 1e-3f + j;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int j = 0; j < PROBE_CHAINS; ++j) a[j] = fmaf(a[j], b, c);
+  float s = 0;
+  for (int j = 0; j < PROBE_CHAINS; ++j) s += a[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+const char* bssn_status_string(bssn_status_t s) {
+  switch (s) {
+    case BSSN_OK: return "ok";
+    case BSSN_ERR_INVALID_ARG: return "invalid argument";
+    case BSSN_ERR_CUDA: return "CUDA error";
+    case BSSN_ERR_NONFINITE: return "non-finite value";
+    case BSSN_ERR_TIMEOUT: return "device wait timed out";
+    case BSSN_ERR_UNSUPPORTED: return "unsupported";
+    case BSSN_ERR_NOMEM: return "out of memory";
+  }
+  return "unknown status";
+}
+
+bssn_status_t bssn_last_error(void) { return (bssn_status_t)g_last_error.load(); }
+void bssn_clear_error(void) { g_last_error.store(BSSN_OK); }
+
+unsigned long long bssn_work_bytes(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec) {
+  if (!grid_ok(grid) || !params_ok(grid, params)) return 0;
+  if (prec != BSSN_FP64 && prec != BSSN_FP32_RHS) return 0;
+  return work_layout(*grid, *params).total_bytes;
+}
+
+bssn_status_t bssn_fill_ghosts(const bssn_grid_t* grid, int mode, const double* src, double* state, void* stream) {
+  if (!grid_ok(grid) || (mode != 0 && mode != 1) || !aligned16(state)) return BSSN_ERR_INVALID_ARG;
+  if (mode == 1 && (!aligned16(src) || src == state)) return BSSN_ERR_INVALID_ARG;
+  if (grid->ghost == 0) return BSSN_OK;
+  return latch(fill(*grid, mode, src, state, (cudaStream_t)stream));
+}
+
+bssn_status_t bssn_rhs(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec,
+                       const double* state, double* rhs, void* work, unsigned long long work_bytes, void* stream) {
+  if (!grid_ok(grid) || !params_ok(grid, params) || !prec_ok(prec)) return BSSN_ERR_INVALID_ARG;
+  if (!aligned16(state) || !aligned16(rhs) || !aligned16(work) || state == rhs) return BSSN_ERR_INVALID_ARG;
+  if (work_bytes < work_layout(*grid, *params).total_bytes) return BSSN_ERR_INVALID_ARG;
+  const WorkPtrs w = work_ptrs(work, *grid, *params, prec);
+  const RK rk = make_rk(0, 0.0);
+  return latch(run_stage(params->fd_order, prec, *grid, *params, rk, state, state, nullptr, rhs, w, 1,
+                         (cudaStream_t)stream));
+}
+
+bssn_status_t bssn_ko_dissipation(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec,
+                                  const double* state, double* rhs, void* stream) {
+  if (!grid_ok(grid) || !params_ok(grid, params) || !prec_ok(prec)) return BSSN_ERR_INVALID_ARG;
+  if (!aligned16(state) || !aligned16(rhs) || state == rhs) return BSSN_ERR_INVALID_ARG;
+  const Layout L = make_layout(*grid);
+  cudaError_t e;
+  if (params->fd_order == 4)
+    e = launch_ko<4>(L, *grid, params->ko_eps, prec, state, rhs, (cudaStream_t)stream);
+  else
+    e = launch_ko<8>(L, *grid, params->ko_eps, prec, state, rhs, (cudaStream_t)stream);
+  return latch(e);
+}
+
+bssn_status_t bssn_rk4_stage(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec,
+                             int stage, double dt, const double* y0, const double* ys, double* acc, double* ynext,
+                             void* work, unsigned long long work_bytes, void* stream) {
+  if (!grid_ok(grid) || !params_ok(grid, params) || !prec_ok(prec)) return BSSN_ERR_INVALID_ARG;
+  if (stage < 0 || stage > 3 || !std::isfinite(dt)) return BSSN_ERR_INVALID_ARG;
+  if (!aligned16(y0) || !aligned16(ys) || !aligned16(acc) || !aligned16(ynext) || !aligned16(work))
+    return BSSN_ERR_INVALID_ARG;
+  if (ynext == ys || ynext == acc || acc == ys || acc == y0) return BSSN_ERR_INVALID_ARG;
+  if (work_bytes < work_layout(*grid, *params).total_bytes) return BSSN_ERR_INVALID_ARG;
+  const WorkPtrs w = work_ptrs(work, *grid, *params, prec);
+  return latch(run_stage(params->fd_order, prec, *grid, *params, make_rk(stage, dt), ys, y0, acc, ynext, w, 0,
+                         (cudaStream_t)stream));
+}
+
+bssn_status_t bssn_diff_tables(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec,
+                               const double* state, void* work, unsigned long long work_bytes, void* stream) {
+  if (!grid_ok(grid) || !params_ok(grid, params) || !prec_ok(prec)) return BSSN_ERR_INVALID_ARG;
+  if (!aligned16(state) || !aligned16(work)) return BSSN_ERR_INVALID_ARG;
+  if (work_bytes < work_layout(*grid, *params).total_bytes) return BSSN_ERR_INVALID_ARG;
+  const WorkPtrs w = work_ptrs(work, *grid, *params, prec);
+  return latch(run_diffs(params->fd_order, prec, make_layout(*grid), state, w, (cudaStream_t)stream));
+}
+
+bssn_status_t bssn_rk4_stage_fused(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec,
+                                   int stage, double dt, const double* y0, const double* ys, double* acc,
+                                   double* ynext, void* work, unsigned long long work_bytes, void* stream) {
+  if (!grid_ok(grid) || !params_ok(grid, params) || !prec_ok(prec)) return BSSN_ERR_INVALID_ARG;
+  if (stage < 0 || stage > 3 || !std::isfinite(dt)) return BSSN_ERR_INVALID_ARG;
+  if (!aligned16(y0) || !aligned16(ys) || !aligned16(acc) || !aligned16(ynext) || !aligned16(work))
+    return BSSN_ERR_INVALID_ARG;
+  if (ynext == ys || ynext == acc || acc == ys || acc == y0) return BSSN_ERR_INVALID_ARG;
+  if (work_bytes < work_layout(*grid, *params).total_bytes) return BSSN_ERR_INVALID_ARG;
+  const WorkPtrs w = work_ptrs(work, *grid, *params, prec);
+  return latch(run_fused(params->fd_order, prec, *grid, *params, make_rk(stage, dt), ys, y0, acc, ynext, w, 0,
+                         (cudaStream_t)stream));
+}
+
+bssn_status_t bssn_rk4_step(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec, double dt,
+                            int bc, const double* ghost_src, double* state, double* bufs, void* work,
+                            unsigned long long work_bytes, void* stream) {
+  if (!grid_ok(grid) || !params_ok(grid, params) || !prec_ok(prec)) return BSSN_ERR_INVALID_ARG;
+  if ((bc != 0 && bc != 1) || !std::isfinite(dt)) return BSSN_ERR_INVALID_ARG;
+  if (bc == 1 && !aligned16(ghost_src)) return BSSN_ERR_INVALID_ARG;
+  if (!aligned16(state) || !aligned16(bufs) || !aligned16(work)) return BSSN_ERR_INVALID_ARG;
+  if (work_bytes < work_layout(*grid, *params).total_bytes) return BSSN_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)NV * grid->var_stride;
+  double* ya = bufs;
+  double* yb = bufs + n;
+  double* acc = bufs + 2 * n;
+  const WorkPtrs w = work_ptrs(work, *grid, *params, prec);
+  const int order = params->fd_order;
+  cudaError_t e = cudaSuccess;
+  const double* ys = state;
+  double* outs[4] = {ya, yb, ya, state};
+  for (int st = 0; st < 4 && e == cudaSuccess; ++st) {
+    if (grid->ghost > 0) e = fill(*grid, bc, ghost_src, const_cast<double*>(ys), s);
+    if (e != cudaSuccess) break;
+    e = run_stage(order, prec, *grid, *params, make_rk(st, dt), ys, state, acc, outs[st], w, 0, s);
+    ys = outs[st];
+  }
+  if (e == cudaSuccess && grid->ghost > 0) e = fill(*grid, bc, ghost_src, state, s);
+  return latch(e);
+}
+
+bssn_status_t bssn_constraints(const bssn_grid_t* grid, const bssn_params_t* params, const double* state, double* ham,
+                               double* mom, double* gcon, double* out_l2, double* out_max, void* work,
+                               unsigned long long work_bytes, void* stream) {
+  if (!grid_ok(grid) || !params_ok(grid, params)) return BSSN_ERR_INVALID_ARG;
+  if (!aligned16(state) || !aligned16(work) || !out_l2 || !out_max) return BSSN_ERR_INVALID_ARG;
+  if ((ham && !aligned16(ham)) || (mom && !aligned16(mom)) || (gcon && !aligned16(gcon))) return BSSN_ERR_INVALID_ARG;
+  if (work_bytes < work_layout(*grid, *params).total_bytes) return BSSN_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Layout L = make_layout(*grid);
+  const WorkPtrs w = work_ptrs(work, *grid, *params, BSSN_FP64);
+  cudaError_t e = cudaMemsetAsync(w.flag, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) e = run_diffs(params->fd_order, BSSN_FP64, L, state, w, s);
+  if (e == cudaSuccess) {
+    if (params->fd_order == 4)
+      e = launch_constraints<4>(L, make_coef<4, double>(*grid, 0.0), state, w.dX64, w.dY64, ham, mom, gcon, w.part,
+                                w.flag, s);
+    else
+      e = launch_constraints<8>(L, make_coef<8, double>(*grid, 0.0), state, w.dX64, w.dY64, ham, mom, gcon, w.part,
+                                w.flag, s);
+  }
+  if (e == cudaSuccess) {
+    k_reduce_partials<<<1, 256, 0, s>>>(w.part, con_blocks(L), w.finals);
+    e = cudaGetLastError();
+  }
+  double host[16];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, w.finals, 16 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return latch(e);
+  const double npts = (double)L.npts;
+  for (int q = 0; q < 7; ++q) {
+    out_l2[q] = std::sqrt(host[q] / npts);
+    out_max[q] = host[7 + q];
+  }
+  unsigned int flag;
+  std::memcpy(&flag, &host[14], sizeof(flag));
+  return flag ? BSSN_ERR_NONFINITE : BSSN_OK;
+}
+
+bssn_status_t bssn_probe_fp_rates(double* out) {
+  if (!out) return BSSN_ERR_INVALID_ARG;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return latch(e);
+  const int threads = 256, blocks = sms * 8;
+  double* buf = nullptr;
+  e = cudaMalloc(&buf, sizeof(double) * blocks * threads);
+  if (e != cudaSuccess) return latch(e);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int iters[3] = {2048, 32768, 2048};
+  for (int kind = 0; kind < 3 && e == cudaSuccess; ++kind) {
+    float best = 1e30f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      cudaEventRecord(e0);
+      if (kind == 0) k_probe_dfma<<<blocks, threads>>>(buf, 1.0000001, 1e-9, iters[kind]);
+      if (kind == 1) k_probe_ffma<<<blocks, threads>>>(buf, 1.0000001f, 1e-9f, iters[kind]);
+      if (kind == 2) k_probe_dadd<<<blocks, threads>>>(buf, 1e-9, 0.0, iters[kind]);
+      cudaEventRecord(e1);
+      e = cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) best = ms;
+    }
+    out[kind] = (double)blocks * threads * iters[kind] * PROBE_CHAINS / (best * 1e-3);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  return latch(e == cudaSuccess ? cudaGetLastError() : e);
+}
+
+}  // extern "C"

@@ -1,0 +1,398 @@
+// CUDA kernels of libbssn, templated on the finite-difference order P and
+// on the arithmetic type R of the right-hand side (double, or float for the
+// FP32-RHS form).
+//
+// Design. On GB300 the FP64 pipe issues ~74x fewer operations per second
+// than the FP32 pipe (and double<->float conversions run on that same slow
+// pipe), so the double-precision kernels are shaped to execute as few FP64
+// instructions per grid point as possible; loads, index arithmetic and
+// register spills are cheap by comparison.
+//
+//  * k_to_f32 (FP32 form only): one conversion of the state to single
+//    precision per stage, so that no stencil load converts.
+//  * k_diffs: for the 11 variables that need mixed second derivatives,
+//    stores the first differences u(i+a) - u(i-a) along x and along y
+//    (a = 1..p/2) over the interior extended by p/2 points in the directions
+//    the mixed stencils walk. Differences of stored values are exact; every
+//    mixed derivative is then a weighted sum of exact differences of them -
+//    the tensor-product stencil at half its cost, with its rounding
+//    behaviour.
+//  * k_stage: one thread per interior point: first, second and mixed
+//    derivatives, upwinded advection (the lopsided stencil is mirrored by the
+//    sign of the shift through the address, so warps never diverge),
+//    Kreiss-Oliger dissipation (sharing the paired sums of the second
+//    derivatives), the pointwise algebra and the RK4 stage epilogue, which
+//    is always double precision.
+//
+// Tiles and staging follow the paper's kernel frames only loosely (Sec. 2.6):
+// neighbours are read through the L1/L2 caches; the first-difference tables
+// play the role of its "RHS derivatives" arrays (Sec. 2.3, loop fission).
+#pragma once
+#include "bssn_common.cuh"
+#include "bssn_point.cuh"
+
+namespace bssn {
+
+__device__ __forceinline__ double fmaR(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaR(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <typename R>
+struct StagePtrs {
+  const R* ys;         // state the right-hand side is evaluated on (ghosts filled), in type R
+  const double* ys64;  // the same state in double precision (W for the FP64 1/W of the FP32 form)
+  const double* y0;    // RK4 base state
+  double* acc;         // RK4 accumulator
+  double* out;         // ynext (stage) or rhs (right-hand side only)
+  const R* dX;         // x-difference tables
+  const R* dY;         // y-difference tables
+};
+
+__device__ __forceinline__ void point_coords(const Layout& L, long long lin, int& i, int& j, int& k) {
+  i = (int)(lin % L.nx);
+  const long long t = lin / L.nx;
+  j = (int)(t % L.ny);
+  k = (int)(t / L.ny);
+}
+
+// ------------------------------------------------------------------ FP32 copy
+static __global__ void __launch_bounds__(256) k_to_f32(long long n, long long vs, long long npad,
+                                                const double* __restrict__ u, float* __restrict__ f) {
+  const long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (lin >= n) return;
+  const long long v = lin / npad, q = lin - v * npad;
+  f[v * vs + q] = __double2float_rn(__ldg(u + v * vs + q));
+}
+
+// ------------------------------------------------------------------ differences
+template <int P, typename R>
+__global__ void __launch_bounds__(256) k_diffs(Layout L, const R* __restrict__ u, R* __restrict__ dX,
+                                               R* __restrict__ dY) {
+  constexpr int H = FD<P>::H;
+  const long long ex = L.nx, ey = L.ny + 2 * H, ez = L.nz + 2 * H;
+  const long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (lin >= ex * ey * ez) return;
+  const int i = (int)(lin % ex);
+  const long long t = lin / ex;
+  const int j = (int)(t % ey) - H;
+  const int k = (int)(t / ey) - H;
+  const long long p = L.off0 + i + j * L.sy + k * L.sz;
+  const bool doy = (j >= 0 && j < L.ny);
+#pragma unroll 1
+  for (int m = 0; m < NM; ++m) {
+    const R* v = u + mvar(m) * L.vs;
+#pragma unroll
+    for (int a = 1; a <= H; ++a) {
+      const long long o = (long long)(m * H + a - 1) * L.vs + p;
+      dX[o] = __ldg(v + p + a) - __ldg(v + p - a);
+      if (doy) dY[o] = __ldg(v + p + a * L.sy) - __ldg(v + p - a * L.sy);
+    }
+  }
+}
+
+// first derivative along a stride from the state: sum_a c_a (u_a - u_-a)
+template <int H, typename R>
+__device__ __forceinline__ R d1_direct(const R* __restrict__ v, long long p, long long s, const R* c) {
+  R r = c[1] * (__ldg(v + p + s) - __ldg(v + p - s));
+#pragma unroll
+  for (int a = 2; a <= H; ++a) r = fmaR(c[a], __ldg(v + p + a * s) - __ldg(v + p - a * s), r);
+  return r;
+}
+
+// first derivative from a difference table: sum_a c_a tab_a
+template <int H, typename R>
+__device__ __forceinline__ R d1_table(const R* __restrict__ tab, long long vs, long long p, const R* c) {
+  R r = c[1] * __ldg(tab + p);
+#pragma unroll
+  for (int a = 2; a <= H; ++a) r = fmaR(c[a], __ldg(tab + (a - 1) * vs + p), r);
+  return r;
+}
+
+// mixed derivative: sum_a sum_b cm_ab (tab_a(p + b s) - tab_a(p - b s))
+template <int H, typename R>
+__device__ __forceinline__ R dmix_table(const R* __restrict__ tab, long long vs, long long p, long long s,
+                                        const R (*cm)[5]) {
+  R r = R(0);
+#pragma unroll
+  for (int a = 1; a <= H; ++a) {
+    const R* t = tab + (a - 1) * vs;
+#pragma unroll
+    for (int b = 1; b <= H; ++b) r = fmaR(cm[a][b], __ldg(t + p + b * s) - __ldg(t + p - b * s), r);
+  }
+  return r;
+}
+
+// upwinded advection stencil sum_i up_i u(p + sgn (UPLO+i) s)
+template <int P, typename R>
+__device__ __forceinline__ R upwind(const R* __restrict__ v, long long p, long long s_signed, const R* up) {
+  using F = FD<P>;
+  R r = up[0] * __ldg(v + p + F::UPLO * s_signed);
+#pragma unroll
+  for (int i = 1; i < F::UPN; ++i) r = fmaR(up[i], __ldg(v + p + (F::UPLO + i) * s_signed), r);
+  return r;
+}
+
+__device__ __forceinline__ double abs_bits(double x) {
+  return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ float abs_bits(float x) { return __int_as_float(__float_as_int(x) & 0x7fffffff); }
+__device__ __forceinline__ bool negative_bits(double x) { return __double_as_longlong(x) < 0; }
+__device__ __forceinline__ bool negative_bits(float x) { return __float_as_int(x) < 0; }
+
+// Gather every derivative of the right-hand side at point p.
+// ko_out (if WITH_KO) receives the Kreiss-Oliger term of every variable.
+template <int P, bool WITH_KO, bool WITH_ADV, typename R>
+__device__ __forceinline__ void gather(const Layout& L, const Coef<R>& C, const R* __restrict__ u,
+                                       const R* __restrict__ dX, const R* __restrict__ dY, long long p,
+                                       PointIn<R>& Q, R* ko_out) {
+  using F = FD<P>;
+  constexpr int H = F::H, RR = F::R;
+  const long long vs = L.vs;
+  const long long st[3] = {1, L.sy, L.sz};
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Q.u[v] = __ldg(u + v * vs + p);
+
+  // ---- the 11 variables with second derivatives
+#pragma unroll 1
+  for (int m = 0; m < NM; ++m) {
+    const int var = mvar(m);
+    const R* v = u + var * vs;
+    const R* tx = dX + (long long)m * H * vs;
+    const R* ty = dY + (long long)m * H * vs;
+    R d1v[3], d2v[6];
+    d1v[0] = d1_table<H>(tx, vs, p, C.c1[0]);
+    d1v[1] = d1_table<H>(ty, vs, p, C.c1[1]);
+    d1v[2] = d1_direct<H>(v, p, L.sz, C.c1[2]);
+    const R m2u0 = R(-2) * __ldg(v + p);
+    R ko = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      R dd = R(0);
+#pragma unroll
+      for (int a = 1; a <= RR; ++a) {
+        if (a > H && !WITH_KO) break;
+        const R sa = (__ldg(v + p + a * st[d]) + __ldg(v + p - a * st[d])) + m2u0;
+        if (a <= H) dd = fmaR(C.c2[d][a], sa, dd);
+        if (WITH_KO) ko = fmaR(C.ko[d][a], sa, ko);
+      }
+      d2v[sym(d, d)] = dd;
+    }
+    d2v[1] = dmix_table<H>(tx, vs, p, L.sy, C.cm[0]);  // xy
+    d2v[2] = dmix_table<H>(tx, vs, p, L.sz, C.cm[1]);  // xz
+    d2v[4] = dmix_table<H>(ty, vs, p, L.sz, C.cm[2]);  // yz
+    if (WITH_KO) ko_out[var] = ko;
+    if (m == 0) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Q.dW[d] = d1v[d];
+#pragma unroll
+      for (int s = 0; s < 6; ++s) Q.ddW[s] = d2v[s];
+    } else if (m <= 6) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Q.dg[d][m - 1] = d1v[d];
+#pragma unroll
+      for (int s = 0; s < 6; ++s) Q.ddg[m - 1][s] = d2v[s];
+    } else if (m == 7) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Q.da[d] = d1v[d];
+#pragma unroll
+      for (int s = 0; s < 6; ++s) Q.dda[s] = d2v[s];
+    } else {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Q.db[d][m - 8] = d1v[d];
+#pragma unroll
+      for (int s = 0; s < 6; ++s) Q.ddb[m - 8][s] = d2v[s];
+    }
+  }
+
+  // ---- first derivatives of K and Gt^i
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    Q.dK[d] = d1_direct<H>(u + V_TRK * vs, p, st[d], C.c1[d]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Q.dGam[d][i] = d1_direct<H>(u + (V_GAM1 + i) * vs, p, st[d], C.c1[d]);
+  }
+
+  // ---- dissipation of the other 13 variables
+  if (WITH_KO) {
+    const int others[13] = {V_TRK, V_AT11, V_AT12, V_AT13, V_AT22, V_AT23, V_AT33, V_GAM1, V_GAM2, V_GAM3,
+                            V_B1,  V_B2,   V_B3};
+#pragma unroll 1
+    for (int q = 0; q < 13; ++q) {
+      const int var = others[q];
+      const R* v = u + var * vs;
+      const R m2u0 = R(-2) * __ldg(v + p);
+      R ko = R(0);
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int a = 1; a <= RR; ++a)
+          ko = fmaR(C.ko[d][a], (__ldg(v + p + a * st[d]) + __ldg(v + p - a * st[d])) + m2u0, ko);
+      ko_out[var] = ko;
+    }
+  }
+
+  // ---- upwinded advection of all 24 variables
+  if (WITH_ADV) {
+    long long ss[3];
+    R ab[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const R b = Q.u[V_BETA1 + d];
+      ss[d] = negative_bits(b) ? -st[d] : st[d];
+      ab[d] = abs_bits(b);
+    }
+#pragma unroll 1
+    for (int var = 0; var < NV; ++var) {
+      const R* v = u + var * vs;
+      R a = ab[0] * upwind<P>(v, p, ss[0], C.up[0]);
+      a = fmaR(ab[1], upwind<P>(v, p, ss[1], C.up[1]), a);
+      a = fmaR(ab[2], upwind<P>(v, p, ss[2], C.up[2]), a);
+      Q.adv[var] = a;
+    }
+  } else {
+#pragma unroll
+    for (int var = 0; var < NV; ++var) Q.adv[var] = R(0);
+  }
+}
+
+// 1/W: always computed in double precision (the conformal-factor division
+// that dominates near punctures)
+template <typename R>
+__device__ __forceinline__ R inv_w(const PointIn<R>& Q, const double* ys64, long long p, long long vs);
+template <>
+__device__ __forceinline__ double inv_w<double>(const PointIn<double>& Q, const double*, long long, long long) {
+  return 1.0 / Q.u[V_W];
+}
+template <>
+__device__ __forceinline__ float inv_w<float>(const PointIn<float>&, const double* ys64, long long p, long long) {
+  return __double2float_rn(1.0 / __ldg(ys64 + p));  // W is variable 0
+}
+
+// ------------------------------------------------------------------ fused stage
+// MODE 0: RK4 stage (right-hand side + dissipation, then the stage update).
+// MODE 1: right-hand side only, written to out.
+template <int P, int MODE, typename R>
+__global__ void __launch_bounds__(128) k_stage(Layout L, Coef<R> C, Gauge gz, RK rk, StagePtrs<R> S) {
+  const long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (lin >= L.npts) return;
+  int i, j, k;
+  point_coords(L, lin, i, j, k);
+  const long long p = L.off0 + i + j * L.sy + k * L.sz;
+  PointIn<R> Q;
+  R ko[NV];
+  gather<P, MODE == 0, true, R>(L, C, S.ys, S.dX, S.dY, p, Q, ko);
+  R rhs[NV];
+  const R iW = inv_w<R>(Q, S.ys64, p, L.vs);
+  rhs_point<R>(Q, gz, iW, rhs);
+  const long long vs = L.vs;
+  if (MODE == 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) S.out[v * vs + p] = (double)rhs[v];
+    return;
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const long long o = v * vs + p;
+    const double kv = (double)(rhs[v] + ko[v]);
+    const double y0 = __ldg(S.y0 + o);
+    if (rk.stage == 0) {
+      S.acc[o] = rk.bdt * kv;
+      S.out[o] = fma(rk.cdt, kv, y0);
+    } else if (rk.stage < 3) {
+      S.acc[o] = fma(rk.bdt, kv, S.acc[o]);
+      S.out[o] = fma(rk.cdt, kv, y0);
+    } else {
+      S.out[o] = y0 + fma(rk.bdt, kv, S.acc[o]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ dissipation only
+template <int P, typename R>
+__global__ void __launch_bounds__(256) k_ko(Layout L, Coef<R> C, const double* __restrict__ u, double* rhs) {
+  using F = FD<P>;
+  const long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (lin >= L.npts) return;
+  int i, j, k;
+  point_coords(L, lin, i, j, k);
+  const long long p = L.off0 + i + j * L.sy + k * L.sz;
+  const long long st[3] = {1, L.sy, L.sz};
+#pragma unroll 1
+  for (int var = 0; var < NV; ++var) {
+    const double* v = u + var * L.vs;
+    const R m2u0 = R(-2) * (R)__ldg(v + p);
+    R ko = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int a = 1; a <= F::R; ++a)
+        ko = fmaR(C.ko[d][a], ((R)__ldg(v + p + a * st[d]) + (R)__ldg(v + p - a * st[d])) + m2u0, ko);
+    rhs[var * L.vs + p] += (double)ko;
+  }
+}
+
+// ------------------------------------------------------------------ constraints
+// Per-block partial results: 7 sums of squares, 7 maxima, written to
+// part[blockIdx.x * 14 + q]. Always double precision.
+template <int P>
+__global__ void __launch_bounds__(128) k_constraints(Layout L, Coef<double> C, const double* __restrict__ u,
+                                                     const double* __restrict__ dX, const double* __restrict__ dY,
+                                                     double* ham, double* mom, double* gcon, double* part,
+                                                     unsigned int* flag) {
+  constexpr int H = FD<P>::H;
+  const long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double c[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) c[q] = 0.0;
+  bool bad = false;
+  if (lin < L.npts) {
+    int i, j, k;
+    point_coords(L, lin, i, j, k);
+    const long long p = L.off0 + i + j * L.sy + k * L.sz;
+    PointIn<double> Q;
+    gather<P, false, false, double>(L, C, u, dX, dY, p, Q, nullptr);
+    double dAt[3][6];
+    const long long st[3] = {1, L.sy, L.sz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int s = 0; s < 6; ++s) dAt[d][s] = d1_direct<H>(u + (V_AT11 + s) * L.vs, p, st[d], C.c1[d]);
+    const double iW = 1.0 / Q.u[V_W];
+    constraints_point<double>(Q, dAt, iW, c);
+    if (ham) ham[p] = c[0];
+    if (mom)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) mom[a * L.vs + p] = c[1 + a];
+    if (gcon)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) gcon[a * L.vs + p] = c[4 + a];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) bad |= !isfinite(c[q]);
+  }
+  if (bad) atomicOr(flag, 1u);
+  __shared__ double red[4][14];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    double s = c[q] * c[q];
+    double m = fabs(c[q]);
+    if (!(m == m)) m = 0.0;  // NaN handled by the flag
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_down_sync(0xffffffffu, s, o);
+      m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    }
+    if (lane == 0) {
+      red[warp][q] = s;
+      red[warp][7 + q] = m;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 14) {
+    const int q = threadIdx.x;
+    double r = red[0][q];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = (q < 7) ? r + red[w][q] : fmax(r, red[w][q]);
+    part[(long long)blockIdx.x * 14 + q] = r;
+  }
+}
+
+}  // namespace bssn

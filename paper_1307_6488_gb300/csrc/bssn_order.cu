@@ -1,0 +1,74 @@
+// Instantiates the kernels and launchers for one finite-difference order,
+// selected at compile time with -DBSSN_ORDER=4 or -DBSSN_ORDER=8.
+#include "bssn_kernels.cuh"
+#include "bssn_launch.h"
+
+#ifndef BSSN_ORDER
+#error "compile with -DBSSN_ORDER=4 or -DBSSN_ORDER=8"
+#endif
+
+namespace bssn {
+
+static inline unsigned int blocks_for(long long n, int threads) { return (unsigned int)((n + threads - 1) / threads); }
+
+template <>
+cudaError_t launch_diffs<BSSN_ORDER>(const Layout& L, bssn_precision_t prec, const void* u, void* dX, void* dY,
+                                     cudaStream_t s) {
+  constexpr int H = FD<BSSN_ORDER>::H;
+  const long long n = (long long)L.nx * (L.ny + 2 * H) * (L.nz + 2 * H);
+  if (prec == BSSN_FP64)
+    k_diffs<BSSN_ORDER, double><<<blocks_for(n, 256), 256, 0, s>>>(L, (const double*)u, (double*)dX, (double*)dY);
+  else
+    k_diffs<BSSN_ORDER, float><<<blocks_for(n, 256), 256, 0, s>>>(L, (const float*)u, (float*)dX, (float*)dY);
+  return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t stage_typed(const Layout& L, const bssn_grid_t& G, double eps, const Gauge& gz, const RK& rk,
+                               const StageArgs& A, int mode, cudaStream_t s) {
+  StagePtrs<R> S{(const R*)A.ys, A.ys64, A.y0, A.acc, A.out, (const R*)A.dX, (const R*)A.dY};
+  const Coef<R> C = make_coef<BSSN_ORDER, R>(G, eps);
+  const unsigned int nb = blocks_for(L.npts, STAGE_THREADS);
+  if (mode == 0)
+    k_stage<BSSN_ORDER, 0, R><<<nb, STAGE_THREADS, 0, s>>>(L, C, gz, rk, S);
+  else
+    k_stage<BSSN_ORDER, 1, R><<<nb, STAGE_THREADS, 0, s>>>(L, C, gz, rk, S);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_stage<BSSN_ORDER>(const Layout& L, const bssn_grid_t& G, double eps, bssn_precision_t prec,
+                                     const Gauge& gz, const RK& rk, const StageArgs& A, int mode, cudaStream_t s) {
+  if (prec == BSSN_FP64) return stage_typed<double>(L, G, eps, gz, rk, A, mode, s);
+  return stage_typed<float>(L, G, eps, gz, rk, A, mode, s);
+}
+
+template <>
+cudaError_t launch_ko<BSSN_ORDER>(const Layout& L, const bssn_grid_t& G, double eps, bssn_precision_t prec,
+                                  const double* u, double* rhs, cudaStream_t s) {
+  if (prec == BSSN_FP64)
+    k_ko<BSSN_ORDER, double><<<blocks_for(L.npts, 256), 256, 0, s>>>(L, make_coef<BSSN_ORDER, double>(G, eps), u, rhs);
+  else
+    k_ko<BSSN_ORDER, float><<<blocks_for(L.npts, 256), 256, 0, s>>>(L, make_coef<BSSN_ORDER, float>(G, eps), u, rhs);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_constraints<BSSN_ORDER>(const Layout& L, const Coef<double>& C, const double* u,
+                                           const double* dX, const double* dY, double* ham, double* mom,
+                                           double* gcon, double* part, unsigned int* flag, cudaStream_t s) {
+  k_constraints<BSSN_ORDER><<<(unsigned int)con_blocks(L), CON_THREADS, 0, s>>>(L, C, u, dX, dY, ham, mom, gcon,
+                                                                               part, flag);
+  return cudaGetLastError();
+}
+
+#if BSSN_ORDER == 4
+cudaError_t launch_to_f32(const Layout& L, const double* u, float* f, cudaStream_t s) {
+  const long long npad = (L.nx + 2LL * L.g) * (L.ny + 2LL * L.g) * (L.nz + 2LL * L.g);
+  const long long n = (long long)NV * npad;
+  k_to_f32<<<blocks_for(n, 256), 256, 0, s>>>(n, L.vs, npad, u, f);
+  return cudaGetLastError();
+}
+#endif
+
+}  // namespace bssn

@@ -64,21 +64,14 @@ def flat_space(nx, ny, nz, g, beta=(0.0, 0.0, 0.0)):
 
 
 def periodic_wrap(u, g):
-    """Fill the ghost zones of every variable by periodic wrap (in place)."""
+    """Fill the ghost zones of every variable by periodic wrap (in place);
+    works for any interior size, including n < g."""
     if g == 0:
         return u
     for axis in (1, 2, 3):
         n = u.shape[axis] - 2 * g
-        src_lo = [slice(None)] * 4
-        dst_lo = [slice(None)] * 4
-        src_lo[axis] = slice(n, n + g)
-        dst_lo[axis] = slice(0, g)
-        u[tuple(dst_lo)] = u[tuple(src_lo)]
-        src_hi = [slice(None)] * 4
-        dst_hi = [slice(None)] * 4
-        src_hi[axis] = slice(g, 2 * g)
-        dst_hi[axis] = slice(n + g, n + 2 * g)
-        u[tuple(dst_hi)] = u[tuple(src_hi)]
+        idx = (np.arange(-g, n + g) % n) + g
+        u[...] = np.take(u, idx, axis=axis)
     return u
 
 

@@ -1,0 +1,101 @@
+"""The C ABI (include/bssn.h) without a GPU: the library loads, exports
+every declared entry point, sizes its scratch, and rejects invalid arguments
+with a status code before launching anything (no call here reaches a kernel:
+each one is invalid for at least one reason the host checks)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1307_6488_gb300 import binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1307_6488_gb300 import build
+    build.build()
+    return B.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "bssn.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bssn_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_inputs_module_holds_no_evolution_arithmetic():
+    src = open(os.path.join(ROOT, "paper_1307_6488_gb300", "inputs.py")).read()
+    for word in ("rhs", "ko_", "rk4", "stencil", "upwind"):
+        assert word not in src.lower().replace("right-hand side", ""), word
+
+
+def test_status_strings(L):
+    for s in range(7):
+        assert B.status_string(s)
+    assert B.status_string(99) == "unknown status"
+
+
+def test_work_bytes(L):
+    g = B.make_grid(32, 24, 16, ghost=5, dx=0.1)
+    p8 = B.make_params(fd_order=8)
+    p4 = B.make_params(fd_order=4)
+    n8 = B.work_bytes(g, p8)
+    n4 = B.work_bytes(g, p4)
+    assert n8 >= 2 * 11 * 4 * g.var_stride * 8
+    assert n4 >= 2 * 11 * 2 * g.var_stride * 8
+    assert n8 > n4
+    bad = B.make_grid(32, 24, 16, ghost=4, dx=0.1)  # ghost 4 < 5 needed at 8th order
+    assert B.work_bytes(bad, p8) == 0
+    assert B.work_bytes(g, p8, 7) == 0
+
+
+FAKE = 1 << 20  # aligned but never dereferenced: every call below is invalid
+
+
+def test_invalid_arguments_rejected(L):
+    G = ctypes.byref
+    g = B.make_grid(8, ghost=3, dx=0.1)
+    p = B.make_params(fd_order=4)
+    nb = B.work_bytes(g, p)
+    E = B.ERR_INVALID_ARG
+    # order not supported
+    assert L.bssn_rhs(G(g), G(B.make_params(fd_order=6)), 0, FAKE, FAKE + 4096, FAKE * 2, nb, None) == E
+    # ghost too small for 8th order
+    assert L.bssn_rhs(G(g), G(B.make_params(fd_order=8)), 0, FAKE, FAKE + 4096, FAKE * 2, nb, None) == E
+    # misaligned state pointer
+    assert L.bssn_rhs(G(g), G(p), 0, FAKE + 8, FAKE * 4, FAKE * 2, nb, None) == E
+    # aliasing state and rhs
+    assert L.bssn_rhs(G(g), G(p), 0, FAKE, FAKE, FAKE * 2, nb, None) == E
+    # scratch too small
+    assert L.bssn_rhs(G(g), G(p), 0, FAKE, FAKE * 4, FAKE * 2, nb - 8, None) == E
+    # unknown precision
+    assert L.bssn_rhs(G(g), G(p), 9, FAKE, FAKE * 4, FAKE * 2, nb, None) == E
+    # bad stage / non-finite dt / aliasing
+    assert L.bssn_rk4_stage(G(g), G(p), 0, 4, 0.1, FAKE, FAKE, FAKE * 2, FAKE * 3, FAKE * 4, nb, None) == E
+    assert L.bssn_rk4_stage(G(g), G(p), 0, 0, float("nan"), FAKE, FAKE, FAKE * 2, FAKE * 3, FAKE * 4, nb, None) == E
+    assert L.bssn_rk4_stage(G(g), G(p), 0, 1, 0.1, FAKE, FAKE * 3, FAKE * 2, FAKE * 3, FAKE * 4, nb, None) == E
+    # bad grid: zero size, odd var_stride, stride too small, bad spacing
+    for bad in (B.Grid(0, 8, 8, 3, 0.1, 0.1, 0.1, 4096), B.Grid(8, 8, 8, 3, 0.1, 0.1, 0.1, 14 ** 3 + 1),
+                B.Grid(8, 8, 8, 3, 0.1, 0.1, 0.1, 100), B.Grid(8, 8, 8, 3, -0.1, 0.1, 0.1, 4096)):
+        assert L.bssn_fill_ghosts(G(bad), 0, None, FAKE, None) == E
+    # ghost modes
+    assert L.bssn_fill_ghosts(G(g), 2, None, FAKE, None) == E
+    assert L.bssn_fill_ghosts(G(g), 1, None, FAKE, None) == E
+    # bad gauge selections
+    assert L.bssn_rhs(G(g), G(B.make_params(lapse=3)), 0, FAKE, FAKE * 4, FAKE * 2, nb, None) == E
+    assert L.bssn_rhs(G(g), G(B.make_params(shift=2)), 0, FAKE, FAKE * 4, FAKE * 2, nb, None) == E
+    # constraints without host outputs
+    assert L.bssn_constraints(G(g), G(p), FAKE, None, None, None, None, None, FAKE * 2, nb, None) == E
+    # step: bad boundary mode
+    assert L.bssn_rk4_step(G(g), G(p), 0, 0.1, 3, None, FAKE, FAKE * 2, FAKE * 4, nb, None) == E
+    assert B.last_error() == B.OK

@@ -1,0 +1,111 @@
+"""FP32-RHS form: derivatives, right-hand side and dissipation in single
+precision on the double-precision state, 1/W and the RK4 update in double
+precision. Its error against the FP64 oracle is stated and bounded here.
+
+Single precision represents the state to 6e-8 relative; a second
+difference of it over L/h points carries ~ 6e-8 * 4 (L/h)^2 relative error,
+so on the smooth data below (L/h ~ 16) the bound is ~1e-4 per tensor field.
+Data with 1e-10 noise on O(1) fields (the 24^3 gauge wave) is below single
+precision resolution and is a double-precision-only case."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1307_6488_gb300 import binding as B
+from paper_1307_6488_gb300 import inputs
+
+from gpu_common import grid_for, interior, need_gpu, oracle_params, perturbed_bl, rel_err_tensor
+
+pytestmark = pytest.mark.gpu
+
+FP32_RHS_TOL = 3e-4
+FP32_STEP_TOL = 1e-3
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_fp32_flat_space_exact_zero(order):
+    torch = need_gpu()
+    g = order // 2 + 1
+    u = inputs.flat_space(9, 8, 7, g)
+    p = B.make_params(fd_order=order)
+    grid = grid_for(u, g, 0.1)
+    d = B.upload(u, grid)
+    out = B.alloc_state(grid)
+    work = B.alloc_work(grid, p, B.FP32_RHS)
+    B.rhs(grid, p, B.FP32_RHS, d, out, work)
+    B.ko_dissipation(grid, p, B.FP32_RHS, d, out)
+    torch.cuda.synchronize()
+    assert np.all(interior(B.download(out, grid), g) == 0.0)
+
+
+def smooth_bl(nx, ny, nz, g, h, seed):
+    """Brill-Lindquist-like data (off-grid punctures, kept away from the box)
+    plus a seeded smooth perturbation: every variable nonzero and smooth."""
+    return perturbed_bl(nx, ny, nz, g, h, seed=seed, amp=1e-2)
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_fp32_rhs_vs_oracle(order):
+    torch = need_gpu()
+    g = order // 2 + 1
+    h = 0.12
+    u = smooth_bl(17, 13, 11, g, h, seed=40 + order)
+    p = B.make_params(fd_order=order)
+    grid = grid_for(u, g, h)
+    d = B.upload(u, grid)
+    work = B.alloc_work(grid, p, B.FP32_RHS)
+    for ko in (False, True):
+        out = B.alloc_state(grid)
+        B.rhs(grid, p, B.FP32_RHS, d, out, work)
+        if ko:
+            B.ko_dissipation(grid, p, B.FP32_RHS, d, out)
+        torch.cuda.synchronize()
+        want = oracle.rhs(u, g, h, oracle_params(p), ko=ko)
+        err = rel_err_tensor(B.download(out, grid), want, g)
+        assert np.max(err) < FP32_RHS_TOL, dict(zip(inputs.VARS, err))
+        assert np.max(err) > 1e-9  # it really is single precision
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_fp32_steps_vs_oracle(order):
+    """Three RK4 steps with static ghosts: change of the state against the
+    oracle's change, per tensor field."""
+    torch = need_gpu()
+    g = order // 2 + 1
+    h = 0.15
+    u = smooth_bl(14, 12, 10, g, h, seed=60 + order)
+    p = B.make_params(fd_order=order)
+    grid = grid_for(u, g, h)
+    state = B.upload(u, grid)
+    src = B.upload(u, grid)
+    bufs = B.alloc_state(grid, n=3)
+    work = B.alloc_work(grid, p, B.FP32_RHS)
+    want = u.copy()
+    dt = 0.25 * h
+    for _ in range(3):
+        B.rk4_step(grid, p, B.FP32_RHS, dt, 1, src, state, bufs, work)
+        want = oracle.rk4_step(want, g, h, dt, oracle_params(p), bc=1, ghost_src=u)
+    torch.cuda.synchronize()
+    got = B.download(state, grid)
+    err = rel_err_tensor(got - u, want - u, g)
+    assert np.max(err) < FP32_STEP_TOL, dict(zip(inputs.VARS, err))
+
+
+def test_fp32_stage_split_matches_fused_call():
+    """bssn_diff_tables + bssn_rk4_stage_fused == bssn_rk4_stage, both forms."""
+    torch = need_gpu()
+    g = 5
+    u = smooth_bl(12, 12, 12, g, 0.1, seed=77)
+    inputs.periodic_wrap(u, g)
+    p = B.make_params(fd_order=8)
+    grid = grid_for(u, g, 0.1)
+    y0 = B.upload(u, grid)
+    for prec in (B.FP64, B.FP32_RHS):
+        work = B.alloc_work(grid, p, prec)
+        a1, n1 = B.alloc_state(grid), B.alloc_state(grid)
+        a2, n2 = B.alloc_state(grid), B.alloc_state(grid)
+        B.rk4_stage(grid, p, prec, 0, 0.02, y0, y0, a1, n1, work)
+        B.diff_tables(grid, p, prec, y0, work)
+        B.rk4_stage_fused(grid, p, prec, 0, 0.02, y0, y0, a2, n2, work)
+        torch.cuda.synchronize()
+        assert torch.equal(n1, n2) and torch.equal(a1, a2)
