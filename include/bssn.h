@@ -151,6 +151,34 @@ bssn_status_t bssn_rk4_stage_fused(const bssn_grid_t* grid, const bssn_params_t*
                                    int stage, double dt, const double* y0, const double* ys, double* acc,
                                    double* ynext, void* work, unsigned long long work_bytes, void* stream);
 
+/* Largest scratch, in bytes, that bssn_rk4_stage_noalloc can use (64 MiB). */
+#define BSSN_NOALLOC_SCRATCH_BYTES (64ull << 20)
+
+/* bssn_rk4_stage for callers that cannot allocate device memory: same
+ * arguments and results, but no `work` buffer and no allocation of any kind.
+ * The paper has no counterpart to this entry point. It is for code that may
+ * not call cudaMalloc: a plugin inside a host application that owns the
+ * device memory budget, or a time-critical loop that must not pay
+ * cudaMalloc's implicit synchronisation. Such callers still pass y0, ys, acc
+ * and ynext.
+ * Scratch: a file-scope device array of BSSN_NOALLOC_SCRATCH_BYTES, created on
+ * each GPU where this entry point runs and held until the process exits. A
+ * grid whose scratch need (bssn_work_bytes() for the same grid, params and
+ * precision) exceeds it is rejected with BSSN_ERR_INVALID_ARG before anything
+ * is launched. For example, at 8th order in FP64 n <= 35 interior points per
+ * axis fit; at 4th order, n <= 51.
+ * Set-up: the first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture.
+ * Sharing: every call uses the same array and overwrites what the previous
+ * call left there; nothing in it has to start at zero. Calls that overlap on
+ * the GPU (on different streams without ordering between them) race on the
+ * array; serialise them. CUDA failures are reported by the returned status
+ * only (bssn_last_error does not see them). */
+bssn_status_t bssn_rk4_stage_noalloc(const bssn_grid_t* grid, const bssn_params_t* params,
+                                     bssn_precision_t prec, int stage, double dt, const double* y0,
+                                     const double* ys, double* acc, double* ynext, void* stream);
+
 /* One full RK4 step in place on `state`: four fused stages with the ghosts
  * filled before each (bc 0 periodic, bc 1 static from ghost_src). Needs three
  * state-sized buffers in `bufs` (bufs, bufs + var_stride*24, ...: 3*24*

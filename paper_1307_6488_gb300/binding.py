@@ -166,6 +166,19 @@ def rk4_stage_fused(grid, params, prec, stage, dt, y0, ys, acc, ynext, work, str
            "rk4_stage_fused")
 
 
+def rk4_stage_noalloc(grid, params, prec, stage, dt, y0, ys, acc, ynext, stream=None):
+    """bssn_rk4_stage_noalloc: the stage without a scratch buffer or any
+    allocation (the library's static scratch; see include/bssn.h)."""
+    L = lib()
+    if not getattr(L, "_noalloc_typed", False):
+        L.bssn_rk4_stage_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_double, _p, _p, _p, _p, _p]
+        L.bssn_rk4_stage_noalloc.restype = ctypes.c_int
+        L._noalloc_typed = True
+    _check(L.bssn_rk4_stage_noalloc(ctypes.byref(grid), ctypes.byref(params), prec, stage, dt, _ptr(y0), _ptr(ys),
+                                    _ptr(acc), _ptr(ynext), _stream(stream)), "rk4_stage_noalloc")
+
+
 def rk4_step(grid, params, prec, dt, bc, ghost_src, state, bufs, work, stream=None):
     _check(lib().bssn_rk4_step(ctypes.byref(grid), ctypes.byref(params), prec, dt, bc, _ptr(ghost_src), _ptr(state),
                                _ptr(bufs), _ptr(work), _nbytes(work), _stream(stream)), "rk4_step")
