@@ -188,6 +188,49 @@ bssn_status_t bssn_rk4_step(const bssn_grid_t* grid, const bssn_params_t* params
                             double dt, int bc, const double* ghost_src, double* state, double* bufs,
                             void* work, unsigned long long work_bytes, void* stream);
 
+/* ---------------------------------------------------------------- batched patches
+ * Many independent uneven grid patches advanced by one RK4 step per call,
+ * the single-GPU analogue of the block-structured (AMR / multi-block) grids
+ * the paper plans for (Sec. 4; tile selection prior art, Sec. 2.6). Each
+ * patch has static ghosts: before every stage they are copied from the
+ * patch's t = 0 values. There is no exchange between patches. */
+typedef struct bssn_plan bssn_plan_t;
+
+typedef struct {
+  bssn_grid_t grid;          /* the patch's grid (its own size, ghost width, spacing) */
+  double* state;             /* DEVICE state of the patch (layout as above): initial values
+                                in, the stepped values out; caller-owned */
+  const double* ghost_src;   /* DEVICE t = 0 values of the patch (same layout): the source
+                                of its static ghosts; caller-owned, must not equal state */
+} bssn_block_t;
+
+/* Builds a plan for nblocks patches (params and precision shared by all).
+ * The plan allocates and owns, per patch, three stage buffers and its
+ * difference tables, plus the patch table and one CUDA graph per step size
+ * (about 3 + 2*11*p/2*8/(24*8) state copies per patch in FP64). autotune = 1
+ * times every candidate tile shape of the fused stage kernel on one
+ * representative patch per size class and keeps the fastest (cached per
+ * process by size class, order and precision); autotune = 0 uses runs of 128
+ * consecutive points. Synchronizes the device. Returns BSSN_ERR_NOMEM if an
+ * allocation fails (nothing is leaked). */
+bssn_status_t bssn_plan_create(bssn_plan_t** out, const bssn_block_t* blocks, int nblocks,
+                               const bssn_params_t* params, bssn_precision_t prec, int autotune);
+
+/* One RK4 step (four fused stages, Sec. 3.3's method of lines) of every
+ * patch in the plan: one CUDA graph launch on `stream` (captured on the first
+ * call with this dt, and again whenever dt changes). Each patch's state holds
+ * the new values afterwards, ghosts refilled. Asynchronous. */
+bssn_status_t bssn_batch_step(bssn_plan_t* plan, double dt, void* stream);
+
+/* Interior points and stage tiles of the plan (HOST outputs, nullable); shapes
+ * (HOST, nullable, nblocks entries) receives each patch's tile shape index:
+ * 0 = runs of 128 consecutive points, 1..6 = (32,4,1) (16,8,1) (8,8,2)
+ * (32,2,2) (16,4,2) (8,4,4). */
+bssn_status_t bssn_plan_info(const bssn_plan_t* plan, long long* points, long long* tiles, int* shapes);
+
+/* Frees everything the plan owns (synchronizes the device). */
+bssn_status_t bssn_plan_destroy(bssn_plan_t* plan);
+
 /* Constraints at interior points (always double precision):
  *   H   = R + 2/3 K^2 - At_ij At^ij                      (Hamiltonian)
  *   M_i = gt^jk D_k At_ij - 3/W At_i^j d_j W - 2/3 d_i K  (momentum)

@@ -179,6 +179,50 @@ def rk4_stage_noalloc(grid, params, prec, stage, dt, y0, ys, acc, ynext, stream=
                                     _ptr(acc), _ptr(ynext), _stream(stream)), "rk4_stage_noalloc")
 
 
+class Block(ctypes.Structure):
+    _fields_ = [("grid", Grid), ("state", ctypes.c_void_p), ("ghost_src", ctypes.c_void_p)]
+
+
+def _plan_lib():
+    L = lib()
+    if not getattr(L, "_plan_typed", False):
+        L.bssn_plan_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Block), ctypes.c_int,
+                                       ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int]
+        L.bssn_batch_step.argtypes = [_p, ctypes.c_double, _p]
+        L.bssn_plan_info.argtypes = [_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), _p]
+        L.bssn_plan_destroy.argtypes = [_p]
+        for n in ("bssn_plan_create", "bssn_batch_step", "bssn_plan_info", "bssn_plan_destroy"):
+            getattr(L, n).restype = ctypes.c_int
+        L._plan_typed = True
+    return L
+
+
+def plan_create(blocks, params, prec=FP64, autotune=1):
+    """blocks: list of (Grid, state, ghost_src) with device tensors/addresses.
+    Returns an opaque plan handle (int)."""
+    arr = (Block * len(blocks))(*[Block(g, _ptr(s), _ptr(src)) for (g, s, src) in blocks])
+    h = ctypes.c_void_p()
+    _check(_plan_lib().bssn_plan_create(ctypes.byref(h), arr, len(blocks), ctypes.byref(params), prec, autotune),
+           "plan_create")
+    return h.value
+
+
+def batch_step(plan, dt, stream=None):
+    _check(_plan_lib().bssn_batch_step(plan, dt, _stream(stream)), "batch_step")
+
+
+def plan_info(plan, nblocks):
+    pts, tiles = ctypes.c_longlong(), ctypes.c_longlong()
+    shapes = np.zeros(nblocks, dtype=np.int32)
+    _check(_plan_lib().bssn_plan_info(plan, ctypes.byref(pts), ctypes.byref(tiles), shapes.ctypes.data_as(_p)),
+           "plan_info")
+    return pts.value, tiles.value, shapes
+
+
+def plan_destroy(plan):
+    _check(_plan_lib().bssn_plan_destroy(plan), "plan_destroy")
+
+
 def rk4_step(grid, params, prec, dt, bc, ghost_src, state, bufs, work, stream=None):
     _check(lib().bssn_rk4_step(ctypes.byref(grid), ctypes.byref(params), prec, dt, bc, _ptr(ghost_src), _ptr(state),
                                _ptr(bufs), _ptr(work), _nbytes(work), _stream(stream)), "rk4_step")

@@ -20,6 +20,7 @@ UNITS = [
     ("bssn_order.cu", "bssn_order4.o", ["-DBSSN_ORDER=4"]),
     ("bssn_order.cu", "bssn_order8.o", ["-DBSSN_ORDER=8"]),
     ("bssn_noalloc.cu", "bssn_noalloc.o", []),
+    ("bssn_batch.cu", "bssn_batch.o", []),
 ]
 
 

@@ -271,12 +271,22 @@ __device__ __forceinline__ float inv_w<float>(const PointIn<float>&, const doubl
 // MODE 0: RK4 stage (right-hand side + dissipation, then the stage update).
 // MODE 1: right-hand side only, written to out.
 template <int P, int MODE, typename R>
+__device__ __forceinline__ void stage_point(const Layout& L, const Coef<R>& C, const Gauge& gz, const RK& rk,
+                                            const StagePtrs<R>& S, long long p);
+
+template <int P, int MODE, typename R>
 __global__ void __launch_bounds__(128) k_stage(Layout L, Coef<R> C, Gauge gz, RK rk, StagePtrs<R> S) {
   const long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (lin >= L.npts) return;
   int i, j, k;
   point_coords(L, lin, i, j, k);
-  const long long p = L.off0 + i + j * L.sy + k * L.sz;
+  stage_point<P, MODE, R>(L, C, gz, rk, S, L.off0 + i + j * L.sy + k * L.sz);
+}
+
+// One interior point p of one stage: gather, algebra, dissipation, epilogue.
+template <int P, int MODE, typename R>
+__device__ __forceinline__ void stage_point(const Layout& L, const Coef<R>& C, const Gauge& gz, const RK& rk,
+                                            const StagePtrs<R>& S, long long p) {
   PointIn<R> Q;
   R ko[NV];
   gather<P, MODE == 0, true, R>(L, C, S.ys, S.dX, S.dY, p, Q, ko);

@@ -141,6 +141,54 @@ def brill_lindquist(n, g, lo=-8.0, hi=8.0, masses=(0.5, 0.5), centers=((-1.5, 0,
     return u, h
 
 
+def patch_tree(nblocks=192, seed=6488, sides=tuple(range(16, 97, 8)), h0=0.5, levels=4,
+               centers=((-1.5, 0.0, 0.0), (1.5, 0.0, 0.0))):
+    """Seeded set of refinement patches around two punctures: patch b has
+    level L in [0, levels) (finer levels drawn more often), spacing
+    h0 / 2^L (ratio-2 levels), per-axis sizes drawn from `sides`, and its
+    centre near puncture b % 2 at an offset that shrinks with the level.
+    Returns a list of dicts n=(nx, ny, nz), h, origin (lower corner of the
+    interior cell faces), level."""
+    out = []
+    for b in range(nblocks):
+        r = 0.5 * (uniform_noise(seed, b, (8,)) + 1.0)  # uniform [0, 1)
+        level = min(levels - 1, int(levels * np.sqrt(r[0])))
+        h = h0 / 2 ** level
+        n = tuple(int(sides[min(len(sides) - 1, int(len(sides) * r[1 + a]))]) for a in range(3))
+        reach = 3.0 / 2 ** level
+        c = centers[b % len(centers)]
+        centre = [c[a] + (2 * r[4 + a] - 1) * reach for a in range(3)]
+        origin = tuple(centre[a] - n[a] * h / 2 for a in range(3))
+        out.append(dict(n=n, h=h, origin=origin, level=level))
+    return out
+
+
+def bl_conformal_tricubic(n, g, h, origin, masses=(0.5, 0.5), centers=((-1.5, 0.0, 0.0), (1.5, 0.0, 0.0))):
+    """psi^-2 of Brill-Lindquist data on one patch (interior and g ghosts,
+    cell centres origin + (i + 1/2) h), by tricubic Lagrange interpolation of
+    its values on the node lattice origin + j h: the 4-point midpoint weights
+    (-1, 9, 9, -1)/16 applied along x, then y, then z. Shape (nz+2g, ny+2g,
+    nx+2g). This is W = alpha of the patch."""
+    nx, ny, nz = n
+    ax = [origin[a] + np.arange(-g - 1, n[a] + g + 2) * h for a in range(3)]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    psi = np.ones_like(X)
+    for m, c in zip(masses, centers):
+        psi += m / (2 * np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2))
+    f = psi ** -2.0
+
+    def mid(a, axis):
+        m = a.shape[axis] - 3
+        s = [slice(None)] * 3
+
+        def take(k):
+            s[axis] = slice(k, k + m)
+            return a[tuple(s)]
+        return (-take(0) + 9 * take(1) + 9 * take(2) - take(3)) / 16.0
+
+    return mid(mid(mid(f, 2), 1), 0)
+
+
 def smooth_perturbation(u, g, amplitude, seed, h, periodic=False):
     """Add a seeded smooth perturbation to every variable, ghosts included:
     a sum of three plane waves per variable with seeded wave vectors (1..3

@@ -99,3 +99,22 @@ def test_invalid_arguments_rejected(L):
     # step: bad boundary mode
     assert L.bssn_rk4_step(G(g), G(p), 0, 0.1, 3, None, FAKE, FAKE * 2, FAKE * 4, nb, None) == E
     assert B.last_error() == B.OK
+
+
+def test_plan_invalid_arguments_rejected(L):
+    p = B.make_params(fd_order=4)
+    good = B.make_grid(8, ghost=4, dx=0.1)
+    bad = B.make_grid(8, ghost=2, dx=0.1)  # ghost 2 < 3 needed at 4th order
+    with pytest.raises(B.BssnError) as e:
+        B.plan_create([(bad, FAKE, FAKE * 2)], p)
+    assert e.value.status == B.ERR_INVALID_ARG
+    with pytest.raises(B.BssnError) as e:
+        B.plan_create([(good, FAKE, FAKE)], p)  # state aliases its ghost source
+    assert e.value.status == B.ERR_INVALID_ARG
+    with pytest.raises(B.BssnError) as e:
+        B.plan_create([(good, FAKE + 8, FAKE * 2)], p)  # misaligned
+    assert e.value.status == B.ERR_INVALID_ARG
+    with pytest.raises(B.BssnError) as e:
+        B.plan_create([(good, FAKE, FAKE * 2)], p, prec=5)
+    assert e.value.status == B.ERR_INVALID_ARG
+    assert L.bssn_plan_destroy(None) == B.ERR_INVALID_ARG
