@@ -281,6 +281,51 @@ def run_gpu(args):
         return dict(state=state, ms=ms, stage_ms=float(np.mean(stage_ms)), launches=launches[0], l2=l2,
                     clocks=clk.summary() if clk else None)
 
+    def run_batched(prec):
+        """192 seeded uneven patches (sides 16..96, 4 ratio-2 levels around the
+        punctures, 4 ghosts, tricubic Brill-Lindquist fill), 4th order, one
+        graph launch per RK4 step over all patches."""
+        patches = inputs.patch_tree()
+        pb = B.make_params(fd_order=4, ko_eps=0.1, lapse=0, shift=0, eta=2.0)
+        blocks = []
+        for q in patches:
+            gq = B.make_grid(*q["n"], ghost=4, dx=q["h"])
+            w = torch.from_numpy(inputs.bl_conformal_tricubic(q["n"], 4, q["h"], q["origin"])).to(dev)
+            st = B.alloc_state(gq, device=dev)
+            v4 = B.view4(st, gq)
+            v4[inputs.IDX["W"]] = w
+            v4[inputs.IDX["alpha"]] = w
+            for i in range(3):
+                v4[inputs.IDX["gt11"] + inputs.SYM[i][i]] = 1.0
+            blocks.append((gq, st, st.clone()))
+        dtb = 0.25 * min(q["h"] for q in patches)
+        t_tune = time.perf_counter()
+        plan = B.plan_create(blocks, pb, prec, 1)
+        t_tune = time.perf_counter() - t_tune
+        try:
+            pts, tiles, shapes = B.plan_info(plan, len(blocks))
+            for _ in range(args.warmup):
+                B.batch_step(plan, dtb)
+            torch.cuda.synchronize()
+            barrier(world)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                B.batch_step(plan, dtb)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        finally:
+            B.plan_destroy(plan)
+        del blocks
+        torch.cuda.empty_cache()
+        return {"value": world * pts * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
+                "patches": len(patches), "interior_points": int(pts), "tiles": int(tiles),
+                "tile_shapes_chosen": np.bincount(shapes, minlength=7).tolist(), "plan_create_s": t_tune,
+                "fd_order": 4, "dt": dtb, "graph_launches_per_step": 1,
+                "kernel_nodes_per_step": 13 if prec == B.FP64 else 17}
+
     f64 = run_form(B.FP64, not args.profile)
     f32 = run_form(B.FP32_RHS, False)
     if args.profile:
@@ -289,6 +334,10 @@ def run_gpu(args):
             print(json.dumps({"profile_grid": n, "fp64_stage_ms": f64["stage_ms"], "fp32_stage_ms": f32["stage_ms"]}))
         return
     err32 = tensor_rel_err(B.download(f32["state"], grid), B.download(f64["state"], grid), G)
+    batched = {}
+    if not args.no_batched:
+        batched["batched_fp64"] = run_batched(B.FP64)
+        batched["batched_fp32_rhs"] = run_batched(B.FP32_RHS)
 
     # end to end through the public API with host buffers (pinned): upload the
     # step's input state, one RK4 step (bssn_rk4_step), read the result back
@@ -355,6 +404,7 @@ def run_gpu(args):
                          "err_vs_fp64_per_var": [float(x) for x in err32],
                          "ham_l2_after": float(f32["l2"][0]), "gpu_launches": f32["launches"],
                          "steps": args.steps + args.warmup},
+            **batched,
         },
         "fp_rates_measured": rates,
     }
@@ -369,6 +419,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--grid", type=int, default=N, help="interior points per axis (profiling: smaller cases)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 192-patch batched workload")
     ap.add_argument("--profile", action="store_true",
                     help="only the FP64 and FP32 timed loops (no probe, e2e, CPU leg): for ncu captures")
     args = ap.parse_args()
