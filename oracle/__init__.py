@@ -48,6 +48,12 @@ def lib():
         L.oracle_constraints.restype = _i
         L.oracle_flop_counts.argtypes = [_i, _p]
         L.oracle_flop_counts.restype = _i
+        L.oracle_conv3d_fwd.argtypes = [_i, _i, _i, _i, _i, _i, _p, _p, _p, _p]
+        L.oracle_conv3d_bwd.argtypes = [_i, _i, _i, _i, _i, _i, _p, _p, _p, _p, _p, _p]
+        L.oracle_gelu.argtypes = [_ll, _p, _p]
+        L.oracle_gelu_grad.argtypes = [_ll, _p, _p]
+        L.oracle_corrector_loss.argtypes = [_i, _i, _i, _i, _i, _p, _p, _p, _p, _p, _p]
+        L.oracle_corrector_loss.restype = _d
         _L = L
     return _L
 
@@ -207,3 +213,57 @@ def flop_counts(fd_order):
     keys = ["first", "second", "mixed_tensor", "upwind_dir", "ko_var", "rhs_algebra", "gather_rhs",
             "constraints_algebra"]
     return dict(zip(keys, (int(x) for x in out)))
+
+
+# ------------------------------------------------------------------ corrector network (corrector_oracle.cpp)
+def conv3d_fwd(x, W, b):
+    """x: (S, Z, Y, X, Ci); W: (27, Co, Ci), tap (dz+1)*9+(dy+1)*3+(dx+1); b: (Co,).
+    Zero padding. Returns (S, Z, Y, X, Co)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    b = None if b is None else np.ascontiguousarray(b, dtype=np.float64)
+    S, Z, Y, X, Ci = x.shape
+    Co = W.shape[1]
+    out = np.zeros((S, Z, Y, X, Co))
+    lib().oracle_conv3d_fwd(S, Z, Y, X, Ci, Co, _ptr(x), _ptr(W), _ptr(b), _ptr(out))
+    return out
+
+
+def conv3d_bwd(x, W, dout):
+    """Gradients (dx, dW, db) of conv3d_fwd for upstream gradient dout."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    dout = np.ascontiguousarray(dout, dtype=np.float64)
+    S, Z, Y, X, Ci = x.shape
+    Co = W.shape[1]
+    dx = np.zeros_like(x)
+    dW = np.zeros_like(W)
+    db = np.zeros(Co)
+    lib().oracle_conv3d_bwd(S, Z, Y, X, Ci, Co, _ptr(x), _ptr(W), _ptr(dout), _ptr(dx), _ptr(dW), _ptr(db))
+    return dx, dW, db
+
+
+def gelu(x, grad=False):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros_like(x)
+    (lib().oracle_gelu_grad if grad else lib().oracle_gelu)(x.size, _ptr(x), _ptr(y))
+    return y
+
+
+def corrector_loss(params, channels, x, target, want_grad=True):
+    """Loss (and gradient, packed like params, and output) of the conv+GELU
+    network with the given channel list on x (S, Z, Y, X, ch[0])."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    target = np.ascontiguousarray(target, dtype=np.float64)
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    ch = np.ascontiguousarray(channels, dtype=np.int32)
+    S, Z, Y, X, _ = x.shape
+    out = np.zeros((S, Z, Y, X, channels[-1]))
+    grad = np.zeros_like(params) if want_grad else None
+    loss = lib().oracle_corrector_loss(S, Z, Y, X, len(channels) - 1, ch.ctypes.data_as(ctypes.c_void_p),
+                                       _ptr(params), _ptr(x), _ptr(target), _ptr(out), _ptr(grad))
+    return loss, grad, out
+
+
+def corrector_param_count(channels):
+    return sum(27 * channels[l + 1] * channels[l] + channels[l + 1] for l in range(len(channels) - 1))

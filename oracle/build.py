@@ -7,15 +7,15 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "bssn_oracle.cpp")
+SRCS = [os.path.join(HERE, "bssn_oracle.cpp"), os.path.join(HERE, "corrector_oracle.cpp")]
 LIB = os.path.join(HERE, "liboracle.so")
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+    if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(s) for s in SRCS):
         return LIB
     cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-           "-o", LIB + ".tmp", SRC]
+           "-o", LIB + ".tmp", *SRCS]
     if verbose:
         print(" ".join(cmd))
     subprocess.run(cmd, check=True)
