@@ -231,6 +231,57 @@ bssn_status_t bssn_plan_info(const bssn_plan_t* plan, long long* points, long lo
 /* Frees everything the plan owns (synchronizes the device). */
 bssn_status_t bssn_plan_destroy(bssn_plan_t* plan);
 
+/* ---------------------------------------------------------------- learned corrector
+ * A 3D convolutional network that corrects a coarse-grid RK4 step towards
+ * the restricted fine-grid step: 5 layers of 3x3x3 convolutions, channels
+ * 24 -> 32 -> 32 -> 32 -> 32 -> 24, GELU (exact, erf form) after the first
+ * four, zero padding; input channel v = (u_v - in_offset_v) * in_scale_v of
+ * the coarse-step state, output channel v = (target_v - u_v) * out_scale_v.
+ * BF16 operands with FP32 accumulation on the tcgen05 tensor cores (forward,
+ * input gradient and weight gradient), FP32 master weights and Adam. The
+ * paper has no learned component; this is the build's extension (4).
+ * Parameters are packed per layer as W[27][32 co][32 ci] then b[32] (FP32),
+ * tap t = (dz+1)*9 + (dy+1)*3 + (dx+1), padded channels zero. */
+typedef struct bssn_corrector bssn_corrector_t;
+
+/* Network for grids of n^3 interior points (n = 32, 64 or 128; training needs
+ * n = 64) and batches of up to max_batch samples; weights initialised from
+ * seed (uniform +-sqrt(6/fan_in), last layer x0.1, biases 0), scales 0/1/1.
+ * Allocates all its buffers. Synchronizes. */
+bssn_status_t bssn_corrector_create(bssn_corrector_t** out, int n, int max_batch, unsigned long long seed);
+bssn_status_t bssn_corrector_destroy(bssn_corrector_t* c);
+/* Number of FP32 parameters in the packed layout (5 x (27*32*32 + 32)). */
+long long bssn_corrector_param_count(void);
+/* Copy the FP32 parameters from (write = 0) or to (write = 1) the HOST array. */
+bssn_status_t bssn_corrector_params(bssn_corrector_t* c, float* host, int write);
+/* Copy layer `layer`'s (0..4) pre-activation output of the last forward pass,
+ * S samples, to out (DEVICE FP32 [S][n^3][32]). Synchronizes. */
+bssn_status_t bssn_corrector_layer_output(bssn_corrector_t* c, int layer, int S, float* out);
+/* Copy the gradient of the last loss evaluation to the HOST array (packed). */
+bssn_status_t bssn_corrector_grads(bssn_corrector_t* c, float* host);
+/* HOST arrays of 24: input offset, input scale (> 0), output scale (> 0). */
+bssn_status_t bssn_corrector_set_scales(bssn_corrector_t* c, const double* in_offset, const double* in_scale,
+                                        const double* out_scale);
+/* Network output for S samples of raw input x (DEVICE, BF16 bits,
+ * [S][n][n][n][32] channels last): out (DEVICE FP32 [S][n^3][32]).
+ * Returns BSSN_ERR_TIMEOUT if a bounded device wait gave up. Synchronizes. */
+bssn_status_t bssn_corrector_forward_raw(bssn_corrector_t* c, int S, const void* x_bf16, float* out, void* stream);
+/* Mean squared error over the first 24 output channels against target
+ * (DEVICE FP32 [S][n^3][32]) and its gradient (read with
+ * bssn_corrector_grads); *loss is a HOST double. Synchronizes. */
+bssn_status_t bssn_corrector_loss_grad_raw(bssn_corrector_t* c, int S, const void* x_bf16, const float* target,
+                                           double* loss, void* stream);
+/* One Adam step (lr; beta 0.9/0.999) on S training pairs given as HOST
+ * arrays of DEVICE state pointers (layout of grid, n^3 interior points):
+ * coarse[i] = the coarse RK4 step's result, target[i] = the restricted fine
+ * result. *loss (HOST) receives the loss before the step. Synchronizes. */
+bssn_status_t bssn_corrector_train_step(bssn_corrector_t* c, const bssn_grid_t* grid, int S,
+                                        const double* const* coarse, const double* const* target, float lr,
+                                        double* loss, void* stream);
+/* state += network correction of state (DEVICE, layout of grid), interior
+ * points. Synchronizes. */
+bssn_status_t bssn_corrector_apply(bssn_corrector_t* c, const bssn_grid_t* grid, double* state, void* stream);
+
 /* Constraints at interior points (always double precision):
  *   H   = R + 2/3 K^2 - At_ij At^ij                      (Hamiltonian)
  *   M_i = gt^jk D_k At_ij - 3/W At_i^j d_j W - 2/3 d_i K  (momentum)

@@ -223,6 +223,98 @@ def plan_destroy(plan):
     _check(_plan_lib().bssn_plan_destroy(plan), "plan_destroy")
 
 
+def _corr_lib():
+    L = lib()
+    if not getattr(L, "_corr_typed", False):
+        vp = ctypes.c_void_p
+        L.bssn_corrector_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong]
+        L.bssn_corrector_destroy.argtypes = [vp]
+        L.bssn_corrector_param_count.restype = ctypes.c_longlong
+        L.bssn_corrector_params.argtypes = [vp, vp, ctypes.c_int]
+        L.bssn_corrector_grads.argtypes = [vp, vp]
+        L.bssn_corrector_set_scales.argtypes = [vp, vp, vp, vp]
+        L.bssn_corrector_forward_raw.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+        L.bssn_corrector_loss_grad_raw.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.POINTER(ctypes.c_double), vp]
+        L.bssn_corrector_train_step.argtypes = [vp, ctypes.POINTER(Grid), ctypes.c_int, vp, vp, ctypes.c_float,
+                                                ctypes.POINTER(ctypes.c_double), vp]
+        L.bssn_corrector_apply.argtypes = [vp, ctypes.POINTER(Grid), vp, vp]
+        L.bssn_corrector_layer_output.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
+        for n in ("bssn_corrector_create", "bssn_corrector_destroy", "bssn_corrector_params", "bssn_corrector_grads",
+                  "bssn_corrector_set_scales", "bssn_corrector_forward_raw", "bssn_corrector_loss_grad_raw",
+                  "bssn_corrector_train_step", "bssn_corrector_apply", "bssn_corrector_layer_output"):
+            getattr(L, n).restype = ctypes.c_int
+        L._corr_typed = True
+    return L
+
+
+def corrector_create(n, max_batch, seed=0):
+    h = ctypes.c_void_p()
+    _check(_corr_lib().bssn_corrector_create(ctypes.byref(h), n, max_batch, seed), "corrector_create")
+    return h.value
+
+
+def corrector_destroy(c):
+    _check(_corr_lib().bssn_corrector_destroy(c), "corrector_destroy")
+
+
+def corrector_param_count():
+    return int(_corr_lib().bssn_corrector_param_count())
+
+
+def corrector_params(c, values=None):
+    """Read (values None) or write the packed FP32 parameters."""
+    n = corrector_param_count()
+    if values is None:
+        out = np.zeros(n, dtype=np.float32)
+        _check(_corr_lib().bssn_corrector_params(c, out.ctypes.data_as(_p), 0), "corrector_params")
+        return out
+    v = np.ascontiguousarray(values, dtype=np.float32)
+    assert v.size == n
+    _check(_corr_lib().bssn_corrector_params(c, v.ctypes.data_as(_p), 1), "corrector_params")
+
+
+def corrector_grads(c):
+    out = np.zeros(corrector_param_count(), dtype=np.float32)
+    _check(_corr_lib().bssn_corrector_grads(c, out.ctypes.data_as(_p)), "corrector_grads")
+    return out
+
+
+def corrector_set_scales(c, in_offset, in_scale, out_scale):
+    a = [np.ascontiguousarray(x, dtype=np.float64) for x in (in_offset, in_scale, out_scale)]
+    _check(_corr_lib().bssn_corrector_set_scales(c, *[x.ctypes.data_as(_p) for x in a]), "corrector_set_scales")
+
+
+def corrector_forward_raw(c, S, x_bf16, out, stream=None):
+    _check(_corr_lib().bssn_corrector_forward_raw(c, S, _ptr(x_bf16), _ptr(out), _stream(stream)),
+           "corrector_forward_raw")
+
+
+def corrector_loss_grad_raw(c, S, x_bf16, target, stream=None):
+    loss = ctypes.c_double()
+    _check(_corr_lib().bssn_corrector_loss_grad_raw(c, S, _ptr(x_bf16), _ptr(target), ctypes.byref(loss),
+                                                    _stream(stream)), "corrector_loss_grad_raw")
+    return loss.value
+
+
+def corrector_train_step(c, grid, coarse, target, lr, stream=None):
+    """coarse, target: lists of device state tensors (same length S)."""
+    S = len(coarse)
+    ca = (ctypes.c_void_p * S)(*[_ptr(x) for x in coarse])
+    ta = (ctypes.c_void_p * S)(*[_ptr(x) for x in target])
+    loss = ctypes.c_double()
+    _check(_corr_lib().bssn_corrector_train_step(c, ctypes.byref(grid), S, ca, ta, lr, ctypes.byref(loss),
+                                                 _stream(stream)), "corrector_train_step")
+    return loss.value
+
+
+def corrector_apply(c, grid, state, stream=None):
+    _check(_corr_lib().bssn_corrector_apply(c, ctypes.byref(grid), _ptr(state), _stream(stream)), "corrector_apply")
+
+
+def corrector_layer_output(c, layer, S, out):
+    _check(_corr_lib().bssn_corrector_layer_output(c, layer, S, _ptr(out)), "corrector_layer_output")
+
+
 def rk4_step(grid, params, prec, dt, bc, ghost_src, state, bufs, work, stream=None):
     _check(lib().bssn_rk4_step(ctypes.byref(grid), ctypes.byref(params), prec, dt, bc, _ptr(ghost_src), _ptr(state),
                                _ptr(bufs), _ptr(work), _nbytes(work), _stream(stream)), "rk4_step")

@@ -21,6 +21,7 @@ UNITS = [
     ("bssn_order.cu", "bssn_order8.o", ["-DBSSN_ORDER=8"]),
     ("bssn_noalloc.cu", "bssn_noalloc.o", []),
     ("bssn_batch.cu", "bssn_batch.o", []),
+    ("bssn_corrector.cu", "bssn_corrector.o", []),
 ]
 
 
