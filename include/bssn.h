@@ -231,6 +231,26 @@ bssn_status_t bssn_plan_info(const bssn_plan_t* plan, long long* points, long lo
 /* Frees everything the plan owns (synchronizes the device). */
 bssn_status_t bssn_plan_destroy(bssn_plan_t* plan);
 
+/* ---------------------------------------------------------------- 2:1 transfer
+ * Between a coarse grid and one refined by 2 in every direction (fine n =
+ * 2 x coarse n on each axis, same physical box; cell centred), all 24
+ * variables, interior points only (ratio-2 levels, Sec. 4's planned AMR).
+ * bssn_restrict: order 2: coarse(i,j,k) = mean of fine (2i+a, 2j+b, 2k+c),
+ *   a,b,c in {0,1} (second order); order 4: tricubic Lagrange interpolation
+ *   at the coarse centre, halfway between fine 2i and 2i+1 (1D weights
+ *   (-1,9,9,-1)/16 on fine 2i-1..2i+2; needs fine ghost >= 1, filled). Other
+ *   orders: BSSN_ERR_INVALID_ARG. The order-4 form keeps restriction after
+ *   prolongation exact on tricubics, so a coarse -> fine -> coarse round trip
+ *   adds only fourth-order error.
+ * bssn_prolong: tricubic Lagrange interpolation through coarse cell centres
+ *   (1D weights (-5,35,105,-7)/128 on coarse i-2..i+1 for fine cell 2i and
+ *   (-7,105,35,-5)/128 on i-1..i+2 for 2i+1); needs coarse ghost >= 2 with
+ *   the ghosts filled. Both asynchronous; the two states must not overlap. */
+bssn_status_t bssn_restrict(const bssn_grid_t* fine, const double* fine_state, const bssn_grid_t* coarse,
+                            double* coarse_state, int order, void* stream);
+bssn_status_t bssn_prolong(const bssn_grid_t* coarse, const double* coarse_state, const bssn_grid_t* fine,
+                           double* fine_state, void* stream);
+
 /* ---------------------------------------------------------------- learned corrector
  * A 3D convolutional network that corrects a coarse-grid RK4 step towards
  * the restricted fine-grid step: 5 layers of 3x3x3 convolutions, channels
@@ -278,6 +298,18 @@ bssn_status_t bssn_corrector_loss_grad_raw(bssn_corrector_t* c, int S, const voi
 bssn_status_t bssn_corrector_train_step(bssn_corrector_t* c, const bssn_grid_t* grid, int S,
                                         const double* const* coarse, const double* const* target, float lr,
                                         double* loss, void* stream);
+/* Pack one training pair for bssn_corrector_train_step_raw: x_bf16 (DEVICE,
+ * [n^3][32] BF16) = the network input of coarse; t_bf16 (DEVICE, same shape,
+ * nullable together with target) = the normalised correction (target -
+ * coarse) * out_scale. Uses the scales set at the time of the call.
+ * Asynchronous. */
+bssn_status_t bssn_corrector_pack(bssn_corrector_t* c, const bssn_grid_t* grid, const double* coarse,
+                                  const double* target, void* x_bf16, void* t_bf16, void* stream);
+/* One Adam step on S packed pairs (HOST arrays of DEVICE pointers made by
+ * bssn_corrector_pack); *loss (HOST) is the loss before the step.
+ * Synchronizes. */
+bssn_status_t bssn_corrector_train_step_raw(bssn_corrector_t* c, int S, const void* const* x_bf16,
+                                            const void* const* t_bf16, float lr, double* loss, void* stream);
 /* state += network correction of state (DEVICE, layout of grid), interior
  * points. Synchronizes. */
 bssn_status_t bssn_corrector_apply(bssn_corrector_t* c, const bssn_grid_t* grid, double* state, void* stream);

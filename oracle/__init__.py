@@ -48,6 +48,10 @@ def lib():
         L.oracle_constraints.restype = _i
         L.oracle_flop_counts.argtypes = [_i, _p]
         L.oracle_flop_counts.restype = _i
+        L.oracle_restrict.argtypes = [_i, _i, _i, _i, _ll, _i, _i, _i, _i, _ll, _i, _p, _p]
+        L.oracle_restrict.restype = _i
+        L.oracle_prolong.argtypes = [_i, _i, _i, _i, _ll, _i, _i, _i, _i, _ll, _p, _p]
+        L.oracle_prolong.restype = _i
         L.oracle_conv3d_fwd.argtypes = [_i, _i, _i, _i, _i, _i, _p, _p, _p, _p]
         L.oracle_conv3d_bwd.argtypes = [_i, _i, _i, _i, _i, _i, _p, _p, _p, _p, _p, _p]
         L.oracle_gelu.argtypes = [_ll, _p, _p]
@@ -213,6 +217,33 @@ def flop_counts(fd_order):
     keys = ["first", "second", "mixed_tensor", "upwind_dir", "ko_var", "rhs_algebra", "gather_rhs",
             "constraints_algebra"]
     return dict(zip(keys, (int(x) for x in out)))
+
+
+# ------------------------------------------------------------------ 2:1 transfer
+def restrict(f, fg, cg, order=4):
+    """Fine state (24, 2nz+2fg, 2ny+2fg, 2nx+2fg) -> coarse (24, nz+2cg, ...),
+    interior only (coarse ghosts zero). order 2: mean of the 8 fine children;
+    order 4: tricubic interpolation at the coarse centre (fine ghosts >= 1,
+    filled)."""
+    fnx, fny, fnz, fvs = _check_state(f, fg)
+    cnx, cny, cnz = fnx // 2, fny // 2, fnz // 2
+    c = np.zeros((24, cnz + 2 * cg, cny + 2 * cg, cnx + 2 * cg))
+    rc = lib().oracle_restrict(fnx, fny, fnz, fg, fvs, cnx, cny, cnz, cg, int(np.prod(c.shape[1:])), order, _ptr(f),
+                               _ptr(c))
+    if rc != 0:
+        raise ValueError("oracle_restrict: invalid arguments")
+    return c
+
+
+def prolong(c, cg, fg):
+    """Coarse state (ghosts >= 2 filled) -> fine interior (fine ghosts zero)."""
+    cnx, cny, cnz, cvs = _check_state(c, cg)
+    f = np.zeros((24, 2 * cnz + 2 * fg, 2 * cny + 2 * fg, 2 * cnx + 2 * fg))
+    rc = lib().oracle_prolong(cnx, cny, cnz, cg, cvs, 2 * cnx, 2 * cny, 2 * cnz, fg, int(np.prod(f.shape[1:])),
+                              _ptr(c), _ptr(f))
+    if rc != 0:
+        raise ValueError("oracle_prolong: invalid arguments")
+    return f
 
 
 # ------------------------------------------------------------------ corrector network (corrector_oracle.cpp)

@@ -757,6 +757,95 @@ void fill_ghosts(const Grid& G, int mode, const double* src, double* U) {
 // ======================================================================= C API
 extern "C" {
 
+// 2:1 restriction (cell-centred), every variable, interior points. The
+// centre of coarse cell i lies halfway between fine centres 2i and 2i+1.
+//   order 2: coarse (i,j,k) = mean of the 8 fine cells (2i+a, 2j+b, 2k+c)
+//   order 4: the tricubic Lagrange interpolant through the 4 x 4 x 4 fine
+//            centres 2i-1 .. 2i+2 (per axis) evaluated at the coarse centre;
+//            needs fine ghosts >= 1, filled.
+int oracle_restrict(int fnx, int fny, int fnz, int fg, long long fvs, int cnx, int cny, int cnz, int cg,
+                    long long cvs, int order, const double* f, double* c) {
+  if (fnx != 2 * cnx || fny != 2 * cny || fnz != 2 * cnz) return -1;
+  if (order != 2 && order != 4) return -1;
+  if (order == 4 && fg < 1) return -1;
+  Grid F = make_grid(fnx, fny, fnz, fg, 1, 1, 1, fvs);
+  Grid C = make_grid(cnx, cny, cnz, cg, 1, 1, 1, cvs);
+  // 1D nodes (fine offsets from 2i) and weights
+  const int n = order == 2 ? 2 : 4;
+  const int first = order == 2 ? 0 : -1;
+  double w[4];
+  for (int j = 0; j < n; ++j) {
+    if (order == 2) {
+      w[j] = 0.5;
+      continue;
+    }
+    const double x = 0.5;  // coarse centre in fine units from 2i
+    double num = 1.0, den = 1.0;
+    for (int m = 0; m < n; ++m) {
+      if (m == j) continue;
+      num *= x - (first + m);
+      den *= (double)(j - m);
+    }
+    w[j] = num / den;
+  }
+  for (int v = 0; v < NVAR; ++v)
+    for (int k = 0; k < cnz; ++k)
+      for (int j = 0; j < cny; ++j)
+        for (int i = 0; i < cnx; ++i) {
+          double s = 0.0;
+          for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b)
+              for (int d = 0; d < n; ++d)
+                s += w[a] * w[b] * w[d] *
+                     f[v * fvs + F.idx(2 * i + first + d, 2 * j + first + b, 2 * k + first + a)];
+          c[v * cvs + C.idx(i, j, k)] = s;
+        }
+  return 0;
+}
+
+// 2:1 prolongation (cell-centred): fine cell I lies at coarse coordinate
+// I/2 - 1/4 (in coarse cells, centre of coarse cell i at i); its value is the
+// tricubic Lagrange interpolant through the 4 x 4 x 4 nearest coarse centres
+// (the 4 nearest along each axis). Needs coarse ghosts >= 2, filled.
+int oracle_prolong(int cnx, int cny, int cnz, int cg, long long cvs, int fnx, int fny, int fnz, int fg,
+                   long long fvs, const double* c, double* f) {
+  if (fnx != 2 * cnx || fny != 2 * cny || fnz != 2 * cnz || cg < 2) return -1;
+  Grid C = make_grid(cnx, cny, cnz, cg, 1, 1, 1, cvs);
+  Grid F = make_grid(fnx, fny, fnz, fg, 1, 1, 1, fvs);
+  // 1D: nodes i0..i0+3 and Lagrange weights for fine index I
+  auto weights = [](int I, int* i0, double w[4]) {
+    const double x = 0.5 * I - 0.25;           // coarse coordinate of the fine centre
+    const int base = (I % 2 == 0) ? I / 2 - 2 : I / 2 - 1;  // the 4 nearest coarse centres
+    *i0 = base;
+    for (int j = 0; j < 4; ++j) {
+      double num = 1.0, den = 1.0;
+      for (int m = 0; m < 4; ++m) {
+        if (m == j) continue;
+        num *= x - (base + m);
+        den *= (double)(j - m);
+      }
+      w[j] = num / den;
+    }
+  };
+  for (int K = 0; K < fnz; ++K)
+    for (int J = 0; J < fny; ++J)
+      for (int I = 0; I < fnx; ++I) {
+        int ix, iy, iz;
+        double wx[4], wy[4], wz[4];
+        weights(I, &ix, wx);
+        weights(J, &iy, wy);
+        weights(K, &iz, wz);
+        for (int v = 0; v < NVAR; ++v) {
+          double s = 0.0;
+          for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b)
+              for (int d = 0; d < 4; ++d) s += wz[a] * wy[b] * wx[d] * c[v * cvs + C.idx(ix + d, iy + b, iz + a)];
+          f[v * fvs + F.idx(I, J, K)] = s;
+        }
+      }
+  return 0;
+}
+
 // Exact finite-difference weight (num/den) of sample point j among offsets
 // o[0..n-1] for the m-th derivative at 0.
 void oracle_fd_weight(const int* o, int n, int m, int j, long long* num, long long* den) {

@@ -307,6 +307,61 @@ def corrector_train_step(c, grid, coarse, target, lr, stream=None):
     return loss.value
 
 
+def _pack_lib():
+    L = _corr_lib()
+    if not getattr(L, "_pack_typed", False):
+        L.bssn_corrector_pack.argtypes = [_p, ctypes.POINTER(Grid), _p, _p, _p, _p, _p]
+        L.bssn_corrector_pack.restype = ctypes.c_int
+        L.bssn_corrector_train_step_raw.argtypes = [_p, ctypes.c_int, _p, _p, ctypes.c_float,
+                                                    ctypes.POINTER(ctypes.c_double), _p]
+        L.bssn_corrector_train_step_raw.restype = ctypes.c_int
+        L._pack_typed = True
+    return L
+
+
+def corrector_pack(c, grid, coarse, target, x_bf16, t_bf16, stream=None):
+    _check(_pack_lib().bssn_corrector_pack(c, ctypes.byref(grid), _ptr(coarse), _ptr(target), _ptr(x_bf16),
+                                           _ptr(t_bf16), _stream(stream)), "corrector_pack")
+
+
+def corrector_train_step_raw(c, xs, ts, lr, stream=None):
+    """xs, ts: lists of packed BF16 device tensors (same length S)."""
+    L = _pack_lib()
+    S = len(xs)
+    xa = (ctypes.c_void_p * S)(*[_ptr(x) for x in xs])
+    ta = (ctypes.c_void_p * S)(*[_ptr(t) for t in ts])
+    loss = ctypes.c_double()
+    _check(L.bssn_corrector_train_step_raw(c, S, xa, ta, lr, ctypes.byref(loss), _stream(stream)),
+           "corrector_train_step_raw")
+    return loss.value
+
+
+def _transfer_lib():
+    L = lib()
+    if not getattr(L, "_transfer_typed", False):
+        L.bssn_restrict.argtypes = [ctypes.POINTER(Grid), _p, ctypes.POINTER(Grid), _p, ctypes.c_int, _p]
+        L.bssn_prolong.argtypes = [ctypes.POINTER(Grid), _p, ctypes.POINTER(Grid), _p, _p]
+        for n in ("bssn_restrict", "bssn_prolong"):
+            getattr(L, n).restype = ctypes.c_int
+        L._transfer_typed = True
+    return L
+
+
+def restrict(fine_grid, fine_state, coarse_grid, coarse_state, order=4, stream=None):
+    """2:1 restriction of the fine state into the coarse interior: order 2 is
+    the mean of the 8 children, order 4 tricubic interpolation at the coarse
+    centre (fine ghosts >= 1, filled)."""
+    _check(_transfer_lib().bssn_restrict(ctypes.byref(fine_grid), _ptr(fine_state), ctypes.byref(coarse_grid),
+                                         _ptr(coarse_state), order, _stream(stream)), "restrict")
+
+
+def prolong(coarse_grid, coarse_state, fine_grid, fine_state, stream=None):
+    """Tricubic 1:2 prolongation of the coarse state (ghosts filled, ghost >= 2)
+    onto the fine interior."""
+    _check(_transfer_lib().bssn_prolong(ctypes.byref(coarse_grid), _ptr(coarse_state), ctypes.byref(fine_grid),
+                                        _ptr(fine_state), _stream(stream)), "prolong")
+
+
 def corrector_apply(c, grid, state, stream=None):
     _check(_corr_lib().bssn_corrector_apply(c, ctypes.byref(grid), _ptr(state), _stream(stream)), "corrector_apply")
 

@@ -22,6 +22,7 @@ UNITS = [
     ("bssn_noalloc.cu", "bssn_noalloc.o", []),
     ("bssn_batch.cu", "bssn_batch.o", []),
     ("bssn_corrector.cu", "bssn_corrector.o", []),
+    ("bssn_transfer.cu", "bssn_transfer.o", []),
 ]
 
 

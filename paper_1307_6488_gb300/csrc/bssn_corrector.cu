@@ -42,7 +42,7 @@ constexpr int CH = 32;
 constexpr int NL = 5;
 constexpr int NTAP = 27;
 constexpr int BM = 128;
-constexpr int STAGES = 4;
+constexpr int STAGES = 6;  // 2 CTAs (about 104 KB each) per SM
 constexpr int A_BYTES = BM * CH * 2;      // 8 KB per A tile
 constexpr int W_TAP_BYTES = CH * CH * 2;  // 2 KB per tap
 constexpr int CONV_SMEM = 1024 + STAGES * A_BYTES + NTAP * W_TAP_BYTES + 256;
@@ -82,7 +82,7 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
 // MODE 1: d = conv(g) with the transposed, flipped weights; if zprev, d *=
 //         GELU'(zprev); act_out (BF16, padded) receives d.
 template <int MODE>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
     k_conv_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW, Geom G,
               const float* __restrict__ bias, float* __restrict__ zout, __nv_bfloat16* __restrict__ act_out,
               const float* __restrict__ zprev, int gelu, unsigned int* err) {
@@ -96,18 +96,22 @@ __global__ void __launch_bounds__(128, 1)
   uint64_t* wbar = bars + 2 * STAGES;
   uint64_t* done = wbar + 1;
   uint32_t* tslot = (uint32_t*)(done + 1);
-  __shared__ int bad;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tiles_per_plane = G.Y / G.rpt;
-  const int t = blockIdx.x;
-  const int s = t / (G.Z * tiles_per_plane);
-  const int rem = t - s * G.Z * tiles_per_plane;
-  const int z = rem / tiles_per_plane;
-  const int y0 = (rem % tiles_per_plane) * G.rpt;
+  const int ntiles = G.S * G.Z * tiles_per_plane;
+  // persistent: this CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+  const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int nsteps = my_tiles * NTAP;  // one K step per (tile, tap)
+  auto tile_pos = [&](int it, int& s, int& z, int& y0) {
+    const int t = blockIdx.x + it * gridDim.x;
+    s = t / (G.Z * tiles_per_plane);
+    const int rem = t - s * G.Z * tiles_per_plane;
+    z = rem / tiles_per_plane;
+    y0 = (rem % tiles_per_plane) * G.rpt;
+  };
 
   if (tid == 0) {
-    bad = 0;
     for (int i = 0; i < STAGES; ++i) {
       tc::mbar_init(&full[i], 1);
       tc::mbar_init(&empty[i], 1);
@@ -123,91 +127,124 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t taddr = *tslot;
   constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, 32);
 
-  if (tid == 0) {
+  // producer / MMA state (thread 0): steps loaded so far, steps consumed, failure
+  int issued = 0, consumed = 0;
+  bool fail = false;
+  auto load_step = [&](int q) {
+    int s, z, y0;
+    tile_pos(q / NTAP, s, z, y0);
+    const int k = q % NTAP;
+    const int slot = q % STAGES;
+    const int dz = k / 9 - 1, dy = (k / 3) % 3 - 1, dx = k % 3 - 1;
+    tc::mbar_expect_tx(&full[slot], A_BYTES);
+    tc::tma_load_4d(A + slot * A_BYTES, &tmA, 0, 1 + dx, y0 + 1 + dy, s * (G.Z + 2) + z + 1 + dz, &full[slot]);
+  };
+  // wait (bounded) for every A load still in flight before giving up
+  auto drain = [&]() {
+    for (int q = consumed; q < issued; ++q) (void)tc::mbar_wait(&full[q % STAGES], (q / STAGES) & 1, 100000000ull);
+  };
+  if (tid == 0 && nsteps > 0) {
     tc::mbar_expect_tx(wbar, NTAP * W_TAP_BYTES);
     for (int k = 0; k < NTAP; ++k) tc::tma_load_2d(Wt + k * W_TAP_BYTES, &tmW, 0, k * CH, wbar);
-    auto load_a = [&](int k) {
-      const int slot = k % STAGES;
-      const int dz = k / 9 - 1, dy = (k / 3) % 3 - 1, dx = k % 3 - 1;
-      tc::mbar_expect_tx(&full[slot], A_BYTES);
-      tc::tma_load_4d(A + slot * A_BYTES, &tmA, 0, 1 + dx, y0 + 1 + dy, s * (G.Z + 2) + z + 1 + dz, &full[slot]);
-    };
-    for (int k = 0; k < STAGES; ++k) load_a(k);
-    bool ok = tc::mbar_wait(wbar, 0);
-    int pending_from = STAGES;  // loads issued: taps [0, pending_from)
-    for (int k = 0; k < NTAP && ok; ++k) {
-      const int slot = k % STAGES;
-      const uint32_t ph = (k / STAGES) & 1;
-      if (!tc::mbar_wait(&full[slot], ph)) { ok = false; break; }
-      tc::fence_after_sync();
-      const uint64_t ad = tc::smem_desc(tc::smem_u32(A + slot * A_BYTES), 16, 512, tc::SWZ_64B);
-      const uint64_t bd = tc::smem_desc(tc::smem_u32(Wt + k * W_TAP_BYTES), 16, 512, tc::SWZ_64B);
-#pragma unroll
-      for (int j = 0; j < 2; ++j) tc::mma_bf16(taddr, ad + 2 * j, bd + 2 * j, IDESC, (k > 0 || j > 0) ? 1u : 0u);
-      tc::mma_commit(&empty[slot]);
-      if (k + STAGES < NTAP) {
-        if (!tc::mbar_wait(&empty[slot], ph)) { ok = false; break; }
-        load_a(k + STAGES);
-        pending_from = k + STAGES + 1;
-      }
-    }
-    if (!ok) {
-      bad = 1;
+    for (; issued < STAGES && issued < nsteps; ++issued) load_step(issued);
+    if (!tc::mbar_wait(wbar, 0)) {
+      fail = true;
       atomicOr(err, 1u);
-      // let copies already in flight land before the CTA leaves
-      for (int k = pending_from - STAGES; k < pending_from; ++k)
-        if (k >= 0) (void)tc::mbar_wait(&full[k % STAGES], (k / STAGES) & 1, 100000000ull);
+      drain();
     }
-    tc::mma_commit(done);
   }
-  __syncthreads();
-  const int bad0 = bad;
-  bool ok = !bad0 && tc::mbar_wait(done, 0);
-  if (!ok && !bad0) atomicOr(err, 2u);
-  ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
-  tc::fence_after_sync();
-  if (ok) {
-    float acc[32];
-    tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16), acc);
-    const int row = warp * 32 + lane;
-    const int y = y0 + row / G.X, x = row % G.X;
-    const long long pt = (((long long)s * G.Z + z) * G.Y + y) * G.X + x;
-    const long long pp = padded_index(G, s, z, y, x);
-    if (MODE == 0) {
+
+  for (int it = 0; it < my_tiles; ++it) {
+    if (tid == 0 && !fail) {
+      for (int k = 0; k < NTAP && !fail; ++k) {
+        const int q = it * NTAP + k;
+        const int slot = q % STAGES;
+        if (!tc::mbar_wait(&full[slot], (q / STAGES) & 1)) {
+          fail = true;
+          break;
+        }
+        consumed = q + 1;
+        tc::fence_after_sync();
+        const uint64_t ad = tc::smem_desc(tc::smem_u32(A + slot * A_BYTES), 16, 512, tc::SWZ_64B);
+        const uint64_t bd = tc::smem_desc(tc::smem_u32(Wt + k * W_TAP_BYTES), 16, 512, tc::SWZ_64B);
 #pragma unroll
-      for (int c = 0; c < 32; ++c) acc[c] += __ldg(bias + c);
-      if (zout) {
-        float4* zo = (float4*)(zout + pt * CH);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        for (int j = 0; j < 2; ++j) tc::mma_bf16(taddr, ad + 2 * j, bd + 2 * j, IDESC, (k > 0 || j > 0) ? 1u : 0u);
+        tc::mma_commit(&empty[slot]);
+        // refill the slot of the previous step once its MMAs are done; the
+        // ring runs on across tiles, so the next tile's first taps are
+        // already loaded while this tile's epilogue runs
+        if (q >= 1 && issued < nsteps) {
+          const int pq = q - 1;
+          if (!tc::mbar_wait(&empty[pq % STAGES], (pq / STAGES) & 1)) {
+            fail = true;
+            break;
+          }
+          load_step(issued);
+          ++issued;
+        }
       }
-      if (act_out) {
+      tc::mma_commit(done);
+      if (fail) {
+        atomicOr(err, 1u);
+        drain();
+        (void)tc::mbar_wait(done, it & 1, 100000000ull);
+      }
+    }
+    const int any_fail = __syncthreads_or(tid == 0 && fail);
+    bool ok = !any_fail && tc::mbar_wait(done, it & 1);
+    if (!ok && !any_fail) atomicOr(err, 2u);
+    ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+    tc::fence_after_sync();
+    if (ok) {
+      int s, z, y0;
+      tile_pos(it, s, z, y0);
+      float acc[32];
+      tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16), acc);
+      const int row = warp * 32 + lane;
+      const int y = y0 + row / G.X, x = row % G.X;
+      const long long pt = (((long long)s * G.Z + z) * G.Y + y) * G.X + x;
+      const long long pp = padded_index(G, s, z, y, x);
+      if (MODE == 0) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc[c] += __ldg(bias + c);
+        if (zout) {
+          float4* zo = (float4*)(zout + pt * CH);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        }
+        if (act_out) {
+          __align__(16) __nv_bfloat16 h[32];
+#pragma unroll
+          for (int c = 0; c < 32; ++c) h[c] = __float2bfloat16_rn(gelu ? gelu_f(acc[c]) : acc[c]);
+          uint4* dst = (uint4*)(act_out + pp * CH);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) dst[q] = ((const uint4*)h)[q];
+        }
+      } else {
+        if (zprev) {
+          const float4* zp = (const float4*)(zprev + pt * CH);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 v = __ldg(zp + q);
+            acc[4 * q] *= gelu_grad_f(v.x);
+            acc[4 * q + 1] *= gelu_grad_f(v.y);
+            acc[4 * q + 2] *= gelu_grad_f(v.z);
+            acc[4 * q + 3] *= gelu_grad_f(v.w);
+          }
+        }
         __align__(16) __nv_bfloat16 h[32];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) h[c] = __float2bfloat16_rn(gelu ? gelu_f(acc[c]) : acc[c]);
+        for (int c = 0; c < 32; ++c) h[c] = __float2bfloat16_rn(acc[c]);
         uint4* dst = (uint4*)(act_out + pp * CH);
 #pragma unroll
         for (int q = 0; q < 4; ++q) dst[q] = ((const uint4*)h)[q];
       }
-    } else {
-      if (zprev) {
-        const float4* zp = (const float4*)(zprev + pt * CH);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 v = __ldg(zp + q);
-          acc[4 * q] *= gelu_grad_f(v.x);
-          acc[4 * q + 1] *= gelu_grad_f(v.y);
-          acc[4 * q + 2] *= gelu_grad_f(v.z);
-          acc[4 * q + 3] *= gelu_grad_f(v.w);
-        }
-      }
-      __align__(16) __nv_bfloat16 h[32];
-#pragma unroll
-      for (int c = 0; c < 32; ++c) h[c] = __float2bfloat16_rn(acc[c]);
-      uint4* dst = (uint4*)(act_out + pp * CH);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) dst[q] = ((const uint4*)h)[q];
     }
+    // every TMEM read of this tile is done before the next tile's first MMA
+    tc::fence_before_sync();
+    const int stop = __syncthreads_or(!ok);
+    tc::fence_after_sync();
+    if (stop) break;
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -356,26 +393,61 @@ __global__ void k_to_channels_first(Geom G, const __nv_bfloat16* __restrict__ in
 }
 
 // Bias gradient: db[c] = sum over interior points of g[c] (g padded BF16), fixed order.
-__global__ void k_bias_grad(Geom G, const __nv_bfloat16* __restrict__ g, float* __restrict__ db) {
-  const int c = blockIdx.x;  // one block per channel
-  double s = 0.0;
+// Bias gradient db[c] = sum over points of g[., c], in two deterministic
+// passes: per-block partials (each thread sums whole 32-channel rows, then the
+// warp and the block reduce), then one warp sums the BIAS_BLOCKS partials.
+constexpr int BIAS_BLOCKS = 304;
+__global__ void __launch_bounds__(256) k_bias_partial(Geom G, const __nv_bfloat16* __restrict__ g,
+                                                      double* __restrict__ part) {
+  float acc[CH];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) acc[c] = 0.f;
   const long long pts = (long long)G.S * G.Z * G.Y * G.X;
-  for (long long i = threadIdx.x; i < pts; i += blockDim.x) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < pts; i += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(i % G.X);
     const long long r = i / G.X;
     const int y = (int)(r % G.Y);
     const long long r2 = r / G.Y;
-    const int z = (int)(r2 % G.Z), s2 = (int)(r2 / G.Z);
-    s += (double)__bfloat162float(g[padded_index(G, s2, z, y, x) * CH + c]);
+    const int z = (int)(r2 % G.Z), s = (int)(r2 / G.Z);
+    const uint4* src = (const uint4*)(g + padded_index(G, s, z, y, x) * CH);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 v = __ldg(src + q);
+      const __nv_bfloat162* h = (const __nv_bfloat162*)&v;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 f = __bfloat1622float2(h[j]);
+        acc[8 * q + 2 * j] += f.x;
+        acc[8 * q + 2 * j + 1] += f.y;
+      }
+    }
   }
-  __shared__ double sh[256];
-  sh[threadIdx.x] = s;
+  __shared__ double sh[8][CH];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // warp transpose-reduce: lane c ends with the warp's sum of channel c
+  double mine = 0.0;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    double v = acc[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == c) mine = v;
+  }
+  sh[warp][lane] = mine;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
+  if (threadIdx.x < CH) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w][threadIdx.x];
+    part[blockIdx.x * CH + threadIdx.x] = t;
   }
-  if (threadIdx.x == 0) db[c] = (float)sh[0];
+}
+
+__global__ void k_bias_final(const double* __restrict__ part, int nb, float* __restrict__ db) {
+  const int c = threadIdx.x;
+  if (c >= CH) return;
+  double t = 0.0;
+  for (int b = 0; b < nb; ++b) t += part[b * CH + c];
+  db[c] = (float)t;
 }
 
 // Unpadded BF16 [pts][32] -> interior of a padded buffer.
@@ -510,6 +582,37 @@ __global__ void k_pack_target(Geom G, Layout L, int s, const double* __restrict_
   }
 }
 
+// One training pair packed into unpadded BF16 buffers: x = network input of
+// the coarse state, t = normalised correction (target - coarse) (if target).
+__global__ void k_pack_pair(Geom G, Layout L, const double* __restrict__ coarse, const double* __restrict__ target,
+                            const double* __restrict__ coef, __nv_bfloat16* __restrict__ x,
+                            __nv_bfloat16* __restrict__ t) {
+  const long long pts = (long long)G.Z * G.Y * G.X;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < pts; i += (long long)gridDim.x * blockDim.x) {
+    const int xx = (int)(i % G.X);
+    const long long r = i / G.X;
+    const int y = (int)(r % G.Y), z = (int)(r / G.Y);
+    const long long p = L.off0 + xx + y * L.sy + z * L.sz;
+    __align__(16) __nv_bfloat16 hx[32], ht[32];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const double u = c < NV ? coarse[c * L.vs + p] : 0.0;
+      hx[c] = __float2bfloat16_rn(c < NV ? (float)((u - coef[c]) * coef[NV + c]) : 0.f);
+      if (target) ht[c] = __float2bfloat16_rn(c < NV ? (float)((target[c * L.vs + p] - u) * coef[2 * NV + c]) : 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ((uint4*)(x + i * CH))[q] = ((const uint4*)hx)[q];
+    if (target)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) ((uint4*)(t + i * CH))[q] = ((const uint4*)ht)[q];
+  }
+}
+
+__global__ void k_bf16_to_f32(long long n, const __nv_bfloat16* __restrict__ in, float* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = __bfloat162float(in[i]);
+}
+
 // state += network output / out_scale (interior, sample 0).
 __global__ void k_apply(Geom G, Layout L, const float* __restrict__ out, const double* __restrict__ coef,
                         double* __restrict__ u) {
@@ -590,6 +693,7 @@ struct bssn_corrector {
   float* target = nullptr;       // unpadded FP32 targets
   float* partial = nullptr;      // wgrad partials
   double* lpart = nullptr;       // loss partials
+  double* bpart = nullptr;       // bias-gradient partials [BIAS_BLOCKS][32]
   float* params = nullptr;       // FP32 master [NL][LAYER_PARAMS]
   float* grads = nullptr;
   float* adam_m = nullptr;
@@ -599,6 +703,7 @@ struct bssn_corrector {
   double* coef = nullptr;        // in_offset[24], in_scale[24], out_scale[24]
   unsigned int* err = nullptr;
   int wg_blocks = 0, rows_per_cta = 0;
+  int conv_grid = 0;  // persistent conv grid: resident CTAs per SM x SMs
   long long adam_t = 0;
 };
 
@@ -624,14 +729,19 @@ Geom geom_for(const bssn_corrector* c, int S) {
   return G;
 }
 
+// persistent conv grid for G: every tile once, at most conv_grid CTAs
+int conv_blocks(const bssn_corrector* c, const Geom& G) {
+  const int tiles = G.S * G.Z * (G.Y / G.rpt);
+  return tiles < c->conv_grid ? tiles : c->conv_grid;
+}
+
 // one layer forward on act[l] (sample count in G) -> z[l] and act[l+1]
 cudaError_t layer_forward(bssn_corrector* c, const Geom& G, int l, float* zout, __nv_bfloat16* act_out, int gelu,
                           cudaStream_t s) {
   CUtensorMap ta, tw;
   if (!map_act(&ta, c->act[l], G) || !map_w(&tw, c->wf + (size_t)l * NTAP * CH * CH)) return cudaErrorInvalidValue;
-  const int tiles = G.S * G.Z * (G.Y / G.rpt);
-  k_conv_tc<0><<<tiles, 128, CONV_SMEM, s>>>(ta, tw, G, c->params + (size_t)l * LAYER_PARAMS + NTAP * CH * CH, zout,
-                                             act_out, nullptr, gelu, c->err);
+  const float* bias = c->params + (size_t)l * LAYER_PARAMS + NTAP * CH * CH;
+  k_conv_tc<0><<<conv_blocks(c, G), 128, CONV_SMEM, s>>>(ta, tw, G, bias, zout, act_out, nullptr, gelu, c->err);
   return cudaGetLastError();
 }
 
@@ -678,15 +788,16 @@ cudaError_t network_backward(bssn_corrector* c, const Geom& G, cudaStream_t s) {
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-      k_bias_grad<<<CH, 256, 0, s>>>(G, c->g[cur], gb);
+      k_bias_partial<<<BIAS_BLOCKS, 256, 0, s>>>(G, c->g[cur], c->bpart);
+      k_bias_final<<<1, 32, 0, s>>>(c->bpart, BIAS_BLOCKS, gb);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess && l > 0) {
       CUtensorMap ta, tw;
       if (!map_act(&ta, c->g[cur], G) || !map_w(&tw, c->wb + (size_t)l * NTAP * CH * CH))
         return cudaErrorInvalidValue;
-      const int tiles = G.S * G.Z * (G.Y / G.rpt);
-      k_conv_tc<1><<<tiles, 128, CONV_SMEM, s>>>(ta, tw, G, nullptr, nullptr, c->g[1 - cur], c->z[l - 1], 0, c->err);
+      k_conv_tc<1><<<conv_blocks(c, G), 128, CONV_SMEM, s>>>(ta, tw, G, nullptr, nullptr, c->g[1 - cur], c->z[l - 1], 0,
+                                                             c->err);
       e = cudaGetLastError();
       cur = 1 - cur;
     }
@@ -771,6 +882,8 @@ bssn_status_t bssn_corrector_create(bssn_corrector_t** out, int n, int max_batch
   c->partial = (float*)p;
   if (e == cudaSuccess) e = calloc_dev(c, 256 * sizeof(double), &p);
   c->lpart = (double*)p;
+  if (e == cudaSuccess) e = calloc_dev(c, (size_t)BIAS_BLOCKS * CH * sizeof(double), &p);
+  c->bpart = (double*)p;
   const size_t np = (size_t)NL * LAYER_PARAMS;
   if (e == cudaSuccess) e = calloc_dev(c, np * 4, &p);
   c->params = (float*)p;
@@ -794,6 +907,13 @@ bssn_status_t bssn_corrector_create(bssn_corrector_t** out, int n, int max_batch
     e = cudaFuncSetAttribute(k_wgrad_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, WG<64>::SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_wgrad_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, WG<32>::SMEM);
+  if (e == cudaSuccess) {
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<0>, 128, CONV_SMEM);
+    c->conv_grid = sms * (per_sm > 0 ? per_sm : 1);
+  }
   // seeded initialisation: uniform in +-sqrt(6 / fan_in) (real fan-in), the
   // last layer scaled by 0.1 so the initial correction is small; biases 0;
   // weights of padded channels 0
@@ -935,6 +1055,46 @@ bssn_status_t bssn_corrector_train_step(bssn_corrector_t* c, const bssn_grid_t* 
     if (!coarse[i] || !target[i]) return BSSN_ERR_INVALID_ARG;
     k_pack_state<<<512, 256, 0, s>>>(G, L, i, coarse[i], c->coef, c->act[0]);
     k_pack_target<<<512, 256, 0, s>>>(G, L, i, coarse[i], target[i], c->coef, c->target);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = network_forward(c, G, s);
+  if (e == cudaSuccess) e = loss_and_grad(c, G, loss, s);
+  if (e == cudaSuccess && lr > 0) {
+    c->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)c->adam_t), c2 = 1.f - powf(b2, (float)c->adam_t);
+    const int np = NL * LAYER_PARAMS;
+    k_adam<<<(np + 255) / 256, 256, 0, s>>>(np, c->params, c->grads, c->adam_m, c->adam_v, lr, b1, b2, 1e-8f, c1, c2);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = refresh_weights(c, s);
+  }
+  return status_of(c, e, s);
+}
+
+bssn_status_t bssn_corrector_pack(bssn_corrector_t* c, const bssn_grid_t* grid, const double* coarse,
+                                  const double* target, void* x_bf16, void* t_bf16, void* stream) {
+  if (!c || !grid || !coarse || !x_bf16 || (target && !t_bf16)) return BSSN_ERR_INVALID_ARG;
+  if (grid->nx != c->n || grid->ny != c->n || grid->nz != c->n) return BSSN_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  k_pack_pair<<<512, 256, 0, s>>>(geom_for(c, 1), make_layout(*grid), coarse, target, c->coef,
+                                  (__nv_bfloat16*)x_bf16, (__nv_bfloat16*)t_bf16);
+  return cudaGetLastError() == cudaSuccess ? BSSN_OK : BSSN_ERR_CUDA;
+}
+
+bssn_status_t bssn_corrector_train_step_raw(bssn_corrector_t* c, int S, const void* const* x_bf16,
+                                            const void* const* t_bf16, float lr, double* loss, void* stream) {
+  if (!c || !x_bf16 || !t_bf16 || !loss || S < 1 || S > c->max_batch || !(lr >= 0)) return BSSN_ERR_INVALID_ARG;
+  if (c->n > 64) return BSSN_ERR_UNSUPPORTED;  // the weight gradient walks whole x-rows of 32 or 64 points
+  cudaStream_t s = (cudaStream_t)stream;
+  const Geom G = geom_for(c, S);
+  const Geom G1 = geom_for(c, 1);
+  const long long pts1 = (long long)c->n * c->n * c->n;
+  const long long pad1 = (long long)(c->n + 2) * (c->n + 2) * (c->n + 2);
+  cudaError_t e = cudaMemsetAsync(c->err, 0, 4, s);
+  for (int i = 0; i < S && e == cudaSuccess; ++i) {
+    if (!x_bf16[i] || !t_bf16[i]) return BSSN_ERR_INVALID_ARG;
+    k_pad_copy<<<512, 256, 0, s>>>(G1, (const __nv_bfloat16*)x_bf16[i], c->act[0] + i * pad1 * CH);
+    k_bf16_to_f32<<<512, 256, 0, s>>>(pts1 * CH, (const __nv_bfloat16*)t_bf16[i], c->target + i * pts1 * CH);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = network_forward(c, G, s);

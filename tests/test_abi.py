@@ -118,3 +118,27 @@ def test_plan_invalid_arguments_rejected(L):
         B.plan_create([(good, FAKE, FAKE * 2)], p, prec=5)
     assert e.value.status == B.ERR_INVALID_ARG
     assert L.bssn_plan_destroy(None) == B.ERR_INVALID_ARG
+
+
+def test_transfer_rejects_invalid_arguments(L):
+    """Host-side checks of the 2:1 transfer (no kernel is reached)."""
+    fake = ctypes.c_void_p(4096)  # 16-byte aligned, never dereferenced
+    gf = B.make_grid(8, ghost=1, dx=0.1)
+    gc = B.make_grid(4, ghost=2, dx=0.2)
+    odd = B.make_grid(9, ghost=1, dx=0.1)
+    gc1 = B.make_grid(4, ghost=1, dx=0.2)
+    gf0 = B.make_grid(8, ghost=0, dx=0.1)
+    L.bssn_restrict.argtypes = [ctypes.POINTER(B.Grid), ctypes.c_void_p, ctypes.POINTER(B.Grid), ctypes.c_void_p,
+                                ctypes.c_int, ctypes.c_void_p]
+    L.bssn_prolong.argtypes = [ctypes.POINTER(B.Grid), ctypes.c_void_p, ctypes.POINTER(B.Grid), ctypes.c_void_p,
+                               ctypes.c_void_p]
+    r = lambda f, c, order, pf=fake, pc=ctypes.c_void_p(8192): L.bssn_restrict(ctypes.byref(f), pf, ctypes.byref(c),
+                                                                              pc, order, None)
+    assert r(odd, gc, 4) == B.ERR_INVALID_ARG  # not a 2:1 pair
+    assert r(gf, gc, 3) == B.ERR_INVALID_ARG  # unknown order
+    assert r(gf0, gc, 4) == B.ERR_INVALID_ARG  # order 4 needs a fine ghost
+    assert r(gf, gc, 2, pf=ctypes.c_void_p(4100)) == B.ERR_INVALID_ARG  # misaligned
+    assert r(gf, gc, 2, pc=fake) == B.ERR_INVALID_ARG  # same buffer
+    p = lambda c, f: L.bssn_prolong(ctypes.byref(c), fake, ctypes.byref(f), ctypes.c_void_p(8192), None)
+    assert p(gc1, gf) == B.ERR_INVALID_ARG  # coarse ghost < 2
+    assert p(gc, odd) == B.ERR_INVALID_ARG

@@ -1,0 +1,153 @@
+"""The learned corrector's glue through the C ABI: packing of training pairs
+(normalisation and BF16 rounding, bit-exact against host arithmetic), the
+applied correction (bit-exact against the raw forward pass, which
+test_gpu_corrector.py checks against the oracle), the fallback to the fine
+method, and the accuracy gain of a trained corrector over the plain coarse
+method on held-out Brill-Lindquist data."""
+import numpy as np
+import pytest
+
+from paper_1307_6488_gb300 import binding as B
+
+from gpu_common import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+N = 32
+G = 4
+
+
+def bf16_bits(torch, a):
+    """float64 array -> float32 (round to nearest) -> BF16 (round to nearest
+    even) bit patterns."""
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).view(torch.int16).numpy()
+
+
+def interior_points(u):
+    return u[:, G:-G, G:-G, G:-G].reshape(24, -1).T
+
+
+@pytest.fixture(scope="module")
+def setup():
+    torch = need_gpu()
+    rng = np.random.default_rng(11)
+    grid = B.make_grid(N, ghost=G, dx=0.1)
+    u = rng.standard_normal((24, N + 2 * G, N + 2 * G, N + 2 * G))
+    tgt = u + 0.01 * rng.standard_normal(u.shape)
+    off = rng.standard_normal(24)
+    isc = rng.uniform(0.5, 2.0, 24)
+    osc = rng.uniform(10.0, 100.0, 24)
+    c = B.corrector_create(N, 1, seed=3)
+    B.corrector_set_scales(c, off, isc, osc)
+    yield torch, grid, u, tgt, off, isc, osc, c
+    B.corrector_destroy(c)
+
+
+def test_pack_normalises_and_rounds(setup):
+    torch, grid, u, tgt, off, isc, osc, c = setup
+    xb = torch.empty((N ** 3, 32), dtype=torch.bfloat16, device="cuda")
+    tb = torch.empty_like(xb)
+    B.corrector_pack(c, grid, B.upload(u, grid), B.upload(tgt, grid), xb, tb)
+    torch.cuda.synchronize()
+    I, T = interior_points(u), interior_points(tgt)
+    x = xb.cpu().view(torch.int16).numpy()
+    t = tb.cpu().view(torch.int16).numpy()
+    np.testing.assert_array_equal(x[:, :24], bf16_bits(torch, (I - off) * isc))
+    np.testing.assert_array_equal(t[:, :24], bf16_bits(torch, (T - I) * osc))
+    assert not x[:, 24:].any() and not t[:, 24:].any()
+
+
+def test_apply_adds_unscaled_network_output(setup):
+    torch, grid, u, tgt, off, isc, osc, c = setup
+    xb = torch.empty((N ** 3, 32), dtype=torch.bfloat16, device="cuda")
+    tb = torch.empty_like(xb)
+    state = B.upload(u, grid)
+    B.corrector_pack(c, grid, state, state, xb, tb)
+    out = torch.empty((N ** 3, 32), dtype=torch.float32, device="cuda")
+    B.corrector_forward_raw(c, 1, xb, out)
+    B.corrector_apply(c, grid, state)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy().astype(np.float64)
+    assert np.abs(o[:, :24]).max() > 0
+    want = u.copy()
+    want[:, G:-G, G:-G, G:-G] += (o[:, :24] / osc).T.reshape(24, N, N, N)
+    got = B.download(state, grid)
+    np.testing.assert_array_equal(got, want)
+
+
+def _bl_stepper(masses=(0.45, 0.55), separation=2.7):
+    from paper_1307_6488_gb300 import learned as LR
+    return LR, LR.Stepper(LR.Problem("bl", N, masses=masses, separation=separation))
+
+
+def test_fallback_is_the_fine_method(setup):
+    torch, _, _, _, _, _, _, c = setup
+    LR, st = _bl_stepper()
+    B.corrector_set_scales(c, np.zeros(24), np.ones(24), np.ones(24))
+    y = st.src_c.clone()
+    before = y.clone()
+    # factor 0: the learned step is never accepted
+    used, h_learned, h_plain = LR.learned_step(st, c, y, fallback_factor=0.0)
+    assert used and h_plain > 0
+    fine = B.alloc_state(st.p.gf)
+    st.prolong(before, fine)
+    st.fine_step(fine)
+    st.fine_step(fine)
+    ref = B.alloc_state(st.p.gc)
+    st.restrict(fine, ref)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(B.download(y, st.p.gc), B.download(ref, st.p.gc))
+
+
+def test_fallback_triggers_on_a_harmful_correction(setup):
+    torch, _, _, _, _, _, _, c = setup
+    LR, st = _bl_stepper()
+    # tiny output scale: the correction is the raw network output x 1e6
+    B.corrector_set_scales(c, np.zeros(24), np.ones(24), np.full(24, 1e-6))
+    y = st.src_c.clone()
+    used, h_learned, h_plain = LR.learned_step(st, c, y, fallback_factor=2.0)
+    assert used and not (h_learned <= 2.0 * h_plain)
+    # accepted when the bound is loose enough
+    B.corrector_set_scales(c, np.zeros(24), np.ones(24), np.full(24, 1e12))
+    y = st.src_c.clone()
+    used, h_learned, h_plain = LR.learned_step(st, c, y, fallback_factor=2.0)
+    assert not used
+
+
+def test_trained_corrector_beats_the_plain_coarse_method():
+    """Train on pairs the plain method generates (16 fine trajectories at
+    64^3 -> 32^3 coarse, 10 pairs each: Brill-Lindquist pairs with masses
+    0.3-0.7 and separations 2-4, every fifth a gauge wave), then evolve two
+    held-out Brill-Lindquist problems 8 coarse steps: the learned error
+    against the restricted fine solution must be under half the plain
+    coarse error, with no fallback, and the Hamiltonian-constraint L2 must
+    stay within 10% of the fine method's."""
+    torch = need_gpu()
+    from paper_1307_6488_gb300 import learned as LR
+    rng = np.random.default_rng(0)
+    probs = []
+    for i in range(16):
+        if i % 5 == 4:
+            probs.append(LR.Problem("gw", N, amplitude=float(rng.uniform(0.02, 0.1))))
+        else:
+            m = rng.uniform(0.3, 0.7, 2)
+            probs.append(LR.Problem("bl", N, masses=tuple(m), separation=float(rng.uniform(2, 4))))
+    c = B.corrector_create(N, 4, seed=1)
+    try:
+        pairs = [(pr, LR.trajectory_pairs(LR.Stepper(pr), 10)) for pr in probs]
+        sample = [pp for (_, ps) in pairs for pp in ps[::3]]
+        B.corrector_set_scales(c, *LR.default_scales(sample, probs[0].gc))
+        data = LR.Dataset(c, N)
+        for pr, ps in pairs:
+            data.add(ps, pr.gc)
+        del pairs, sample
+        losses = LR.train(c, data, epochs=30, batch=4, lr=1e-3, lr_final=5e-5)
+        assert np.mean(losses[-10:]) < 0.2 * losses[0]
+        for kw in (dict(masses=(0.45, 0.55), separation=2.7), dict(masses=(0.35, 0.65), separation=3.5)):
+            st = LR.Stepper(LR.Problem("bl", N, **kw))
+            r = LR.evaluate(st, c, 8)
+            assert r["fallbacks"] == 0, r
+            assert r["err_learned"] < 0.5 * r["err_plain"], r
+            assert abs(r["ham_learned"] - r["ham_fine"]) < 0.1 * r["ham_fine"], r
+    finally:
+        B.corrector_destroy(c)

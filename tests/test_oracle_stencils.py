@@ -9,6 +9,7 @@ The stencils follow the paper's 'customized finite differencing operators'
   * exactness on monomials up to the operator's degree,
 and Kreiss-Oliger dissipation against its closed-form Fourier symbol.
 """
+import os
 from fractions import Fraction as F
 
 import numpy as np
@@ -16,14 +17,19 @@ import pytest
 
 import oracle
 
-# closed-form centered weights w_a for offsets a = 1..p/2 (w_-a = -w_a for the
-# first derivative, w_-a = w_a for the second)
-TEXTBOOK = {
-    (1, 4): [F(2, 3), F(-1, 12)],
-    (1, 8): [F(4, 5), F(-1, 5), F(4, 105), F(-1, 280)],
-    (2, 4): [F(4, 3), F(-1, 12)],
-    (2, 8): [F(8, 5), F(-1, 5), F(8, 315), F(-1, 560)],
-}
+
+
+def _textbook():
+    """Closed-form centred weights w_a, a = 1..p/2, from the golden table
+    (Fornberg 1988, Table 1): {(m, order): [w_1, w_2, ...]}."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fd_weights.txt")
+    table = {}
+    for m, order, a, num, den in np.loadtxt(path, comments="#", dtype=np.int64):
+        table.setdefault((int(m), int(order)), {})[int(a)] = F(int(num), int(den))
+    return {k: [v[a] for a in sorted(v)] for k, v in table.items()}
+
+
+TEXTBOOK = _textbook()
 
 
 @pytest.mark.parametrize("m,order", [(1, 4), (1, 8), (2, 4), (2, 8)])
