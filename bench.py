@@ -42,6 +42,14 @@ WORKLOAD = ("Brill-Lindquist two punctures (m=0.5 at x=+-1.5), 128^3 on [-8,8]^3
 # variable). See DESIGN.md "Algorithmic work".
 FLOPS_PER_POINT_STAGE = None  # filled from the oracle's counter at start-up
 
+# Measured copy bandwidth and dense BF16 GEMM rate of this GPU type
+# (absent on machines where they were not measured).
+try:
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as _f:
+        MEASURED = json.load(_f)
+except (OSError, ValueError):
+    MEASURED = {}
+
 # DRAM traffic of the fused stage kernel per launch, from one ncu capture of
 # the same source (profiles/); ignored when the kernel source has changed.
 TRAFFIC = {"src_sha": None, "bytes_per_launch_128": None}
@@ -326,6 +334,147 @@ def run_gpu(args):
                 "fd_order": 4, "dt": dtb, "graph_launches_per_step": 1,
                 "kernel_nodes_per_step": 13 if prec == B.FP64 else 17}
 
+    def run_learned():
+        """Learned half-resolution evolution: train the corrector on pairs the
+        plain method generates (64^3 coarse step vs restricted 128^3 fine
+        step; Brill-Lindquist data with masses 0.3-0.7 and separations 2-4,
+        every fifth trajectory a gauge wave; 4th order), then time learned
+        coarse steps (coarse RK4 + correction + Hamiltonian check, fallback
+        to the fine method) against the plain fine method over the same
+        physical time, and state the error of each against the restricted
+        fine solution."""
+        from paper_1307_6488_gb300 import learned as LR
+        nc, per_traj = 64, 10
+        ntraj = max(1, args.learned_pairs // per_traj)
+        rng = np.random.default_rng(0)
+        probs = []
+        for i in range(ntraj):
+            if i % 5 == 4:
+                probs.append(LR.Problem("gw", nc, amplitude=float(rng.uniform(0.02, 0.1))))
+            else:
+                m = rng.uniform(0.3, 0.7, 2)
+                probs.append(LR.Problem("bl", nc, masses=tuple(m), separation=float(rng.uniform(2, 4))))
+        corr = B.corrector_create(nc, 4, seed=1)
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            data = LR.Dataset(corr, nc)
+            # normalisation scales from the first (pilot) trajectories, which
+            # include a gauge wave; every pair is packed to BF16 as soon as
+            # the scales are known, so only packed pairs stay resident
+            pilot = min(len(probs), 5)
+            pending = []
+            for i, pr in enumerate(probs):
+                ps = LR.trajectory_pairs(LR.Stepper(pr), per_traj)
+                if i >= pilot:
+                    data.add(ps, pr.gc)
+                    continue
+                pending.append((pr, ps))
+                if i == pilot - 1:
+                    sample = [pp for _, qs in pending for pp in qs[::3]]
+                    B.corrector_set_scales(corr, *LR.default_scales(sample, pr.gc))
+                    for q, qs in pending:
+                        data.add(qs, q.gc)
+                    pending = sample = None
+            torch.cuda.synchronize()
+            t_gen = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            losses = LR.train(corr, data, epochs=args.learned_epochs, batch=4, lr=1e-3, lr_final=5e-5)
+            torch.cuda.synchronize()
+            t_train = time.perf_counter() - t0
+            train_steps = len(losses)
+            del data
+            # held-out problems: accuracy over 8 coarse steps
+            held = {"bl_m0.45_0.55_d2.7": ("bl", dict(masses=(0.45, 0.55), separation=2.7)),
+                    "bl_m0.35_0.65_d3.5": ("bl", dict(masses=(0.35, 0.65), separation=3.5)),
+                    "gauge_wave_a0.07": ("gw", dict(amplitude=0.07))}
+            acc = {}
+            for name, (kind, kw) in held.items():
+                st = LR.Stepper(LR.Problem(kind, nc, **kw))
+                acc[name] = LR.evaluate(st, corr, 8)
+            # throughput: learned coarse step vs two plain fine steps (same dt_c)
+            st = LR.Stepper(LR.Problem("bl", nc, masses=(0.45, 0.55), separation=2.7))
+            y = st.src_c.clone()
+            scratch = torch.empty_like(y)
+            fb = 0
+            for _ in range(args.warmup):
+                fb += LR.learned_step(st, corr, y, scratch=scratch)[0]
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                fb += LR.learned_step(st, corr, y, scratch=scratch)[0]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_learned = e0.elapsed_time(e1) / args.steps
+            f = st.src_f.clone()
+            for _ in range(args.warmup):
+                st.fine_step(f)
+            e0.record(stream)
+            for _ in range(args.steps):
+                st.fine_step(f)
+                st.fine_step(f)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_fine2 = e0.elapsed_time(e1) / args.steps
+            c = st.src_c.clone()
+            e0.record(stream)
+            for _ in range(args.steps):
+                st.coarse_step(c)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_coarse = e0.elapsed_time(e1) / args.steps
+            # the network alone: one 64^3 forward pass (input copy, 5 tensor-core
+            # convolutions, output copy), inputs resident
+            xb = torch.empty((nc ** 3, 32), dtype=torch.bfloat16, device=dev)
+            tb = torch.empty_like(xb)
+            B.corrector_pack(corr, st.p.gc, y, y, xb, tb)
+            out = torch.empty((nc ** 3, 32), dtype=torch.float32, device=dev)
+            for _ in range(args.warmup):
+                B.corrector_forward_raw(corr, 1, xb, out)
+            torch.cuda.synchronize()
+            reps = max(10, args.steps)
+            e0.record(stream)
+            for _ in range(reps):
+                B.corrector_forward_raw(corr, 1, xb, out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_forward = e0.elapsed_time(e1) / reps
+            mma32 = B.probe_mma_rate(32)
+        finally:
+            B.corrector_destroy(corr)
+        torch.cuda.empty_cache()
+        nf3 = (2 * nc) ** 3
+        # algorithmic network flops per point: 2 x 27 taps x (24x32 + 3 x 32x32 + 32x24) multiply-adds
+        net_flops = 2 * 27 * (24 * 32 + 3 * 32 * 32 + 32 * 24)
+        conv_tflops = net_flops * nc ** 3 / (ms_forward * 1e-3) / 1e12
+        return {"value": 2 * nf3 / (ms_learned * 1e-3), "unit": "fine-grid-equivalent point updates/s",
+                "plain_fine_value": 2 * nf3 / (ms_fine2 * 1e-3),
+                "speedup_vs_plain_fine": ms_fine2 / ms_learned,
+                "ms_learned_step": ms_learned, "ms_two_fine_steps": ms_fine2, "ms_plain_coarse_step": ms_coarse,
+                "fallbacks_in_timed_steps": int(fb),
+                "network_forward_ms_64cubed": ms_forward,
+                "network_roofline": {"bound": "tensor", "achieved": conv_tflops,
+                                     "peak": mma32, "unit": "TFLOP/s", "frac": conv_tflops / mma32,
+                                     "flops_per_point": net_flops,
+                                     "peak_source": "measured rate of back-to-back M=128 N=32 K=16 BF16 tcgen05 "
+                                                    "MMAs (bssn_probe_mma_rate), the instruction ceiling of the "
+                                                    "N = 32-channel convolutions",
+                                     "frac_of_dense_bf16": conv_tflops / MEASURED.get("bf16_tflops", 1922.5)},
+                "accuracy_8_coarse_steps": acc,
+                "accuracy_note": "err_* = RMS over interior points and variables of (x - restricted fine) / "
+                                 "per-variable RMS change of the fine solution over the run; ham_* = Hamiltonian "
+                                 "constraint L2 (FP64)",
+                "training": {"pairs": ntraj * per_traj, "trajectories": ntraj, "epochs": args.learned_epochs,
+                             "batch": 4, "adam_steps": train_steps, "loss_first": losses[0],
+                             "loss_last20_mean": float(np.mean(losses[-20:])), "gen_s": t_gen, "train_s": t_train,
+                             "ms_per_train_step": 1e3 * t_train / max(1, train_steps)},
+                "config": "coarse 64^3 / fine 128^3 on [-8,8]^3 (gauge wave [-0.5,0.5]^3), 4 ghosts, 4th order, "
+                          "1+log + Gamma-driver, KO 0.1, dt_c = 0.25 h_c, FP64 evolution; corrector 5 x conv3d "
+                          "3^3, 32 channels, GELU, BF16 tcgen05 with FP32 accumulation; fallback if H L2 > 2x "
+                          "plain coarse"}
+
     f64 = run_form(B.FP64, not args.profile)
     f32 = run_form(B.FP32_RHS, False)
     if args.profile:
@@ -338,6 +487,8 @@ def run_gpu(args):
     if not args.no_batched:
         batched["batched_fp64"] = run_batched(B.FP64)
         batched["batched_fp32_rhs"] = run_batched(B.FP32_RHS)
+    if not args.no_learned:
+        batched["learned_64_from_128"] = run_learned()
 
     # end to end through the public API with host buffers (pinned): upload the
     # step's input state, one RK4 step (bssn_rk4_step), read the result back
@@ -420,6 +571,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--grid", type=int, default=N, help="interior points per axis (profiling: smaller cases)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 192-patch batched workload")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-corrector form")
+    ap.add_argument("--learned-pairs", type=int, default=200,
+                    help="training pairs for the learned form (10 per fine trajectory; the full set is 2000)")
+    ap.add_argument("--learned-epochs", type=int, default=20)
     ap.add_argument("--profile", action="store_true",
                     help="only the FP64 and FP32 timed loops (no probe, e2e, CPU leg): for ncu captures")
     args = ap.parse_args()

@@ -332,6 +332,14 @@ bssn_status_t bssn_constraints(const bssn_grid_t* grid, const bssn_params_t* par
  * out[2] = FP64 add/s. HOST array. Synchronizes the device. */
 bssn_status_t bssn_probe_fp_rates(double* out);
 
+/* Measures the rate of back-to-back dense BF16 tcgen05 MMAs (M = 128, K = 16,
+ * FP32 accumulation, one CTA per SM, operands fixed in shared memory) with
+ * N = n output columns (32, 64, 128 or 256) and writes it to *tflops (HOST),
+ * in TFLOP/s over all SMs. The convolutions issue N = 32 (one column per
+ * output channel); their roofline is this rate at n = 32. Synchronizes the
+ * device. Not a computation of the paper. */
+bssn_status_t bssn_probe_mma_rate(int n, double* tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -362,6 +362,16 @@ def prolong(coarse_grid, coarse_state, fine_grid, fine_state, stream=None):
                                         _ptr(fine_state), _stream(stream)), "prolong")
 
 
+def probe_mma_rate(n=32):
+    """Measured TFLOP/s of back-to-back M=128 K=16 BF16 MMAs with N = n."""
+    L = _corr_lib()
+    L.bssn_probe_mma_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.bssn_probe_mma_rate.restype = ctypes.c_int
+    out = ctypes.c_double()
+    _check(L.bssn_probe_mma_rate(n, ctypes.byref(out)), "probe_mma_rate")
+    return out.value
+
+
 def corrector_apply(c, grid, state, stream=None):
     _check(_corr_lib().bssn_corrector_apply(c, ctypes.byref(grid), _ptr(state), _stream(stream)), "corrector_apply")
 

@@ -42,11 +42,9 @@ constexpr int CH = 32;
 constexpr int NL = 5;
 constexpr int NTAP = 27;
 constexpr int BM = 128;
-constexpr int STAGES = 6;  // 2 CTAs (about 104 KB each) per SM
 constexpr int A_BYTES = BM * CH * 2;      // 8 KB per A tile
 constexpr int W_TAP_BYTES = CH * CH * 2;  // 2 KB per tap
-constexpr int CONV_SMEM = 1024 + STAGES * A_BYTES + NTAP * W_TAP_BYTES + 256;
-constexpr int WG_STAGES = 3;
+constexpr int WG_STAGES = 4;
 constexpr int XOFF = 8;                   // interior column of the channels-first copies
 constexpr int LAYER_PARAMS = NTAP * CH * CH + CH;
 // weight-gradient tiles for x-rows of XW (32 or 64) points: one channel row is
@@ -64,11 +62,32 @@ struct WG {
 
 struct Geom {
   int S, Z, Y, X;  // samples and interior points per axis
-  int rpt;         // y-rows per 128-point tile (128 / X)
 };
 
-__host__ __device__ inline long long padded_index(const Geom& G, int s, int z, int y, int x) {
-  return (((long long)s * (G.Z + 2) + z + 1) * (G.Y + 2) + y + 1) * (G.X + 2) + x + 1;
+// Padded activations and gradients (BF16, one zero point on every side) are
+// stored chunk-major: per sample s and padded plane zz (0 .. Z+1), four
+// planes of 8 channels each, [Y+2][X+2][8]. Offsets below count 8-channel
+// groups (16 bytes). A slab of consecutive rows of one chunk plane is then
+// contiguous, which the convolution's shared-memory slabs rely on.
+__host__ __device__ inline long long chunk_off(const Geom& G, int s, int zz, int q, int yy, int xx) {
+  return ((((long long)s * (G.Z + 2) + zz) * 4 + q) * (G.Y + 2) + yy) * (G.X + 2) + xx;
+}
+__host__ __device__ inline long long chunk_stride(const Geom& G) { return (long long)(G.Y + 2) * (G.X + 2); }
+
+// the 32 channels (4 x 16 bytes) of interior point (s, z, y, x)
+__device__ __forceinline__ void store_point(const Geom& G, __nv_bfloat16* buf, int s, int z, int y, int x,
+                                            const __nv_bfloat16* h) {
+  uint4* p = (uint4*)buf + chunk_off(G, s, z + 1, 0, y + 1, x + 1);
+  const long long cs = chunk_stride(G);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) p[q * cs] = ((const uint4*)h)[q];
+}
+__device__ __forceinline__ void load_point(const Geom& G, const __nv_bfloat16* buf, int s, int z, int y, int x,
+                                           __nv_bfloat16* h) {
+  const uint4* p = (const uint4*)buf + chunk_off(G, s, z + 1, 0, y + 1, x + 1);
+  const long long cs = chunk_stride(G);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) ((uint4*)h)[q] = __ldg(p + q * cs);
 }
 
 __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
@@ -81,181 +100,291 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
 //         padded, GELU applied if gelu) as requested.
 // MODE 1: d = conv(g) with the transposed, flipped weights; if zprev, d *=
 //         GELU'(zprev); act_out (BF16, padded) receives d.
+//
+// Shared-memory slabs instead of one load per tap. A work unit is (sample,
+// block of R output rows, run of L output planes). For every input plane the
+// unit needs (L + 2 of them) one TMA box brings rows y0-1 .. y0+R, points
+// x = 0 .. X (the last one is the zero pad) and all 32 channels into a slab
+// laid out [chunk of 8 channels][row][x] with X+1 entries per row, so entry
+// e = row (X+1) + x sits at e * 16 bytes within its chunk. Because the pad
+// entry separates the rows, the input of tap (dy, dx) for output entry e is
+// entry e + dy (X+1) + dx: a plain shift. The M = 128 rows of an MMA are 128
+// consecutive output entries (pad entries and rows past R give results that
+// are discarded), the A operand of every tap is the same slab seen through a
+// shifted no-swizzle descriptor (core matrices 8 entries x 16 bytes, SBO =
+// 128 bytes, LBO = one chunk), and T tiles of 128 entries cover the R rows.
+//   warp 4 (one lane)  loads the 27 weight taps once and streams slabs into a
+//                      4-deep ring (an input plane serves three output planes);
+//   warp 5 (one lane)  issues 27 taps x 2 MMAs (K = 16) per tile into one of
+//                      two TMEM accumulator sets (T x 32 columns each) and
+//                      releases a slab at its last use; it never waits for
+//                      an MMA to finish;
+//   warps 0-3          read the accumulators out (TMEM lanes 32w .. 32w+31)
+//                      and run the epilogue while the next output plane
+//                      accumulates into the other set.
+// Every wait is bounded; a role that times out sets the error word and the
+// CTA-wide abort flag, the others leave their loops, in-flight copies and
+// MMAs are waited for (bounded) and TMEM is freed.
+constexpr int CONV_THREADS = 192;
+constexpr int SLABS = 4;
+
+struct ConvPlan {
+  int R;              // output rows per unit
+  int T;              // 128-entry M tiles covering R rows of X+1 entries
+  int L;              // output planes per unit (set per call)
+  int nyb, nzs;       // row blocks, plane runs
+  int chunk_bytes;    // (R+2)(X+1) x 16
+  int plane_bytes;    // 4 chunks
+  int tail_bytes;     // past the last slab: reads of discarded rows
+  int tmem_cols;      // power of two >= 2 T 32
+  int smem;           // dynamic shared memory
+  int slab_off;       // offset of slab 0 from the 1024-aligned base
+  int bar_off;        // offset of the barriers
+};
+
 template <int MODE>
-__global__ void __launch_bounds__(128, 2)
-    k_conv_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW, Geom G,
+__global__ void __launch_bounds__(CONV_THREADS, 1)
+    k_conv_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW, Geom G, ConvPlan P,
               const float* __restrict__ bias, float* __restrict__ zout, __nv_bfloat16* __restrict__ act_out,
               const float* __restrict__ zprev, int gelu, unsigned int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* A = base;
-  uint8_t* Wt = base + STAGES * A_BYTES;
-  uint64_t* bars = (uint64_t*)(Wt + NTAP * W_TAP_BYTES);
+  uint8_t* Wt = base;                // 27 taps x [32 co][32 ci], 64-byte swizzle
+  uint8_t* slab = base + P.slab_off;  // SLABS x plane_bytes; the 16 bytes before it are zero
+  uint64_t* bars = (uint64_t*)(base + P.bar_off);
   uint64_t* full = bars;
-  uint64_t* empty = bars + STAGES;
-  uint64_t* wbar = bars + 2 * STAGES;
-  uint64_t* done = wbar + 1;
-  uint32_t* tslot = (uint32_t*)(done + 1);
+  uint64_t* empty = bars + SLABS;
+  uint64_t* tfull = bars + 2 * SLABS;   // [2] accumulator set complete
+  uint64_t* tempty = tfull + 2;         // [2] accumulator set read out (one arrive per epilogue warp)
+  uint64_t* wbar = tempty + 2;
+  uint64_t* drain = wbar + 1;           // all MMAs of this CTA finished
+  uint32_t* tslot = (uint32_t*)(drain + 1);
+  __shared__ volatile int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tiles_per_plane = G.Y / G.rpt;
-  const int ntiles = G.S * G.Z * tiles_per_plane;
-  // persistent: this CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...
-  const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  const int nsteps = my_tiles * NTAP;  // one K step per (tile, tap)
-  auto tile_pos = [&](int it, int& s, int& z, int& y0) {
-    const int t = blockIdx.x + it * gridDim.x;
-    s = t / (G.Z * tiles_per_plane);
-    const int rem = t - s * G.Z * tiles_per_plane;
-    z = rem / tiles_per_plane;
-    y0 = (rem % tiles_per_plane) * G.rpt;
+  const int XS = G.X + 1;
+  const int units = G.S * P.nyb * P.nzs;
+  auto unit_pos = [&](int u, int& s, int& yb, int& z0, int& len) {
+    const int zs = u % P.nzs;
+    const int t = u / P.nzs;
+    yb = t % P.nyb;
+    s = t / P.nyb;
+    z0 = zs * P.L;
+    len = min(P.L, G.Z - z0);
   };
 
+  // zero the entry before slab 0 and the tail (read only for discarded rows)
+  {
+    uint32_t* lead = (uint32_t*)(slab - 128);
+    if (tid < 32) lead[tid] = 0u;
+    uint32_t* tail = (uint32_t*)(slab + SLABS * P.plane_bytes);
+    for (int i = tid; i < P.tail_bytes / 4; i += blockDim.x) tail[i] = 0u;
+    tc::fence_proxy_async();
+  }
   if (tid == 0) {
-    for (int i = 0; i < STAGES; ++i) {
+    abort_flag = 0;
+    for (int i = 0; i < SLABS; ++i) {
       tc::mbar_init(&full[i], 1);
       tc::mbar_init(&empty[i], 1);
     }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&tfull[b], 1);
+      tc::mbar_init(&tempty[b], 4);
+    }
     tc::mbar_init(wbar, 1);
-    tc::mbar_init(done, 1);
+    tc::mbar_init(drain, 1);
     tc::mbar_fence_init();
   }
-  if (warp == 0) tc::tmem_alloc(tslot, 32);
+  if (warp == 0) tc::tmem_alloc(tslot, (uint32_t)P.tmem_cols);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t taddr = *tslot;
   constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, 32);
+  const bool any = (int)blockIdx.x < units;
 
-  // producer / MMA state (thread 0): steps loaded so far, steps consumed, failure
-  int issued = 0, consumed = 0;
-  bool fail = false;
-  auto load_step = [&](int q) {
-    int s, z, y0;
-    tile_pos(q / NTAP, s, z, y0);
-    const int k = q % NTAP;
-    const int slot = q % STAGES;
-    const int dz = k / 9 - 1, dy = (k / 3) % 3 - 1, dx = k % 3 - 1;
-    tc::mbar_expect_tx(&full[slot], A_BYTES);
-    tc::tma_load_4d(A + slot * A_BYTES, &tmA, 0, 1 + dx, y0 + 1 + dy, s * (G.Z + 2) + z + 1 + dz, &full[slot]);
-  };
-  // wait (bounded) for every A load still in flight before giving up
-  auto drain = [&]() {
-    for (int q = consumed; q < issued; ++q) (void)tc::mbar_wait(&full[q % STAGES], (q / STAGES) & 1, 100000000ull);
-  };
-  if (tid == 0 && nsteps > 0) {
-    tc::mbar_expect_tx(wbar, NTAP * W_TAP_BYTES);
-    for (int k = 0; k < NTAP; ++k) tc::tma_load_2d(Wt + k * W_TAP_BYTES, &tmW, 0, k * CH, wbar);
-    for (; issued < STAGES && issued < nsteps; ++issued) load_step(issued);
-    if (!tc::mbar_wait(wbar, 0)) {
-      fail = true;
-      atomicOr(err, 1u);
-      drain();
-    }
-  }
-
-  for (int it = 0; it < my_tiles; ++it) {
-    if (tid == 0 && !fail) {
-      for (int k = 0; k < NTAP && !fail; ++k) {
-        const int q = it * NTAP + k;
-        const int slot = q % STAGES;
-        if (!tc::mbar_wait(&full[slot], (q / STAGES) & 1)) {
-          fail = true;
-          break;
-        }
-        consumed = q + 1;
-        tc::fence_after_sync();
-        const uint64_t ad = tc::smem_desc(tc::smem_u32(A + slot * A_BYTES), 16, 512, tc::SWZ_64B);
-        const uint64_t bd = tc::smem_desc(tc::smem_u32(Wt + k * W_TAP_BYTES), 16, 512, tc::SWZ_64B);
-#pragma unroll
-        for (int j = 0; j < 2; ++j) tc::mma_bf16(taddr, ad + 2 * j, bd + 2 * j, IDESC, (k > 0 || j > 0) ? 1u : 0u);
-        tc::mma_commit(&empty[slot]);
-        // refill the slot of the previous step once its MMAs are done; the
-        // ring runs on across tiles, so the next tile's first taps are
-        // already loaded while this tile's epilogue runs
-        if (q >= 1 && issued < nsteps) {
-          const int pq = q - 1;
-          if (!tc::mbar_wait(&empty[pq % STAGES], (pq / STAGES) & 1)) {
-            fail = true;
+  if (warp == 4) {
+    // ---- TMA producer
+    if (lane == 0 && any) {
+      tc::mbar_expect_tx(wbar, NTAP * W_TAP_BYTES);
+      for (int k = 0; k < NTAP; ++k) tc::tma_load_2d(Wt + k * W_TAP_BYTES, &tmW, 0, k * CH, wbar);
+      uint32_t g = 0;  // slabs issued (sequence over all units)
+      bool ok = true;
+      for (int u = blockIdx.x; ok && u < units; u += gridDim.x) {
+        int s, yb, z0, len;
+        unit_pos(u, s, yb, z0, len);
+        for (int k = 0; k < len + 2; ++k) {
+          const uint32_t buf = g % SLABS;
+          if (g >= SLABS && !tc::mbar_wait_or_abort(&empty[buf], ((g / SLABS) - 1) & 1, &abort_flag)) {
+            if (!abort_flag) atomicOr(err, 1u);
+            abort_flag = 1;
+            ok = false;
             break;
           }
-          load_step(issued);
-          ++issued;
+          tc::mbar_expect_tx(&full[buf], (uint32_t)P.plane_bytes);
+          // padded plane z0 + k holds input plane z0 - 1 + k; padded row yb R
+          // is output row yb R - 1
+          tc::tma_load_5d(slab + buf * P.plane_bytes, &tmA, 0, 1, yb * P.R, 0, s * (G.Z + 2) + z0 + k, &full[buf]);
+          ++g;
         }
       }
-      tc::mma_commit(done);
-      if (fail) {
-        atomicOr(err, 1u);
-        drain();
-        (void)tc::mbar_wait(done, it & 1, 100000000ull);
-      }
+      // the last use of every slab buffer has landed before the CTA leaves
+      for (uint32_t q = g > SLABS ? g - SLABS : 0; q < g; ++q)
+        (void)tc::mbar_wait(&full[q % SLABS], (q / SLABS) & 1, 100000000ull);
+      (void)tc::mbar_wait(wbar, 0, 100000000ull);
     }
-    const int any_fail = __syncthreads_or(tid == 0 && fail);
-    bool ok = !any_fail && tc::mbar_wait(done, it & 1);
-    if (!ok && !any_fail) atomicOr(err, 2u);
-    ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
-    tc::fence_after_sync();
-    if (ok) {
-      int s, z, y0;
-      tile_pos(it, s, z, y0);
-      float acc[32];
-      tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16), acc);
-      const int row = warp * 32 + lane;
-      const int y = y0 + row / G.X, x = row % G.X;
-      const long long pt = (((long long)s * G.Z + z) * G.Y + y) * G.X + x;
-      const long long pp = padded_index(G, s, z, y, x);
-      if (MODE == 0) {
+  } else if (warp == 5) {
+    // ---- MMA issuer
+    if (lane == 0 && any) {
+      bool ok = tc::mbar_wait_or_abort(wbar, 0, &abort_flag);
+      const uint32_t slab0 = tc::smem_u32(slab);
+      const uint64_t w_desc0 = tc::smem_desc(tc::smem_u32(Wt), 16, 512, tc::SWZ_64B);
+      // entry shift of tap (dy, dx) relative to the output entry, as a
+      // descriptor address increment (entries of 16 bytes): (1 + dy)(X+1) + dx
+      int tap_off[9];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) acc[c] += __ldg(bias + c);
-        if (zout) {
-          float4* zo = (float4*)(zout + pt * CH);
+      for (int t = 0; t < 9; ++t) tap_off[t] = XS * (t / 3) + (t % 3) - 1;
+      const uint32_t k_half = (uint32_t)(2 * P.chunk_bytes) >> 4;
+      uint32_t g = 0, step = 0;  // slab sequence at the unit's first plane; output planes done
+      for (int u = blockIdx.x; ok && u < units; u += gridDim.x) {
+        int s, yb, z0, len;
+        unit_pos(u, s, yb, z0, len);
+        for (int o = 0; ok && o < len; ++o, ++step) {
+          const uint32_t a = step & 1;
+          if (step >= 2 && !tc::mbar_wait_or_abort(&tempty[a], ((step >> 1) - 1) & 1, &abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t dbase = taddr + a * (uint32_t)(P.T * 32);
+          for (int dz = 0; dz < 3; ++dz) {
+            const uint32_t accum0 = dz ? 1u : 0u;  // the first MMA of a tile starts the sum
+            const uint32_t gg = g + o + dz;  // the slab of input plane z0 + o + dz - 1
+            const uint32_t buf = gg % SLABS;
+            if (!tc::mbar_wait_or_abort(&full[buf], (gg / SLABS) & 1, &abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after_sync();
+            // descriptors change only in the start-address field (bits 0-13,
+            // bytes / 16): an entry shift adds the entry count, the second K
+            // half adds two chunks, the next tap's weights add 2 KB
+            const uint64_t a_plane = tc::smem_desc(slab0 + buf * (uint32_t)P.plane_bytes, (uint32_t)P.chunk_bytes, 128,
+                                                   tc::SWZ_NONE);
+            const uint64_t b_plane = w_desc0 + (uint64_t)(dz * 9 * (W_TAP_BYTES >> 4));
+            for (int j = 0; j < P.T; ++j) {
+              const uint64_t a_tile = a_plane + (uint64_t)(128 * j);  // 128 entries (of 16 bytes) per tile
+              const uint32_t d = dbase + (uint32_t)(j * 32);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+              for (int t = 0; t < 9; ++t) {
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                  const uint64_t ad = a_tile + (uint64_t)(int64_t)tap_off[t] + (uint64_t)(kk * k_half);
+                  const uint64_t bd = b_plane + (uint64_t)(t * (W_TAP_BYTES >> 4) + 2 * kk);
+                  tc::mma_bf16(d, ad, bd, IDESC, (t | kk) ? 1u : accum0);
+                }
+              }
+            }
+            // release slabs at their last use: input plane o at dz = 0, the
+            // last two planes of the unit after the unit's last output plane
+            if (dz == 0) tc::mma_commit(&empty[buf]);
+            if (dz > 0 && o == len - 1) tc::mma_commit(&empty[buf]);
+          }
+          if (ok) tc::mma_commit(&tfull[a]);
         }
-        if (act_out) {
-          __align__(16) __nv_bfloat16 h[32];
-#pragma unroll
-          for (int c = 0; c < 32; ++c) h[c] = __float2bfloat16_rn(gelu ? gelu_f(acc[c]) : acc[c]);
-          uint4* dst = (uint4*)(act_out + pp * CH);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) dst[q] = ((const uint4*)h)[q];
+        g += (uint32_t)(len + 2);
+      }
+      if (!ok) {
+        if (!abort_flag) atomicOr(err, 1u);
+        abort_flag = 1;
+      }
+      // every MMA this thread issued has finished before TMEM is freed
+      tc::mma_commit(drain);
+      (void)tc::mbar_wait(drain, 0, 100000000ull);
+    }
+  } else {
+    // ---- epilogue (warps 0-3)
+    uint32_t step = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; ok && u < units; u += gridDim.x) {
+      int s, yb, z0, len;
+      unit_pos(u, s, yb, z0, len);
+      for (int o = 0; o < len; ++o, ++step) {
+        const uint32_t a = step & 1;
+        ok = tc::mbar_wait_or_abort(&tfull[a], (step >> 1) & 1, &abort_flag);
+        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+        if (!ok) {
+          if (lane == 0) {
+            if (!abort_flag) atomicOr(err, 2u);
+            abort_flag = 1;
+          }
+          break;
         }
-      } else {
-        if (zprev) {
-          const float4* zp = (const float4*)(zprev + pt * CH);
+        tc::fence_after_sync();
+        const int z = z0 + o;
+        for (int j = 0; j < P.T; ++j) {
+          float acc[32];
+          tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + a * (uint32_t)(P.T * 32) + (uint32_t)(j * 32), acc);
+          if (j == P.T - 1) {
+            // registers hold the last tile: hand the set back to the MMA warp
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&tempty[a]);
+          }
+          const int e = XS + 128 * j + 32 * warp + lane;
+          const int row = e / XS, x = e - row * XS;
+          const int y = yb * P.R + row - 1;
+          if (x >= G.X || row > P.R || y >= G.Y) continue;
+          const long long pt = (((long long)s * G.Z + z) * G.Y + y) * G.X + x;
+          if (MODE == 0) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const float4 v = __ldg(zp + q);
-            acc[4 * q] *= gelu_grad_f(v.x);
-            acc[4 * q + 1] *= gelu_grad_f(v.y);
-            acc[4 * q + 2] *= gelu_grad_f(v.z);
-            acc[4 * q + 3] *= gelu_grad_f(v.w);
+            for (int c = 0; c < 32; ++c) acc[c] += __ldg(bias + c);
+            if (zout) {
+              float4* zo = (float4*)(zout + pt * CH);
+#pragma unroll
+              for (int q = 0; q < 8; ++q)
+                zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+            }
+            if (act_out) {
+              __align__(16) __nv_bfloat16 h[32];
+#pragma unroll
+              for (int c = 0; c < 32; ++c) h[c] = __float2bfloat16_rn(gelu ? gelu_f(acc[c]) : acc[c]);
+              store_point(G, act_out, s, z, y, x, h);
+            }
+          } else {
+            if (zprev) {
+              const float4* zp = (const float4*)(zprev + pt * CH);
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const float4 v = __ldg(zp + q);
+                acc[4 * q] *= gelu_grad_f(v.x);
+                acc[4 * q + 1] *= gelu_grad_f(v.y);
+                acc[4 * q + 2] *= gelu_grad_f(v.z);
+                acc[4 * q + 3] *= gelu_grad_f(v.w);
+              }
+            }
+            __align__(16) __nv_bfloat16 h[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) h[c] = __float2bfloat16_rn(acc[c]);
+            store_point(G, act_out, s, z, y, x, h);
           }
         }
-        __align__(16) __nv_bfloat16 h[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) h[c] = __float2bfloat16_rn(acc[c]);
-        uint4* dst = (uint4*)(act_out + pp * CH);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) dst[q] = ((const uint4*)h)[q];
       }
     }
-    // every TMEM read of this tile is done before the next tile's first MMA
-    tc::fence_before_sync();
-    const int stop = __syncthreads_or(!ok);
-    tc::fence_after_sync();
-    if (stop) break;
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(taddr, 32);
+  if (warp == 0) tc::tmem_dealloc(taddr, (uint32_t)P.tmem_cols);
 }
 
 // ---------------------------------------------------------------- wgrad
 // D[(q, ci)][co] = sum over this CTA's rows of sum_x act(p + off_{tap q}, ci) g(p, co),
 // tap q = min(4 * group + q, 26); one K step = one x-row of 64 points.
+// Warp-specialised like k_conv_tc: warp 4 streams rows through the TMA ring,
+// warp 5 issues the MMAs without waiting on them, warps 0-3 read the single
+// accumulator out at the end.
 template <int XW>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(CONV_THREADS, 2)
     k_wgrad_tc(const __grid_constant__ CUtensorMap tmXm, const __grid_constant__ CUtensorMap tmX0,
                const __grid_constant__ CUtensorMap tmXp, const __grid_constant__ CUtensorMap tmG, Geom G,
                int rows_per_cta, float* __restrict__ partial, unsigned int* err) {
@@ -269,16 +398,18 @@ __global__ void __launch_bounds__(128, 1)
   uint64_t* empty = bars + WG_STAGES;
   uint64_t* done = bars + 2 * WG_STAGES;
   uint32_t* tslot = (uint32_t*)(done + 1);
-  __shared__ int bad;
+  __shared__ volatile int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int group = blockIdx.y;
+  // the 7 tap groups of one row chunk are neighbouring CTAs, so they run
+  // together and share the chunk's rows in L2
+  const int group = blockIdx.x;
   const long long total_rows = (long long)G.S * G.Z * G.Y;
-  const long long r0 = (long long)blockIdx.x * rows_per_cta;
+  const long long r0 = (long long)blockIdx.y * rows_per_cta;
   const int nrows = (int)(r0 >= total_rows ? 0 : (total_rows - r0 < rows_per_cta ? total_rows - r0 : rows_per_cta));
 
   if (tid == 0) {
-    bad = 0;
+    abort_flag = 0;
     for (int i = 0; i < WG_STAGES; ++i) {
       tc::mbar_init(&full[i], 1);
       tc::mbar_init(&empty[i], 1);
@@ -293,69 +424,85 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t taddr = *tslot;
   constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, 32);
 
-  if (tid == 0 && nrows > 0) {
-    auto load = [&](int k) {
-      const int slot = k % WG_STAGES;
-      const long long R = r0 + k;
-      const int y = (int)(R % G.Y);
-      const long long rz = R / G.Y;
-      const int z = (int)(rz % G.Z);
-      const int s = (int)(rz / G.Z);
-      tc::mbar_expect_tx(&full[slot], W::A_BYTES + W::B_BYTES);
+  if (warp == 4) {
+    // ---- TMA producer: one x-row of activations (4 taps) and gradient per step
+    if (lane == 0 && nrows > 0) {
+      int issued = 0;
+      for (int k = 0; k < nrows; ++k) {
+        const int slot = k % WG_STAGES;
+        if (k >= WG_STAGES && !tc::mbar_wait_or_abort(&empty[slot], ((k / WG_STAGES) - 1) & 1, &abort_flag)) {
+          if (!abort_flag) atomicOr(err, 4u);
+          abort_flag = 1;
+          break;
+        }
+        const long long R = r0 + k;
+        const int y = (int)(R % G.Y);
+        const long long rz = R / G.Y;
+        const int z = (int)(rz % G.Z);
+        const int s = (int)(rz / G.Z);
+        tc::mbar_expect_tx(&full[slot], W::A_BYTES + W::B_BYTES);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int tap = min(4 * group + q, NTAP - 1);
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        const CUtensorMap* tm = dx < 0 ? &tmXm : (dx == 0 ? &tmX0 : &tmXp);
-        tc::tma_load_4d(Ast + slot * W::A_BYTES + q * (CH * W::ROWB), tm, XOFF, y + 1 + dy, s * (G.Z + 2) + z + 1 + dz, 0,
-                        &full[slot]);
+        for (int q = 0; q < 4; ++q) {
+          const int tap = min(4 * group + q, NTAP - 1);
+          const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+          const CUtensorMap* tm = dx < 0 ? &tmXm : (dx == 0 ? &tmX0 : &tmXp);
+          tc::tma_load_4d(Ast + slot * W::A_BYTES + q * (CH * W::ROWB), tm, XOFF, y + 1 + dy,
+                          s * (G.Z + 2) + z + 1 + dz, 0, &full[slot]);
+        }
+        tc::tma_load_4d(Bst + slot * W::B_BYTES, &tmG, XOFF, y + 1, s * (G.Z + 2) + z + 1, 0, &full[slot]);
+        issued = k + 1;
       }
-      tc::tma_load_4d(Bst + slot * W::B_BYTES, &tmG, XOFF, y + 1, s * (G.Z + 2) + z + 1, 0, &full[slot]);
-    };
-    const int pro = nrows < WG_STAGES ? nrows : WG_STAGES;
-    for (int k = 0; k < pro; ++k) load(k);
-    bool ok = true;
-    int issued = pro;
-    for (int k = 0; k < nrows; ++k) {
-      const int slot = k % WG_STAGES;
-      const uint32_t ph = (k / WG_STAGES) & 1;
-      if (!tc::mbar_wait(&full[slot], ph)) { ok = false; break; }
-      tc::fence_after_sync();
-      const uint64_t ad = tc::smem_desc(tc::smem_u32(Ast + slot * W::A_BYTES), 16, W::SBO, W::SWZ);
-      const uint64_t bd = tc::smem_desc(tc::smem_u32(Bst + slot * W::B_BYTES), 16, W::SBO, W::SWZ);
+      // the last use of every slot has landed before the CTA leaves
+      for (int k = issued > WG_STAGES ? issued - WG_STAGES : 0; k < issued; ++k)
+        (void)tc::mbar_wait(&full[k % WG_STAGES], (k / WG_STAGES) & 1, 100000000ull);
+    }
+  } else if (warp == 5) {
+    // ---- MMA issuer: never waits for an MMA, only for data
+    if (lane == 0 && nrows > 0) {
+      bool ok = true;
+      for (int k = 0; k < nrows; ++k) {
+        const int slot = k % WG_STAGES;
+        if (!tc::mbar_wait_or_abort(&full[slot], (k / WG_STAGES) & 1, &abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint64_t ad = tc::smem_desc(tc::smem_u32(Ast + slot * W::A_BYTES), 16, W::SBO, W::SWZ);
+        const uint64_t bd = tc::smem_desc(tc::smem_u32(Bst + slot * W::B_BYTES), 16, W::SBO, W::SWZ);
 #pragma unroll
-      for (int j = 0; j < W::KSTEPS; ++j) tc::mma_bf16(taddr, ad + 2 * j, bd + 2 * j, IDESC, (k > 0 || j > 0) ? 1u : 0u);
-      tc::mma_commit(&empty[slot]);
-      if (k + WG_STAGES < nrows) {
-        if (!tc::mbar_wait(&empty[slot], ph)) { ok = false; break; }
-        load(k + WG_STAGES);
-        issued = k + WG_STAGES + 1;
+        for (int j = 0; j < W::KSTEPS; ++j)
+          tc::mma_bf16(taddr, ad + 2 * j, bd + 2 * j, IDESC, (k > 0 || j > 0) ? 1u : 0u);
+        tc::mma_commit(&empty[slot]);
       }
+      if (!ok) {
+        if (!abort_flag) atomicOr(err, 4u);
+        abort_flag = 1;
+      }
+      // completes once every MMA issued above has finished (also on abort)
+      tc::mma_commit(done);
     }
-    if (!ok) {
-      bad = 1;
-      atomicOr(err, 4u);
-      for (int k = issued - WG_STAGES; k < issued; ++k)
-        if (k >= 0) (void)tc::mbar_wait(&full[k % WG_STAGES], (k / WG_STAGES) & 1, 100000000ull);
-    }
-    tc::mma_commit(done);
   }
-  __syncthreads();
-  const int bad0 = bad;
-  bool ok = !bad0 && nrows > 0 && tc::mbar_wait(done, 0);
-  if (!ok && !bad0 && nrows > 0) atomicOr(err, 8u);
-  ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+  // ---- epilogue (warps 0-3; the other two warps only meet the barriers)
+  bool ok = false;
+  if (warp < 4 && nrows > 0) {
+    ok = tc::mbar_wait(done, 0);
+    if (!ok && lane == 0) atomicOr(err, 8u);
+    ok = ok && !abort_flag;
+    ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+  }
   tc::fence_after_sync();
-  float* out = partial + (((long long)group * gridDim.x + blockIdx.x) * 128 + warp * 32 + lane) * CH;
-  if (ok) {
-    float acc[32];
-    tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16), acc);
+  if (warp < 4) {
+    float* out = partial + (((long long)group * gridDim.y + blockIdx.y) * 128 + warp * 32 + lane) * CH;
+    if (ok) {
+      float acc[32];
+      tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16), acc);
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      ((float4*)out)[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-  } else {
+      for (int q = 0; q < 8; ++q)
+        ((float4*)out)[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    } else {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) ((float4*)out)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int q = 0; q < 8; ++q) ((float4*)out)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -385,10 +532,21 @@ __global__ void k_to_channels_first(Geom G, const __nv_bfloat16* __restrict__ in
     const int xs = (int)(i % xp);
     const int x = xs - XOFF;
     const bool inside = x >= 0 && x < G.X;
-    const long long src = (row * (G.X + 2) + x + 1 + dx) * CH;
-#pragma unroll 4
-    for (int c = 0; c < CH; ++c)
-      out[(long long)c * rows * xp + i] = inside ? in[src + c] : __float2bfloat16_rn(0.f);
+    __align__(16) __nv_bfloat16 v[CH];
+    if (inside) {
+      // row = (s (Z+2) + zz) (Y+2) + yy over padded planes and rows
+      const long long plane = row / (G.Y + 2);
+      const int yy = (int)(row % (G.Y + 2));
+      const uint4* src = (const uint4*)in + (plane * 4 * (G.Y + 2) + yy) * (G.X + 2) + x + 1 + dx;
+      const long long cs = chunk_stride(G);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) ((uint4*)v)[q] = __ldg(src + q * cs);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) ((uint4*)v)[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c) out[(long long)c * rows * xp + i] = v[c];
   }
 }
 
@@ -409,10 +567,11 @@ __global__ void __launch_bounds__(256) k_bias_partial(Geom G, const __nv_bfloat1
     const int y = (int)(r % G.Y);
     const long long r2 = r / G.Y;
     const int z = (int)(r2 % G.Z), s = (int)(r2 / G.Z);
-    const uint4* src = (const uint4*)(g + padded_index(G, s, z, y, x) * CH);
+    const uint4* src = (const uint4*)g + chunk_off(G, s, z + 1, 0, y + 1, x + 1);
+    const long long cs = chunk_stride(G);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const uint4 v = __ldg(src + q);
+      const uint4 v = __ldg(src + q * cs);
       const __nv_bfloat162* h = (const __nv_bfloat162*)&v;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -459,10 +618,7 @@ __global__ void k_pad_copy(Geom G, const __nv_bfloat16* __restrict__ in, __nv_bf
     const int y = (int)(r % G.Y);
     const long long r2 = r / G.Y;
     const int z = (int)(r2 % G.Z), s = (int)(r2 / G.Z);
-    const uint4* src = (const uint4*)(in + i * CH);
-    uint4* dst = (uint4*)(out + padded_index(G, s, z, y, x) * CH);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dst[q] = src[q];
+    store_point(G, out, s, z, y, x, in + i * CH);
   }
 }
 
@@ -475,9 +631,10 @@ __global__ void k_unpad_f32(Geom G, const __nv_bfloat16* __restrict__ in, float*
     const int y = (int)(r % G.Y);
     const long long r2 = r / G.Y;
     const int z = (int)(r2 % G.Z), s = (int)(r2 / G.Z);
-    const __nv_bfloat16* src = in + padded_index(G, s, z, y, x) * CH;
+    __align__(16) __nv_bfloat16 h[CH];
+    load_point(G, in, s, z, y, x, h);
 #pragma unroll 8
-    for (int c = 0; c < CH; ++c) out[i * CH + c] = __bfloat162float(src[c]);
+    for (int c = 0; c < CH; ++c) out[i * CH + c] = __bfloat162float(h[c]);
   }
 }
 
@@ -487,7 +644,7 @@ __global__ void k_unpad_f32(Geom G, const __nv_bfloat16* __restrict__ in, float*
 __global__ void k_mse(Geom G, int nout, const float* __restrict__ out, const float* __restrict__ target,
                       __nv_bfloat16* __restrict__ g, double* __restrict__ part) {
   const long long pts = (long long)G.S * G.Z * G.Y * G.X;
-  const double norm = (double)pts * nout;
+  const float gscale = (float)(2.0 / ((double)pts * nout));  // d loss / d out = 2 (out - target) / (pts nout)
   double acc = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < pts; i += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(i % G.X);
@@ -495,20 +652,26 @@ __global__ void k_mse(Geom G, int nout, const float* __restrict__ out, const flo
     const int y = (int)(r % G.Y);
     const long long r2 = r / G.Y;
     const int z = (int)(r2 % G.Z), s = (int)(r2 / G.Z);
+    __align__(16) float o[CH], t[CH];
+#pragma unroll
+    for (int q = 0; q < CH / 4; ++q) {
+      ((float4*)o)[q] = __ldg((const float4*)(out + i * CH) + q);
+      ((float4*)t)[q] = __ldg((const float4*)(target + i * CH) + q);
+    }
     __align__(16) __nv_bfloat16 h[32];
+    float sq = 0.f;  // this point's sum of squares (at most 32 terms)
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
       float gv = 0.f;
       if (c < nout) {
-        const float d = out[i * CH + c] - target[i * CH + c];
-        acc += (double)d * d;
-        gv = (float)(2.0 * d / norm);
+        const float d = o[c] - t[c];
+        sq = fmaf(d, d, sq);
+        gv = d * gscale;
       }
       h[c] = __float2bfloat16_rn(gv);
     }
-    uint4* dst = (uint4*)(g + padded_index(G, s, z, y, x) * CH);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dst[q] = ((const uint4*)h)[q];
+    acc += (double)sq;
+    store_point(G, g, s, z, y, x, h);
   }
   __shared__ double sh[256];
   sh[threadIdx.x] = acc;
@@ -559,9 +722,7 @@ __global__ void k_pack_state(Geom G, Layout L, int s, const double* __restrict__
 #pragma unroll
     for (int c = 0; c < CH; ++c)
       h[c] = __float2bfloat16_rn(c < NV ? (float)((u[c * L.vs + p] - coef[c]) * coef[NV + c]) : 0.f);
-    uint4* dst = (uint4*)(act + padded_index(G, s, z, y, x) * CH);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dst[q] = ((const uint4*)h)[q];
+    store_point(G, act, s, z, y, x, h);
   }
 }
 
@@ -627,6 +788,47 @@ __global__ void k_apply(Geom G, Layout L, const float* __restrict__ out, const d
   }
 }
 
+// ---------------------------------------------------------------- MMA rate probe
+// Back-to-back kind::f16 MMAs (M = 128, K = 16, N = NC) on fixed no-swizzle
+// operands in shared memory, one CTA per SM: the instruction-rate ceiling of
+// the shapes the convolutions issue (N = 32 output channels).
+constexpr int PROBE_A = 128 * 32, PROBE_B = 256 * 32, PROBE_SMEM = 1024 + PROBE_A + PROBE_B + 256;
+
+template <int NC>
+__global__ void __launch_bounds__(128, 1) k_mma_rate(int iters, unsigned long long* ns, unsigned int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bar = (uint64_t*)(base + PROBE_A + PROBE_B);
+  uint32_t* slot = (uint32_t*)(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int i = tid; i < (PROBE_A + PROBE_B) / 4; i += blockDim.x) ((uint32_t*)base)[i] = 0x3c003c00u;
+  tc::fence_proxy_async();
+  if (tid == 0) {
+    tc::mbar_init(bar, 1);
+    tc::mbar_fence_init();
+  }
+  if (warp == 0) tc::tmem_alloc(slot, 256);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = *slot;
+  if (tid == 0) {
+    // A 128 x 16 and B NC x 16, K-major, core matrices 8 rows x 16 bytes
+    const uint64_t ad = tc::smem_desc(tc::smem_u32(base), 2048, 128, tc::SWZ_NONE);
+    const uint64_t bd = tc::smem_desc(tc::smem_u32(base + PROBE_A), NC * 16, 128, tc::SWZ_NONE);
+    constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, NC);
+    const uint64_t t0 = tc::global_ns();
+    for (int i = 0; i < iters; ++i) tc::mma_bf16(taddr, ad, bd, IDESC, i ? 1u : 0u);
+    tc::mma_commit(bar);
+    const bool ok = tc::mbar_wait(bar, 0);
+    ns[blockIdx.x] = tc::global_ns() - t0;
+    if (!ok) atomicOr(err, 1u);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(taddr, 256);
+}
+
 // ---------------------------------------------------------------- host helpers
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -645,18 +847,22 @@ bool encode(CUtensorMap* tm, void* ptr, int rank, const cuuint64_t* dims, const 
             const cuuint32_t* box, CUtensorMapSwizzle swz) {
   auto fn = encode_fn();
   if (!fn) return false;
-  cuuint32_t es[4] = {1, 1, 1, 1};
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
   return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, ptr, dims, strides_bytes, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// channels-last padded activation map: dims {32, X+2, Y+2, S(Z+2)}, box {32, X, rpt, 1}, 64B swizzle
-bool map_act(CUtensorMap* tm, void* ptr, const Geom& G) {
-  const cuuint64_t dims[4] = {CH, (cuuint64_t)G.X + 2, (cuuint64_t)G.Y + 2, (cuuint64_t)G.S * (G.Z + 2)};
-  const cuuint64_t str[3] = {CH * 2, (cuuint64_t)CH * 2 * (G.X + 2), (cuuint64_t)CH * 2 * (G.X + 2) * (G.Y + 2)};
-  const cuuint32_t box[4] = {CH, (cuuint32_t)G.X, (cuuint32_t)G.rpt, 1};
-  return encode(tm, ptr, 4, dims, str, box, CU_TENSOR_MAP_SWIZZLE_64B);
+// Padded chunk-major activations as a 5D tensor {8 channels, X+2, Y+2, 4
+// chunks, S (Z+2) planes}; box {8, X+1, R+2, 4, 1} = one convolution slab
+// (rows y0-1 .. y0+R of one plane, points x = 0 .. X including the zero pad
+// at x = X), no swizzle: in shared memory [chunk][row][x][8 channels].
+bool map_slab(CUtensorMap* tm, void* ptr, const Geom& G, int R) {
+  const cuuint64_t dims[5] = {8, (cuuint64_t)G.X + 2, (cuuint64_t)G.Y + 2, 4, (cuuint64_t)G.S * (G.Z + 2)};
+  const cuuint64_t row = 16ull * (G.X + 2), chunk = row * (G.Y + 2);
+  const cuuint64_t str[4] = {16, row, chunk, 4 * chunk};
+  const cuuint32_t box[5] = {8, (cuuint32_t)G.X + 1, (cuuint32_t)R + 2, 4, 1};
+  return encode(tm, ptr, 5, dims, str, box, CU_TENSOR_MAP_SWIZZLE_NONE);
 }
 
 // weights [27*32 rows][32]: box {32, 32}, 64B swizzle
@@ -703,7 +909,8 @@ struct bssn_corrector {
   double* coef = nullptr;        // in_offset[24], in_scale[24], out_scale[24]
   unsigned int* err = nullptr;
   int wg_blocks = 0, rows_per_cta = 0;
-  int conv_grid = 0;  // persistent conv grid: resident CTAs per SM x SMs
+  int sms = 0;        // streaming multiprocessors (one conv CTA each)
+  ConvPlan conv{};    // slab geometry of the convolutions (R, T, sizes)
   long long adam_t = 0;
 };
 
@@ -729,19 +936,67 @@ Geom geom_for(const bssn_corrector* c, int S) {
   return G;
 }
 
-// persistent conv grid for G: every tile once, at most conv_grid CTAs
-int conv_blocks(const bssn_corrector* c, const Geom& G) {
-  const int tiles = G.S * G.Z * (G.Y / G.rpt);
-  return tiles < c->conv_grid ? tiles : c->conv_grid;
+// Slab geometry for an X-wide grid: the row count R whose R (X+1) output
+// entries fill the T 128-entry tiles best, with four slabs, the weights and
+// the tail within the shared-memory limit, T <= 8 (two accumulator sets in
+// 512 TMEM columns) and 128-byte aligned slabs. Returns false if none fits.
+bool make_conv_plan(int X, int Y, ConvPlan* out) {
+  const int XS = X + 1;
+  double best = -1.0;
+  for (int R = 1; R <= Y; ++R) {
+    ConvPlan P{};
+    P.R = R;
+    P.T = (R * XS + 127) / 128;
+    P.chunk_bytes = (R + 2) * XS * 16;
+    P.plane_bytes = 4 * P.chunk_bytes;
+    if (P.T > 8 || P.plane_bytes % 128) continue;
+    const int over = XS + 128 * P.T + XS + 1 - (R + 2) * XS;  // entries read past a slab (discarded rows)
+    P.tail_bytes = over > 0 ? (over * 16 + 127) / 128 * 128 : 0;
+    P.slab_off = NTAP * W_TAP_BYTES + 128;
+    P.bar_off = P.slab_off + SLABS * P.plane_bytes + P.tail_bytes;
+    P.smem = 1024 + P.bar_off + 256;
+    int cols = 32;
+    while (cols < 2 * P.T * 32) cols *= 2;
+    P.tmem_cols = cols;
+    if (P.smem > 232448) continue;
+    const double eff = (double)R * X / (P.T * 128.0);
+    if (eff >= best) {
+      best = eff;
+      *out = P;
+    }
+  }
+  return best > 0.0;
+}
+
+// Work units for S samples: (sample, row block, run of L planes); L picked
+// so that ceil(units / SMs) (L + 1/2) is smallest. Returns the grid size.
+int conv_units(const bssn_corrector* c, const Geom& G, ConvPlan* P) {
+  *P = c->conv;
+  P->nyb = (G.Y + P->R - 1) / P->R;
+  double best = 1e300;
+  for (int L = 1; L <= G.Z; ++L) {
+    const long long units = (long long)G.S * P->nyb * ((G.Z + L - 1) / L);
+    const double cost = (double)((units + c->sms - 1) / c->sms) * (L + 0.5);
+    if (cost < best) {
+      best = cost;
+      P->L = L;
+    }
+  }
+  P->nzs = (G.Z + P->L - 1) / P->L;
+  const long long units = (long long)G.S * P->nyb * P->nzs;
+  return (int)(units < c->sms ? units : c->sms);
 }
 
 // one layer forward on act[l] (sample count in G) -> z[l] and act[l+1]
 cudaError_t layer_forward(bssn_corrector* c, const Geom& G, int l, float* zout, __nv_bfloat16* act_out, int gelu,
                           cudaStream_t s) {
   CUtensorMap ta, tw;
-  if (!map_act(&ta, c->act[l], G) || !map_w(&tw, c->wf + (size_t)l * NTAP * CH * CH)) return cudaErrorInvalidValue;
+  if (!map_slab(&ta, c->act[l], G, c->conv.R) || !map_w(&tw, c->wf + (size_t)l * NTAP * CH * CH))
+    return cudaErrorInvalidValue;
+  ConvPlan P;
+  const int grid = conv_units(c, G, &P);
   const float* bias = c->params + (size_t)l * LAYER_PARAMS + NTAP * CH * CH;
-  k_conv_tc<0><<<conv_blocks(c, G), 128, CONV_SMEM, s>>>(ta, tw, G, bias, zout, act_out, nullptr, gelu, c->err);
+  k_conv_tc<0><<<grid, CONV_THREADS, P.smem, s>>>(ta, tw, G, P, bias, zout, act_out, nullptr, gelu, c->err);
   return cudaGetLastError();
 }
 
@@ -778,9 +1033,11 @@ cudaError_t network_backward(bssn_corrector* c, const Geom& G, cudaStream_t s) {
     if (!map_cf(&tg, c->cfg, G, c->xp)) return cudaErrorInvalidValue;
     if (e == cudaSuccess) {
       if (G.X == 64)
-        k_wgrad_tc<64><<<dim3(nb, 7), 128, WG<64>::SMEM, s>>>(tm[0], tm[1], tm[2], tg, G, rpc, c->partial, c->err);
+        k_wgrad_tc<64><<<dim3(7, nb), CONV_THREADS, WG<64>::SMEM, s>>>(tm[0], tm[1], tm[2], tg, G, rpc, c->partial,
+                                                                       c->err);
       else
-        k_wgrad_tc<32><<<dim3(nb, 7), 128, WG<32>::SMEM, s>>>(tm[0], tm[1], tm[2], tg, G, rpc, c->partial, c->err);
+        k_wgrad_tc<32><<<dim3(7, nb), CONV_THREADS, WG<32>::SMEM, s>>>(tm[0], tm[1], tm[2], tg, G, rpc, c->partial,
+                                                                       c->err);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
@@ -794,10 +1051,12 @@ cudaError_t network_backward(bssn_corrector* c, const Geom& G, cudaStream_t s) {
     }
     if (e == cudaSuccess && l > 0) {
       CUtensorMap ta, tw;
-      if (!map_act(&ta, c->g[cur], G) || !map_w(&tw, c->wb + (size_t)l * NTAP * CH * CH))
+      if (!map_slab(&ta, c->g[cur], G, c->conv.R) || !map_w(&tw, c->wb + (size_t)l * NTAP * CH * CH))
         return cudaErrorInvalidValue;
-      k_conv_tc<1><<<conv_blocks(c, G), 128, CONV_SMEM, s>>>(ta, tw, G, nullptr, nullptr, c->g[1 - cur], c->z[l - 1], 0,
-                                                             c->err);
+      ConvPlan P;
+      const int grid = conv_units(c, G, &P);
+      k_conv_tc<1><<<grid, CONV_THREADS, P.smem, s>>>(ta, tw, G, P, nullptr, nullptr, c->g[1 - cur], c->z[l - 1], 0,
+                                                      c->err);
       e = cudaGetLastError();
       cur = 1 - cur;
     }
@@ -851,7 +1110,7 @@ bssn_status_t bssn_corrector_create(bssn_corrector_t** out, int n, int max_batch
   if (!c) return BSSN_ERR_NOMEM;
   c->n = n;
   c->max_batch = max_batch;
-  c->G = Geom{max_batch, n, n, n, 128 / n};
+  c->G = Geom{max_batch, n, n, n};
   c->xp = n + 16;
   c->pts = (long long)max_batch * n * n * n;
   c->pad_pts = (long long)max_batch * (n + 2) * (n + 2) * (n + 2);
@@ -901,18 +1160,26 @@ bssn_status_t bssn_corrector_create(bssn_corrector_t** out, int n, int max_batch
   c->coef = (double*)p;
   if (e == cudaSuccess) e = calloc_dev(c, sizeof(unsigned int), &p);
   c->err = (unsigned int*)p;
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM);
+  if (e == cudaSuccess && !make_conv_plan(n, n, &c->conv)) e = cudaErrorInvalidValue;
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_conv_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->conv.smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->conv.smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_wgrad_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, WG<64>::SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_wgrad_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, WG<32>::SMEM);
+  // the tensor-core kernels run two CTAs per SM: ask for the full carveout
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_tc<0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_wgrad_tc<64>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_wgrad_tc<32>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess) {
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0;
     e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<0>, 128, CONV_SMEM);
-    c->conv_grid = sms * (per_sm > 0 ? per_sm : 1);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
   }
   // seeded initialisation: uniform in +-sqrt(6 / fan_in) (real fan-in), the
   // last layer scaled by 0.1 so the initial correction is small; biases 0;
@@ -1128,6 +1395,42 @@ bssn_status_t bssn_corrector_apply(bssn_corrector_t* c, const bssn_grid_t* grid,
     e = cudaGetLastError();
   }
   return status_of(c, e, s);
+}
+
+// Measured dense BF16 rate (TFLOP/s, all SMs) of back-to-back M=128 K=16
+// tcgen05 MMAs with N = n (32, 64, 128 or 256) columns.
+bssn_status_t bssn_probe_mma_rate(int n, double* tflops) {
+  if (!tflops || (n != 32 && n != 64 && n != 128 && n != 256)) return BSSN_ERR_INVALID_ARG;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return BSSN_ERR_CUDA;
+  void (*kern)(int, unsigned long long*, unsigned int*) =
+      n == 32 ? k_mma_rate<32> : n == 64 ? k_mma_rate<64> : n == 128 ? k_mma_rate<128> : k_mma_rate<256>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, PROBE_SMEM);
+  unsigned long long* ns = nullptr;
+  unsigned int* err = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&ns, sizeof(unsigned long long) * sms);
+  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(unsigned int));
+  const int iters = 4096;
+  std::vector<unsigned long long> h(sms);
+  unsigned int herr = 0;
+  for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first launch warms up
+    kern<<<sms, 128, PROBE_SMEM>>>(iters, ns, err);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(h.data(), ns, sizeof(unsigned long long) * sms, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof(unsigned int), cudaMemcpyDeviceToHost);
+  cudaFree(ns);
+  cudaFree(err);
+  if (e != cudaSuccess) return BSSN_ERR_CUDA;
+  if (herr) return BSSN_ERR_TIMEOUT;
+  unsigned long long mx = 1;
+  for (unsigned long long v : h) mx = v > mx ? v : mx;
+  *tflops = 2.0 * 128.0 * n * 16.0 * iters * sms / (mx * 1e-9) / 1e12;
+  return BSSN_OK;
 }
 
 }  // extern "C"

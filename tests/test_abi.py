@@ -142,3 +142,11 @@ def test_transfer_rejects_invalid_arguments(L):
     p = lambda c, f: L.bssn_prolong(ctypes.byref(c), fake, ctypes.byref(f), ctypes.c_void_p(8192), None)
     assert p(gc1, gf) == B.ERR_INVALID_ARG  # coarse ghost < 2
     assert p(gc, odd) == B.ERR_INVALID_ARG
+
+
+def test_mma_rate_probe_rejects_bad_width(L):
+    L.bssn_probe_mma_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    out = ctypes.c_double()
+    for n in (0, 16, 48, 512):
+        assert L.bssn_probe_mma_rate(n, ctypes.byref(out)) == B.ERR_INVALID_ARG
+    assert L.bssn_probe_mma_rate(32, None) == B.ERR_INVALID_ARG
