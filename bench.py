@@ -240,7 +240,7 @@ def run_gpu(args):
     yb = B.alloc_state(grid, device=dev)
     acc = B.alloc_state(grid, device=dev)
     work = B.alloc_work(grid, p, device=dev)
-    rates = None if args.profile else B.probe_fp_rates()
+    rates = None if (args.profile or args.corrector_only) else B.probe_fp_rates()
 
     def run_form(prec, sample_clocks):
         state = state0.clone()
@@ -333,6 +333,66 @@ def run_gpu(args):
                 "tile_shapes_chosen": np.bincount(shapes, minlength=7).tolist(), "plan_create_s": t_tune,
                 "fd_order": 4, "dt": dtb, "graph_launches_per_step": 1,
                 "kernel_nodes_per_step": 13 if prec == B.FP64 else 17}
+
+    def run_fp32_config():
+        """FP32-RHS against FP64 as stated for that form: throughput of both at
+        256^3 (same Brill-Lindquist data, 8th order, g = 5; state 3.6 GB per
+        copy), and the accuracy of FP32 against FP64 after 100 RK4 steps at
+        96^3 (per-variable max relative error, per-tensor error and the
+        Hamiltonian-constraint L2 of each)."""
+        out = {}
+        for nn, nsteps in ((256, max(1, min(args.steps, 5))),):
+            un, hn = inputs.brill_lindquist(nn, G, lo=LO, hi=HI)
+            gn = B.make_grid(nn, ghost=G, dx=hn)
+            src = B.upload(un, gn, device=dev)
+            del un
+            bufs = torch.empty(3 * 24 * gn.var_stride, dtype=torch.float64, device=dev)
+            wk = B.alloc_work(gn, p, device=dev)
+            for name, prec in (("fp64", B.FP64), ("fp32_rhs", B.FP32_RHS)):
+                st = src.clone()
+                for _ in range(2):
+                    B.rk4_step(gn, p, prec, 0.25 * hn, 1, src, st, bufs, wk)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(nsteps):
+                    B.rk4_step(gn, p, prec, 0.25 * hn, 1, src, st, bufs, wk)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / nsteps
+                out[f"{name}_{nn}^3"] = {"value": nn ** 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                                         "steps": nsteps}
+                del st
+            del src, bufs, wk
+            torch.cuda.empty_cache()
+        out["fp32_speedup_256^3"] = out["fp32_rhs_256^3"]["value"] / out["fp64_256^3"]["value"]
+        na, nst = 96, 100
+        ua, ha = inputs.brill_lindquist(na, G, lo=LO, hi=HI)
+        ga = B.make_grid(na, ghost=G, dx=ha)
+        src = B.upload(ua, ga, device=dev)
+        bufs = torch.empty(3 * 24 * ga.var_stride, dtype=torch.float64, device=dev)
+        wk = B.alloc_work(ga, p, device=dev)
+        res = {}
+        for name, prec in (("fp64", B.FP64), ("fp32_rhs", B.FP32_RHS)):
+            st = src.clone()
+            for _ in range(nst):
+                B.rk4_step(ga, p, prec, 0.25 * ha, 1, src, st, bufs, wk)
+            torch.cuda.synchronize()
+            l2, mx, _ = B.constraints(ga, p, st, wk)
+            res[name] = (B.download(st, ga), float(l2[0]))
+        a, b = res["fp32_rhs"][0], res["fp64"][0]
+        ai = a[:, G:-G, G:-G, G:-G].reshape(24, -1)
+        bi = b[:, G:-G, G:-G, G:-G].reshape(24, -1)
+        per_var = np.max(np.abs(ai - bi), axis=1) / np.maximum(np.max(np.abs(bi), axis=1), 1e-300)
+        out["accuracy_96^3_100_steps"] = {
+            "max_rel_per_variable": {v: float(e) for v, e in zip(inputs.VARS, per_var)},
+            "max_rel_per_tensor": float(np.max(tensor_rel_err(a, b, G))),
+            "ham_l2_fp64": res["fp64"][1], "ham_l2_fp32_rhs": res["fp32_rhs"][1],
+            "reference": "the GPU FP64 path (oracle-matched to 1e-12 per right-hand side)"}
+        del src, bufs, wk, res
+        torch.cuda.empty_cache()
+        return out
 
     def run_learned():
         """Learned half-resolution evolution: train the corrector on pairs the
@@ -475,6 +535,44 @@ def run_gpu(args):
                           "3^3, 32 channels, GELU, BF16 tcgen05 with FP32 accumulation; fallback if H L2 > 2x "
                           "plain coarse"}
 
+    if args.corrector_only:
+        # the network's kernels alone on seeded packed data (64^3, batch 4):
+        # Adam training steps and single-sample forward passes; for ncu
+        nc, S = 64, 4
+        corr = B.corrector_create(nc, S, seed=1)
+        try:
+            gen = torch.Generator(device=dev).manual_seed(0)
+            xs = [torch.randn((nc ** 3, 32), device=dev, generator=gen).to(torch.bfloat16) for _ in range(S)]
+            ts = [(0.1 * torch.randn((nc ** 3, 32), device=dev, generator=gen)).to(torch.bfloat16) for _ in range(S)]
+            for x, t in zip(xs, ts):
+                x[:, 24:] = 0
+                t[:, 24:] = 0
+            out = torch.empty((nc ** 3, 32), dtype=torch.float32, device=dev)
+            for _ in range(args.warmup):
+                B.corrector_train_step_raw(corr, xs, ts, 1e-4)
+                B.corrector_forward_raw(corr, 1, xs[0], out)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                B.corrector_train_step_raw(corr, xs, ts, 1e-4)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_train = e0.elapsed_time(e1) / args.steps
+            e0.record(stream)
+            for _ in range(args.steps):
+                B.corrector_forward_raw(corr, 1, xs[0], out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_fwd = e0.elapsed_time(e1) / args.steps
+        finally:
+            B.corrector_destroy(corr)
+        if rank == 0:
+            print(json.dumps({"corrector_only": f"{nc}^3", "batch": S, "ms_per_train_step": ms_train,
+                              "ms_per_forward_1_sample": ms_fwd}))
+        return
+
     f64 = run_form(B.FP64, not args.profile)
     f32 = run_form(B.FP32_RHS, False)
     if args.profile:
@@ -487,6 +585,8 @@ def run_gpu(args):
     if not args.no_batched:
         batched["batched_fp64"] = run_batched(B.FP64)
         batched["batched_fp32_rhs"] = run_batched(B.FP32_RHS)
+    if not args.no_fp32_config:
+        batched["fp32_rhs_vs_fp64"] = run_fp32_config()
     if not args.no_learned:
         batched["learned_64_from_128"] = run_learned()
 
@@ -572,9 +672,13 @@ def main():
     ap.add_argument("--grid", type=int, default=N, help="interior points per axis (profiling: smaller cases)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 192-patch batched workload")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-corrector form")
+    ap.add_argument("--no-fp32-config", action="store_true",
+                    help="skip the FP32-RHS 256^3 throughput and 96^3 100-step accuracy runs")
     ap.add_argument("--learned-pairs", type=int, default=200,
                     help="training pairs for the learned form (10 per fine trajectory; the full set is 2000)")
     ap.add_argument("--learned-epochs", type=int, default=20)
+    ap.add_argument("--corrector-only", action="store_true",
+                    help="only the learned corrector's kernels (training steps and forward passes, 64^3): for ncu")
     ap.add_argument("--profile", action="store_true",
                     help="only the FP64 and FP32 timed loops (no probe, e2e, CPU leg): for ncu captures")
     args = ap.parse_args()

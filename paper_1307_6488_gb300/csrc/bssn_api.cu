@@ -111,15 +111,17 @@ WorkPtrs work_ptrs(void* work, const bssn_grid_t& G, const bssn_params_t& P, bss
 }
 
 // Difference tables of ys (for the FP32 form: first the single-precision copy).
-cudaError_t run_diffs(int order, bssn_precision_t prec, const Layout& L, const double* ys, const WorkPtrs& w,
+cudaError_t run_diffs(int order, bssn_precision_t prec, const bssn_grid_t& G, const double* ys, const WorkPtrs& w,
                       cudaStream_t s) {
+  const Layout L = make_layout(G);
   const void* src = ys;
   if (prec == BSSN_FP32_RHS) {
     cudaError_t e = launch_to_f32(L, ys, w.f32, s);
     if (e != cudaSuccess) return e;
     src = w.f32;
   }
-  return order == 4 ? launch_diffs<4>(L, prec, src, w.dX, w.dY, s) : launch_diffs<8>(L, prec, src, w.dX, w.dY, s);
+  return order == 4 ? launch_diffs<4>(L, G, prec, src, w.dX, w.dY, s)
+                    : launch_diffs<8>(L, G, prec, src, w.dX, w.dY, s);
 }
 
 cudaError_t run_fused(int order, bssn_precision_t prec, const bssn_grid_t& G, const bssn_params_t& P, const RK& rk,
@@ -135,7 +137,7 @@ cudaError_t run_fused(int order, bssn_precision_t prec, const bssn_grid_t& G, co
 cudaError_t run_stage(int order, bssn_precision_t prec, const bssn_grid_t& G, const bssn_params_t& P, const RK& rk,
                       const double* ys, const double* y0, double* acc, double* out, const WorkPtrs& w, int mode,
                       cudaStream_t s) {
-  cudaError_t e = run_diffs(order, prec, make_layout(G), ys, w, s);
+  cudaError_t e = run_diffs(order, prec, G, ys, w, s);
   if (e != cudaSuccess) return e;
   return run_fused(order, prec, G, P, rk, ys, y0, acc, out, w, mode, s);
 }
@@ -307,7 +309,7 @@ bssn_status_t bssn_diff_tables(const bssn_grid_t* grid, const bssn_params_t* par
   if (!aligned16(state) || !aligned16(work)) return BSSN_ERR_INVALID_ARG;
   if (work_bytes < work_layout(*grid, *params).total_bytes) return BSSN_ERR_INVALID_ARG;
   const WorkPtrs w = work_ptrs(work, *grid, *params, prec);
-  return latch(run_diffs(params->fd_order, prec, make_layout(*grid), state, w, (cudaStream_t)stream));
+  return latch(run_diffs(params->fd_order, prec, *grid, state, w, (cudaStream_t)stream));
 }
 
 bssn_status_t bssn_rk4_stage_fused(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec,
@@ -363,7 +365,7 @@ bssn_status_t bssn_constraints(const bssn_grid_t* grid, const bssn_params_t* par
   const Layout L = make_layout(*grid);
   const WorkPtrs w = work_ptrs(work, *grid, *params, BSSN_FP64);
   cudaError_t e = cudaMemsetAsync(w.flag, 0, sizeof(unsigned int), s);
-  if (e == cudaSuccess) e = run_diffs(params->fd_order, BSSN_FP64, L, state, w, s);
+  if (e == cudaSuccess) e = run_diffs(params->fd_order, BSSN_FP64, *grid, state, w, s);
   if (e == cudaSuccess) {
     if (params->fd_order == 4)
       e = launch_constraints<4>(L, make_coef<4, double>(*grid, 0.0), state, w.dX64, w.dY64, ham, mom, gcon, w.part,

@@ -138,14 +138,19 @@ __global__ void __launch_bounds__(256) kb_diffs(const PatchDev* __restrict__ P, 
     const R* u = stencil_src<R>(D, which);
     R* dX = (R*)D.dX;
     R* dY = (R*)D.dY;
+    if constexpr (std::is_same<R, float>::value) {
+      // FP32-RHS form: first-derivative tables (see k_d1tab)
+      d1tab_point<PO>(D.c32, u, L.vs, L.sy, p, doy, dX, dY);
+    } else {
 #pragma unroll 1
-    for (int m = 0; m < NM; ++m) {
-      const R* v = u + mvar(m) * L.vs;
+      for (int m = 0; m < NM; ++m) {
+        const R* v = u + mvar(m) * L.vs;
 #pragma unroll
-      for (int a = 1; a <= H; ++a) {
-        const long long o = (long long)(m * H + a - 1) * L.vs + p;
-        dX[o] = __ldg(v + p + a) - __ldg(v + p - a);
-        if (doy) dY[o] = __ldg(v + p + a * L.sy) - __ldg(v + p - a * L.sy);
+        for (int a = 1; a <= H; ++a) {
+          const long long o = (long long)(m * H + a - 1) * L.vs + p;
+          dX[o] = __ldg(v + p + a) - __ldg(v + p - a);
+          if (doy) dY[o] = __ldg(v + p + a * L.sy) - __ldg(v + p - a * L.sy);
+        }
       }
     }
   }
@@ -154,7 +159,7 @@ __global__ void __launch_bounds__(256) kb_diffs(const PatchDev* __restrict__ P, 
 // Fused stage over the flat tile list: tile t -> patch, tile coordinates,
 // one point per thread.
 template <int PO, typename R>
-__global__ void __launch_bounds__(TILE_THREADS) kb_stage(const PatchDev* __restrict__ P,
+__global__ void __launch_bounds__(TILE_THREADS, stage_min_blocks<R>()) kb_stage(const PatchDev* __restrict__ P,
                                                         const long long* __restrict__ tile0, int np, long long ntiles,
                                                         Gauge gz, RK rk, int in, int out) {
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {

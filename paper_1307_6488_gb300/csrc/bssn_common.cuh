@@ -26,6 +26,8 @@ enum Var : int {
 // variable mvar(m).
 constexpr int NM = 11;
 __host__ __device__ constexpr int mvar(int m) { return m < 7 ? m : m + 10; }
+// Inverse of mvar: the table slot of variable v, or -1.
+__host__ __device__ constexpr int mixed_index(int v) { return v < 7 ? v : (v >= 17 && v <= 20 ? v - 10 : -1); }
 
 // Packed index of the symmetric pair (i, j): 11 12 13 22 23 33.
 __host__ __device__ constexpr int sym(int i, int j) {

@@ -28,6 +28,15 @@
 // neighbours are read through the L1/L2 caches; the first-difference tables
 // play the role of its "RHS derivatives" arrays (Sec. 2.3, loop fission).
 #pragma once
+#include <type_traits>
+
+#ifndef STAGE_F32_TILE_X
+#define STAGE_F32_TILE_X 32
+#endif
+#ifndef STAGE_F32_MIN_BLOCKS
+#define STAGE_F32_MIN_BLOCKS 4
+#endif
+
 #include "bssn_common.cuh"
 #include "bssn_point.cuh"
 
@@ -87,6 +96,47 @@ __global__ void __launch_bounds__(256) k_diffs(Layout L, const R* __restrict__ u
       if (doy) dY[o] = __ldg(v + p + a * L.sy) - __ldg(v + p - a * L.sy);
     }
   }
+}
+
+// First-derivative tables of the FP32-RHS form: dX[m] = D_x u, dY[m] = D_y u
+// of mixed variable m (full 1D first derivatives, not differences), over the
+// same points as the difference tables (y and z extended by H for the mixed
+// stencils, dY on interior y only). Its mixed derivatives are then 1D first
+// derivatives of these tables, which is accurate to FP32 rounding; the FP64
+// form keeps the exact-difference grouping instead.
+template <int P>
+__device__ __forceinline__ void d1tab_point(const Coef<float>& C, const float* __restrict__ u, long long vs,
+                                            long long sy, long long p, bool doy, float* __restrict__ dX,
+                                            float* __restrict__ dY) {
+  constexpr int H = FD<P>::H;
+#pragma unroll 1
+  for (int m = 0; m < NM; ++m) {
+    const float* v = u + mvar(m) * vs;
+    float rx = C.c1[0][1] * (__ldg(v + p + 1) - __ldg(v + p - 1));
+#pragma unroll
+    for (int a = 2; a <= H; ++a) rx = fmaf(C.c1[0][a], __ldg(v + p + a) - __ldg(v + p - a), rx);
+    dX[m * vs + p] = rx;
+    if (doy) {
+      float ry = C.c1[1][1] * (__ldg(v + p + sy) - __ldg(v + p - sy));
+#pragma unroll
+      for (int a = 2; a <= H; ++a) ry = fmaf(C.c1[1][a], __ldg(v + p + a * sy) - __ldg(v + p - a * sy), ry);
+      dY[m * vs + p] = ry;
+    }
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_d1tab(Layout L, Coef<float> C, const float* __restrict__ u,
+                                               float* __restrict__ dX, float* __restrict__ dY) {
+  constexpr int H = FD<P>::H;
+  const long long ex = L.nx, ey = L.ny + 2 * H, ez = L.nz + 2 * H;
+  const long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (lin >= ex * ey * ez) return;
+  const int i = (int)(lin % ex);
+  const long long t = lin / ex;
+  const int j = (int)(t % ey) - H;
+  const int k = (int)(t / ey) - H;
+  d1tab_point<P>(C, u, L.vs, L.sy, L.off0 + i + j * L.sy + k * L.sz, j >= 0 && j < L.ny, dX, dY);
 }
 
 // first derivative along a stride from the state: sum_a c_a (u_a - u_-a)
@@ -254,6 +304,128 @@ __device__ __forceinline__ void gather(const Layout& L, const Coef<R>& C, const 
   }
 }
 
+// FP32-RHS gather. Every variable's line u(p + a s_d), |a| <= r (r = p/2 + 1),
+// is loaded once per axis and feeds the first derivative, the diagonal second
+// derivative, the Kreiss-Oliger term and the upwinded advection (stencil
+// chosen by the sign of beta^d through selects, mirrored for beta^d < 0).
+// Mixed derivatives are first derivatives of the D_x / D_y tables (k_d1tab).
+// About 1000 loads per point instead of the ~2450 of the exact-grouped gather.
+template <int P, bool WITH_KO, bool WITH_ADV>
+__device__ __forceinline__ void gather_lines(const Layout& L, const Coef<float>& C, const float* __restrict__ u,
+                                             const float* __restrict__ dX, const float* __restrict__ dY,
+                                             long long p, PointIn<float>& Q, float* ko_out) {
+  using F = FD<P>;
+  constexpr int H = F::H, RR = F::R;
+  const long long vs = L.vs;
+  const long long st[3] = {1, L.sy, L.sz};
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Q.u[v] = __ldg(u + v * vs + p);
+  bool neg[3];
+  float ab[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float b = Q.u[V_BETA1 + d];
+    neg[d] = negative_bits(b);
+    ab[d] = abs_bits(b);
+  }
+
+#pragma unroll 1
+  for (int var = 0; var < NV; ++var) {
+    const float* v = u + var * vs;
+    const float u0 = Q.u[var];
+    const float m2u0 = -2.f * u0;
+    const int m = mixed_index(var);  // 0..10, or -1
+    const bool need_d1 = m >= 0 || var == V_TRK || (var >= V_GAM1 && var <= V_GAM3);
+    float d1v[3], d2v[3], ko = 0.f, adv = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float lp[RR + 1], lm[RR + 1];
+#pragma unroll
+      for (int a = 1; a <= RR; ++a) {
+        lp[a] = __ldg(v + p + a * st[d]);
+        lm[a] = __ldg(v + p - a * st[d]);
+      }
+      float r1 = C.c1[d][1] * (lp[1] - lm[1]);
+#pragma unroll
+      for (int a = 2; a <= H; ++a) r1 = fmaf(C.c1[d][a], lp[a] - lm[a], r1);
+      d1v[d] = r1;
+      float dd = 0.f;
+#pragma unroll
+      for (int a = 1; a <= RR; ++a) {
+        const float sa = (lp[a] + lm[a]) + m2u0;
+        if (a <= H) dd = fmaf(C.c2[d][a], sa, dd);
+        if (WITH_KO) ko = fmaf(C.ko[d][a], sa, ko);
+      }
+      d2v[d] = dd;
+      if (WITH_ADV) {
+        // value at signed offset o along the upwind direction
+        float w = 0.f;
+#pragma unroll
+        for (int i = 0; i < F::UPN; ++i) {
+          const int o = F::UPLO + i;
+          const float fwd = o > 0 ? lp[o > 0 ? o : 1] : (o < 0 ? lm[o < 0 ? -o : 1] : u0);
+          const float bwd = o > 0 ? lm[o > 0 ? o : 1] : (o < 0 ? lp[o < 0 ? -o : 1] : u0);
+          w = fmaf(C.up[d][i], neg[d] ? bwd : fwd, w);
+        }
+        adv = d == 0 ? ab[0] * w : fmaf(ab[d], w, adv);
+      }
+    }
+    if (WITH_KO) ko_out[var] = ko;
+    Q.adv[var] = WITH_ADV ? adv : 0.f;
+    if (!need_d1) continue;
+    if (var == V_TRK) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Q.dK[d] = d1v[d];
+      continue;
+    }
+    if (var >= V_GAM1 && var <= V_GAM3) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Q.dGam[d][var - V_GAM1] = d1v[d];
+      continue;
+    }
+    // mixed variable m: off-diagonal second derivatives from the tables
+    const float* tx = dX + (long long)m * vs;
+    const float* ty = dY + (long long)m * vs;
+    float xy = C.c1[1][1] * (__ldg(tx + p + L.sy) - __ldg(tx + p - L.sy));
+    float xz = C.c1[2][1] * (__ldg(tx + p + L.sz) - __ldg(tx + p - L.sz));
+    float yz = C.c1[2][1] * (__ldg(ty + p + L.sz) - __ldg(ty + p - L.sz));
+#pragma unroll
+    for (int b = 2; b <= H; ++b) {
+      xy = fmaf(C.c1[1][b], __ldg(tx + p + b * L.sy) - __ldg(tx + p - b * L.sy), xy);
+      xz = fmaf(C.c1[2][b], __ldg(tx + p + b * L.sz) - __ldg(tx + p - b * L.sz), xz);
+      yz = fmaf(C.c1[2][b], __ldg(ty + p + b * L.sz) - __ldg(ty + p - b * L.sz), yz);
+    }
+    float d2s[6];
+    d2s[0] = d2v[0];
+    d2s[1] = xy;
+    d2s[2] = xz;
+    d2s[3] = d2v[1];
+    d2s[4] = yz;
+    d2s[5] = d2v[2];
+    if (m == 0) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Q.dW[d] = d1v[d];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) Q.ddW[q] = d2s[q];
+    } else if (m <= 6) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Q.dg[d][m - 1] = d1v[d];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) Q.ddg[m - 1][q] = d2s[q];
+    } else if (m == 7) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Q.da[d] = d1v[d];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) Q.dda[q] = d2s[q];
+    } else {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Q.db[d][m - 8] = d1v[d];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) Q.ddb[m - 8][q] = d2s[q];
+    }
+  }
+}
+
 // 1/W: always computed in double precision (the conformal-factor division
 // that dominates near punctures)
 template <typename R>
@@ -274,12 +446,34 @@ template <int P, int MODE, typename R>
 __device__ __forceinline__ void stage_point(const Layout& L, const Coef<R>& C, const Gauge& gz, const RK& rk,
                                             const StagePtrs<R>& S, long long p);
 
+// Resident blocks per SM asked of the compiler: the FP64 form is bound by the
+// FP64 pipe and keeps its registers; the FP32 form is latency-bound and trades
+// registers (and some local-memory traffic) for more warps.
+template <typename R>
+constexpr int stage_min_blocks() {
+  return std::is_same<R, float>::value ? STAGE_F32_MIN_BLOCKS : 1;
+}
+
+// tx = 0: each block takes 128 consecutive points (x fastest). tx > 0: each
+// block takes a tile of tx x (128 / tx) points of one z-plane, so that the
+// y-neighbour lines of its rows are shared in L1.
 template <int P, int MODE, typename R>
-__global__ void __launch_bounds__(128) k_stage(Layout L, Coef<R> C, Gauge gz, RK rk, StagePtrs<R> S) {
-  const long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (lin >= L.npts) return;
+__global__ void __launch_bounds__(128, stage_min_blocks<R>()) k_stage(Layout L, Coef<R> C, Gauge gz, RK rk,
+                                                                        StagePtrs<R> S, int tx) {
   int i, j, k;
-  point_coords(L, lin, i, j, k);
+  if (tx == 0) {
+    const long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (lin >= L.npts) return;
+    point_coords(L, lin, i, j, k);
+  } else {
+    const int ty = 128 / tx;
+    const int ntx = (L.nx + tx - 1) / tx, nty = (L.ny + ty - 1) / ty;
+    const int b = blockIdx.x;
+    i = (b % ntx) * tx + (int)threadIdx.x % tx;
+    j = ((b / ntx) % nty) * ty + (int)threadIdx.x / tx;
+    k = b / (ntx * nty);
+    if (i >= L.nx || j >= L.ny) return;
+  }
   stage_point<P, MODE, R>(L, C, gz, rk, S, L.off0 + i + j * L.sy + k * L.sz);
 }
 
@@ -289,7 +483,10 @@ __device__ __forceinline__ void stage_point(const Layout& L, const Coef<R>& C, c
                                             const StagePtrs<R>& S, long long p) {
   PointIn<R> Q;
   R ko[NV];
-  gather<P, MODE == 0, true, R>(L, C, S.ys, S.dX, S.dY, p, Q, ko);
+  if constexpr (std::is_same<R, float>::value)
+    gather_lines<P, MODE == 0, true>(L, C, S.ys, S.dX, S.dY, p, Q, ko);
+  else
+    gather<P, MODE == 0, true, R>(L, C, S.ys, S.dX, S.dY, p, Q, ko);
   R rhs[NV];
   const R iW = inv_w<R>(Q, S.ys64, p, L.vs);
   rhs_point<R>(Q, gz, iW, rhs);

@@ -18,8 +18,11 @@ struct StageArgs {
   const void* dY;
 };
 
+// FP64: first-difference tables (H per mixed variable); FP32_RHS: first-
+// derivative tables (one per mixed variable and axis), which need G's spacing.
 template <int P>
-cudaError_t launch_diffs(const Layout& L, bssn_precision_t prec, const void* u, void* dX, void* dY, cudaStream_t s);
+cudaError_t launch_diffs(const Layout& L, const bssn_grid_t& G, bssn_precision_t prec, const void* u, void* dX,
+                         void* dY, cudaStream_t s);
 template <int P>
 cudaError_t launch_stage(const Layout& L, const bssn_grid_t& G, double eps, bssn_precision_t prec, const Gauge& gz,
                          const RK& rk, const StageArgs& A, int mode, cudaStream_t s);

@@ -90,7 +90,8 @@ extern "C" bssn_status_t bssn_rk4_stage_noalloc(const bssn_grid_t* grid, const b
     src = f32;
   }
   if (e == cudaSuccess)
-    e = params->fd_order == 4 ? launch_diffs<4>(L, prec, src, dX, dY, s) : launch_diffs<8>(L, prec, src, dX, dY, s);
+    e = params->fd_order == 4 ? launch_diffs<4>(L, *grid, prec, src, dX, dY, s)
+                              : launch_diffs<8>(L, *grid, prec, src, dX, dY, s);
   if (e == cudaSuccess) {
     StageArgs A{src, ys, y0, acc, ynext, dX, dY};
     const RK rk = make_rk(stage, dt);

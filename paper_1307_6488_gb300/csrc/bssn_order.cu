@@ -12,14 +12,15 @@ namespace bssn {
 static inline unsigned int blocks_for(long long n, int threads) { return (unsigned int)((n + threads - 1) / threads); }
 
 template <>
-cudaError_t launch_diffs<BSSN_ORDER>(const Layout& L, bssn_precision_t prec, const void* u, void* dX, void* dY,
-                                     cudaStream_t s) {
+cudaError_t launch_diffs<BSSN_ORDER>(const Layout& L, const bssn_grid_t& G, bssn_precision_t prec, const void* u,
+                                     void* dX, void* dY, cudaStream_t s) {
   constexpr int H = FD<BSSN_ORDER>::H;
   const long long n = (long long)L.nx * (L.ny + 2 * H) * (L.nz + 2 * H);
   if (prec == BSSN_FP64)
     k_diffs<BSSN_ORDER, double><<<blocks_for(n, 256), 256, 0, s>>>(L, (const double*)u, (double*)dX, (double*)dY);
   else
-    k_diffs<BSSN_ORDER, float><<<blocks_for(n, 256), 256, 0, s>>>(L, (const float*)u, (float*)dX, (float*)dY);
+    k_d1tab<BSSN_ORDER><<<blocks_for(n, 256), 256, 0, s>>>(L, make_coef<BSSN_ORDER, float>(G, 0.0), (const float*)u,
+                                                           (float*)dX, (float*)dY);
   return cudaGetLastError();
 }
 
@@ -28,11 +29,15 @@ static cudaError_t stage_typed(const Layout& L, const bssn_grid_t& G, double eps
                                const StageArgs& A, int mode, cudaStream_t s) {
   StagePtrs<R> S{(const R*)A.ys, A.ys64, A.y0, A.acc, A.out, (const R*)A.dX, (const R*)A.dY};
   const Coef<R> C = make_coef<BSSN_ORDER, R>(G, eps);
-  const unsigned int nb = blocks_for(L.npts, STAGE_THREADS);
+  // FP32: 2D tiles of STAGE_F32_TILE_X x (128 / STAGE_F32_TILE_X) points
+  const int tx = std::is_same<R, float>::value ? STAGE_F32_TILE_X : 0;
+  const unsigned int nb =
+      tx == 0 ? blocks_for(L.npts, STAGE_THREADS)
+              : (unsigned int)(((L.nx + tx - 1) / tx) * (long long)((L.ny + 128 / tx - 1) / (128 / tx)) * L.nz);
   if (mode == 0)
-    k_stage<BSSN_ORDER, 0, R><<<nb, STAGE_THREADS, 0, s>>>(L, C, gz, rk, S);
+    k_stage<BSSN_ORDER, 0, R><<<nb, STAGE_THREADS, 0, s>>>(L, C, gz, rk, S, tx);
   else
-    k_stage<BSSN_ORDER, 1, R><<<nb, STAGE_THREADS, 0, s>>>(L, C, gz, rk, S);
+    k_stage<BSSN_ORDER, 1, R><<<nb, STAGE_THREADS, 0, s>>>(L, C, gz, rk, S, tx);
   return cudaGetLastError();
 }
 
