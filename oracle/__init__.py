@@ -44,6 +44,8 @@ def lib():
         L.oracle_fill_ghosts.restype = _i
         L.oracle_rk4_step.argtypes = [_i, _i, _i, _i, _d, _d, _d, _ll, _i, _d, _i, _i, _d, _d, _i, _i, _p, _d, _p]
         L.oracle_rk4_step.restype = _i
+        L.oracle_rk3_step.argtypes = L.oracle_rk4_step.argtypes
+        L.oracle_rk3_step.restype = _i
         L.oracle_constraints.argtypes = [_i, _i, _i, _i, _d, _d, _d, _ll, _i, _p, _p, _p, _p, _p, _p]
         L.oracle_constraints.restype = _i
         L.oracle_flop_counts.argtypes = [_i, _p]
@@ -185,6 +187,20 @@ def rk4_step(u, g, h, dt, p: Params, bc=0, ghost_src=None):
                                p.shift_coeff, p.eta, p.advect_gauge, bc, _ptr(ghost_src), dt, _ptr(y))
     if rc != 0:
         raise ValueError("oracle_rk4_step: invalid arguments")
+    return y
+
+
+def rk3_step(u, g, h, dt, p: Params, bc=0, ghost_src=None):
+    """One SSP-RK3 (Shu-Osher) step (RHS + KO), returns a new array."""
+    nx, ny, nz, vs = _check_state(u, g)
+    y = u.copy()
+    if ghost_src is not None:
+        ghost_src = np.ascontiguousarray(ghost_src, dtype=np.float64)
+    hx, hy, hz = (h, h, h) if np.isscalar(h) else h
+    rc = lib().oracle_rk3_step(nx, ny, nz, g, hx, hy, hz, vs, p.fd_order, p.ko_eps, p.lapse, p.shift,
+                               p.shift_coeff, p.eta, p.advect_gauge, bc, _ptr(ghost_src), dt, _ptr(y))
+    if rc != 0:
+        raise ValueError("oracle_rk3_step: invalid arguments")
     return y
 
 

@@ -27,6 +27,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 
 namespace {
@@ -992,6 +993,43 @@ int oracle_rk4_step(int nx, int ny, int nz, int g, double dx, double dy, double 
           state[p] = y0[p] + dt / 6.0 * (k[0][p] + 2.0 * k[1][p] + 2.0 * k[2][p] + k[3][p]);
         }
   fill_ghosts(G, bc, ghost_src, state);
+  return 0;
+}
+
+// One step of the third-order strong-stability-preserving Runge-Kutta method
+// (Shu & Osher 1988), the "3rd order Runge-Kutta" of Sec. 3.3 as Cactus's
+// method of lines runs it:
+//   y1 = y0 + dt f(y0)
+//   y2 = 3/4 y0 + 1/4 (y1 + dt f(y1))
+//   y3 = 1/3 y0 + 2/3 (y2 + dt f(y2))
+// f = right-hand side + Kreiss-Oliger, ghosts filled before each evaluation.
+int oracle_rk3_step(int nx, int ny, int nz, int g, double dx, double dy, double dz, long long vs,
+                    int fd_order, double ko_eps, int lapse, int shift, double shift_coeff, double eta,
+                    int advect_gauge, int bc, const double* ghost_src, double dt, double* state) {
+  if ((fd_order != 4 && fd_order != 8) || g < required_ghost(fd_order)) return -1;
+  Grid G = make_grid(nx, ny, nz, g, dx, dy, dz, vs);
+  Params P = make_params(fd_order, ko_eps, lapse, shift, shift_coeff, eta, advect_gauge);
+  const size_t total = (size_t)vs * NVAR;
+  std::vector<double> y0(state, state + total), y(total), k(total);
+  // weight of y0 and of (y_s + dt f(y_s)) in stage s
+  const double w0[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double w1[3] = {1.0, 0.25, 2.0 / 3.0};
+  fill_ghosts(G, bc, ghost_src, y0.data());
+  y = y0;
+  for (int s = 0; s < 3; ++s) {
+    std::fill(k.begin(), k.end(), 0.0);
+    rhs_grid(G, P, y.data(), k.data());
+    ko_grid(G, P, y.data(), k.data());
+    for (int v = 0; v < NVAR; ++v)
+      for (int kk = 0; kk < G.n[2]; ++kk)
+        for (int j = 0; j < G.n[1]; ++j)
+          for (int i = 0; i < G.n[0]; ++i) {
+            const long long q = v * vs + G.idx(i, j, kk);
+            y[q] = w0[s] * y0[q] + w1[s] * (y[q] + dt * k[q]);
+          }
+    fill_ghosts(G, bc, ghost_src, y.data());
+  }
+  std::copy(y.begin(), y.end(), state);
   return 0;
 }
 
