@@ -334,6 +334,29 @@ def run_gpu(args):
                 "fd_order": 4, "dt": dtb, "graph_launches_per_step": 1,
                 "kernel_nodes_per_step": 13 if prec == B.FP64 else 17}
 
+    def run_rk3(prec):
+        """The paper's own integrator (third-order Runge-Kutta, Shu-Osher
+        SSP form) on the same 128^3 workload: three fused stages per step,
+        no accumulator. Timed through bssn_rk3_step."""
+        st = state0.clone()
+        bufs = torch.empty(2 * 24 * grid.var_stride, dtype=torch.float64, device=dev)
+        wk = B.alloc_work(grid, p, prec, device=dev)
+        for _ in range(args.warmup):
+            B.rk3_step(grid, p, prec, dt, 1, ghost_src, st, bufs, wk)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            B.rk3_step(grid, p, prec, dt, 1, ghost_src, st, bufs, wk)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        l2, _, _ = B.constraints(grid, p, st, wk)
+        del bufs, wk
+        return {"value": world * n ** 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "stages_per_step": 3,
+                "ham_l2_after": float(l2[0]), "steps": args.steps + args.warmup}
+
     def run_fp32_config():
         """FP32-RHS against FP64 as stated for that form: throughput of both at
         256^3 (same Brill-Lindquist data, 8th order, g = 5; state 3.6 GB per
@@ -585,6 +608,8 @@ def run_gpu(args):
     if not args.no_batched:
         batched["batched_fp64"] = run_batched(B.FP64)
         batched["batched_fp32_rhs"] = run_batched(B.FP32_RHS)
+    batched["rk3_fp64"] = run_rk3(B.FP64)
+    batched["rk3_fp32_rhs"] = run_rk3(B.FP32_RHS)
     if not args.no_fp32_config:
         batched["fp32_rhs_vs_fp64"] = run_fp32_config()
     if not args.no_learned:

@@ -188,6 +188,28 @@ bssn_status_t bssn_rk4_step(const bssn_grid_t* grid, const bssn_params_t* params
                             double dt, int bc, const double* ghost_src, double* state, double* bufs,
                             void* work, unsigned long long work_bytes, void* stream);
 
+/* The third-order Runge-Kutta method of lines of Sec. 3.3, taken as the
+ * strong-stability-preserving method of Shu & Osher (1988):
+ *   stage 0: ynext = y0 + dt k(ys)                  (pass ys == y0)
+ *   stage 1: ynext = 3/4 y0 + 1/4 (ys + dt k(ys))   (ys = stage-0 result)
+ *   stage 2: ynext = 1/3 y0 + 2/3 (ys + dt k(ys))   (ys = stage-1 result)
+ * k = right-hand side + Kreiss-Oliger evaluated on ys (its ghosts filled),
+ * at interior points; all DEVICE pointers, 16-byte aligned, FP64 state
+ * layout. No accumulator. ynext may equal y0 (read only at the point being
+ * written) but must not equal ys. prec as for RK4 (FP32_RHS keeps the
+ * combination in FP64). work: >= bssn_work_bytes(). Asynchronous. */
+bssn_status_t bssn_rk3_stage(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec,
+                             int stage, double dt, const double* y0, const double* ys, double* ynext, void* work,
+                             unsigned long long work_bytes, void* stream);
+
+/* One full RK3 step in place on `state`: three stages with the ghosts filled
+ * before each (bc 0 periodic, bc 1 static from ghost_src). bufs holds two
+ * state-sized DEVICE buffers (2 x 24 x var_stride doubles). On return the
+ * interior of state holds the new values and its ghosts are refilled. */
+bssn_status_t bssn_rk3_step(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec, double dt,
+                            int bc, const double* ghost_src, double* state, double* bufs, void* work,
+                            unsigned long long work_bytes, void* stream);
+
 /* ---------------------------------------------------------------- batched patches
  * Many independent uneven grid patches advanced by one RK4 step per call,
  * the single-GPU analogue of the block-structured (AMR / multi-block) grids

@@ -380,6 +380,30 @@ def corrector_layer_output(c, layer, S, out):
     _check(_corr_lib().bssn_corrector_layer_output(c, layer, S, _ptr(out)), "corrector_layer_output")
 
 
+def _rk3_lib():
+    L = lib()
+    if not getattr(L, "_rk3_typed", False):
+        L.bssn_rk3_stage.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_double, _p, _p, _p, _p, ctypes.c_ulonglong, _p]
+        L.bssn_rk3_step.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Params), ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_int, _p, _p, _p, _p, ctypes.c_ulonglong, _p]
+        L.bssn_rk3_stage.restype = ctypes.c_int
+        L.bssn_rk3_step.restype = ctypes.c_int
+        L._rk3_typed = True
+    return L
+
+
+def rk3_stage(grid, params, prec, stage, dt, y0, ys, ynext, work, stream=None):
+    _check(_rk3_lib().bssn_rk3_stage(ctypes.byref(grid), ctypes.byref(params), prec, stage, dt, _ptr(y0), _ptr(ys),
+                                     _ptr(ynext), _ptr(work), _nbytes(work), _stream(stream)), "rk3_stage")
+
+
+def rk3_step(grid, params, prec, dt, bc, ghost_src, state, bufs, work, stream=None):
+    """One SSP-RK3 step in place; bufs holds two state-sized buffers."""
+    _check(_rk3_lib().bssn_rk3_step(ctypes.byref(grid), ctypes.byref(params), prec, dt, bc, _ptr(ghost_src),
+                                    _ptr(state), _ptr(bufs), _ptr(work), _nbytes(work), _stream(stream)), "rk3_step")
+
+
 def rk4_step(grid, params, prec, dt, bc, ghost_src, state, bufs, work, stream=None):
     _check(lib().bssn_rk4_step(ctypes.byref(grid), ctypes.byref(params), prec, dt, bc, _ptr(ghost_src), _ptr(state),
                                _ptr(bufs), _ptr(work), _nbytes(work), _stream(stream)), "rk4_step")

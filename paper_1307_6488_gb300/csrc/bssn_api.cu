@@ -354,6 +354,45 @@ bssn_status_t bssn_rk4_step(const bssn_grid_t* grid, const bssn_params_t* params
   return latch(e);
 }
 
+bssn_status_t bssn_rk3_stage(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec,
+                             int stage, double dt, const double* y0, const double* ys, double* ynext, void* work,
+                             unsigned long long work_bytes, void* stream) {
+  if (!grid_ok(grid) || !params_ok(grid, params) || !prec_ok(prec)) return BSSN_ERR_INVALID_ARG;
+  if (stage < 0 || stage > 2 || !std::isfinite(dt)) return BSSN_ERR_INVALID_ARG;
+  if (!aligned16(y0) || !aligned16(ys) || !aligned16(ynext) || !aligned16(work)) return BSSN_ERR_INVALID_ARG;
+  if (ynext == ys) return BSSN_ERR_INVALID_ARG;
+  if (work_bytes < work_layout(*grid, *params).total_bytes) return BSSN_ERR_INVALID_ARG;
+  const WorkPtrs w = work_ptrs(work, *grid, *params, prec);
+  return latch(run_stage(params->fd_order, prec, *grid, *params, make_rk3(stage, dt), ys, y0, nullptr, ynext, w, 0,
+                         (cudaStream_t)stream));
+}
+
+bssn_status_t bssn_rk3_step(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec, double dt,
+                            int bc, const double* ghost_src, double* state, double* bufs, void* work,
+                            unsigned long long work_bytes, void* stream) {
+  if (!grid_ok(grid) || !params_ok(grid, params) || !prec_ok(prec)) return BSSN_ERR_INVALID_ARG;
+  if ((bc != 0 && bc != 1) || !std::isfinite(dt)) return BSSN_ERR_INVALID_ARG;
+  if (bc == 1 && !aligned16(ghost_src)) return BSSN_ERR_INVALID_ARG;
+  if (!aligned16(state) || !aligned16(bufs) || !aligned16(work)) return BSSN_ERR_INVALID_ARG;
+  if (work_bytes < work_layout(*grid, *params).total_bytes) return BSSN_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)NV * grid->var_stride;
+  const WorkPtrs w = work_ptrs(work, *grid, *params, prec);
+  const int order = params->fd_order;
+  cudaError_t e = cudaSuccess;
+  // y1 -> bufs, y2 -> bufs + n, y3 -> state (y0 is read only at the point written)
+  const double* ys = state;
+  double* outs[3] = {bufs, bufs + n, state};
+  for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
+    if (grid->ghost > 0) e = fill(*grid, bc, ghost_src, const_cast<double*>(ys), s);
+    if (e != cudaSuccess) break;
+    e = run_stage(order, prec, *grid, *params, make_rk3(st, dt), ys, state, nullptr, outs[st], w, 0, s);
+    ys = outs[st];
+  }
+  if (e == cudaSuccess && grid->ghost > 0) e = fill(*grid, bc, ghost_src, state, s);
+  return latch(e);
+}
+
 bssn_status_t bssn_constraints(const bssn_grid_t* grid, const bssn_params_t* params, const double* state, double* ham,
                                double* mom, double* gcon, double* out_l2, double* out_max, void* work,
                                unsigned long long work_bytes, void* stream) {

@@ -133,8 +133,10 @@ inline Gauge make_gauge(const bssn_params_t& P) {
 // RK4 stage constants (classic Butcher tableau), folded with dt.
 struct RK {
   int stage;
-  double cdt;   // node weight * dt for ynext = y0 + cdt k   (stages 0..2)
-  double bdt;   // b_s * dt for acc update / final combination
+  double cdt;   // RK4: node weight * dt for ynext = y0 + cdt k (stages 0..2); RK3: weight of dt k
+  double bdt;   // RK4: b_s * dt for acc update / final combination
+  int method;   // 4: classic RK4 (with acc); 3: SSP-RK3 (no acc)
+  double a0, a1;  // RK3: ynext = a0 y0 + a1 ys + cdt k
 };
 
 inline RK make_rk(int stage, double dt) {
@@ -144,6 +146,24 @@ inline RK make_rk(int stage, double dt) {
   const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
   r.cdt = stage < 3 ? c[stage] * dt : 0.0;
   r.bdt = b[stage] * dt;
+  r.method = 4;
+  r.a0 = r.a1 = 0.0;
+  return r;
+}
+
+// Third-order strong-stability-preserving Runge-Kutta (Shu-Osher), the
+// integrator of Sec. 3.3, stage s = 0..2 as a convex combination:
+//   y1 = y0 + dt k0;  y2 = 3/4 y0 + 1/4 (y1 + dt k1);  y3 = 1/3 y0 + 2/3 (y2 + dt k2)
+inline RK make_rk3(int stage, double dt) {
+  RK r;
+  r.stage = stage;
+  r.method = 3;
+  const double w0[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double w1[3] = {1.0, 0.25, 2.0 / 3.0};
+  r.a0 = w0[stage];
+  r.a1 = w1[stage];
+  r.cdt = w1[stage] * dt;
+  r.bdt = 0.0;
   return r;
 }
 

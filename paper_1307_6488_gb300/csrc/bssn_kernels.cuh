@@ -496,6 +496,15 @@ __device__ __forceinline__ void stage_point(const Layout& L, const Coef<R>& C, c
     for (int v = 0; v < NV; ++v) S.out[v * vs + p] = (double)rhs[v];
     return;
   }
+  if (rk.method == 3) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const long long o = v * vs + p;
+      const double kv = (double)(rhs[v] + ko[v]);
+      S.out[o] = fma(rk.cdt, kv, fma(rk.a1, __ldg(S.ys64 + o), rk.a0 * __ldg(S.y0 + o)));
+    }
+    return;
+  }
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const long long o = v * vs + p;

@@ -150,3 +150,31 @@ def test_mma_rate_probe_rejects_bad_width(L):
     for n in (0, 16, 48, 512):
         assert L.bssn_probe_mma_rate(n, ctypes.byref(out)) == B.ERR_INVALID_ARG
     assert L.bssn_probe_mma_rate(32, None) == B.ERR_INVALID_ARG
+
+
+def test_rk3_rejects_invalid_arguments(L):
+    """Host-side checks of the RK3 entry points (no kernel is reached)."""
+    g = B.make_grid(8, ghost=3, dx=0.1)
+    p = B.make_params(fd_order=4)
+    fake = ctypes.c_void_p(4096)
+    other = ctypes.c_void_p(8192)
+    big = ctypes.c_ulonglong(1 << 40)
+    L.bssn_rk3_stage.argtypes = [ctypes.POINTER(B.Grid), ctypes.POINTER(B.Params), ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_void_p]
+    st = lambda stage, ys, yn, prec=B.FP64: L.bssn_rk3_stage(ctypes.byref(g), ctypes.byref(p), prec, stage, 0.01,
+                                                             fake, ys, yn, fake, big, None)
+    assert st(3, other, ctypes.c_void_p(12288)) == B.ERR_INVALID_ARG  # stages are 0..2
+    assert st(-1, other, ctypes.c_void_p(12288)) == B.ERR_INVALID_ARG
+    assert st(1, other, other) == B.ERR_INVALID_ARG  # ynext must not be ys
+    assert st(1, other, ctypes.c_void_p(12290)) == B.ERR_INVALID_ARG  # misaligned
+    assert st(1, other, ctypes.c_void_p(12288), prec=7) == B.ERR_INVALID_ARG
+    L.bssn_rk3_step.argtypes = [ctypes.POINTER(B.Grid), ctypes.POINTER(B.Params), ctypes.c_int, ctypes.c_double,
+                                ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_ulonglong, ctypes.c_void_p]
+    assert L.bssn_rk3_step(ctypes.byref(g), ctypes.byref(p), B.FP64, 0.01, 2, None, fake, other, fake, big,
+                           None) == B.ERR_INVALID_ARG  # unknown boundary mode
+    assert L.bssn_rk3_step(ctypes.byref(g), ctypes.byref(p), B.FP64, 0.01, 1, None, fake, other, fake, big,
+                           None) == B.ERR_INVALID_ARG  # static boundary needs ghost_src
+    assert L.bssn_rk3_step(ctypes.byref(g), ctypes.byref(p), B.FP64, float("nan"), 0, None, fake, other, fake, big,
+                           None) == B.ERR_INVALID_ARG
