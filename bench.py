@@ -175,8 +175,9 @@ def cpu_oracle_rate(budget_s=15.0, n=32, max_steps=None):
 
 
 def run_reference(args):
-    world, rank, _ = dist_setup()
-    if rank != 0:
+    # under torchrun only rank 0 times the oracle; the other ranks leave at
+    # once (no process group: nothing is exchanged)
+    if int(os.environ.get("RANK", "0")) != 0:
         return
     n = 32
     rates = []
