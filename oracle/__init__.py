@@ -48,6 +48,8 @@ def lib():
         L.oracle_rk3_step.restype = _i
         L.oracle_constraints.argtypes = [_i, _i, _i, _i, _d, _d, _d, _ll, _i, _p, _p, _p, _p, _p, _p]
         L.oracle_constraints.restype = _i
+        L.oracle_psi4.argtypes = [_i, _i, _i, _i, _d, _d, _d, _ll, _i, _d, _d, _d, _p, _p, _p, _p, _p, _p, _p]
+        L.oracle_psi4.restype = _i
         L.oracle_flop_counts.argtypes = [_i, _p]
         L.oracle_flop_counts.restype = _i
         L.oracle_restrict.argtypes = [_i, _i, _i, _i, _ll, _i, _i, _i, _i, _ll, _i, _p, _p]
@@ -223,6 +225,23 @@ def constraints(u, g, h, fd_order, fields=False):
     if fields:
         return l2, mx, rc, (ham, mom, gcon)
     return l2, mx, rc
+
+
+def psi4(u, g, h, fd_order, origin):
+    """Weyl diagnostics at interior points: returns dict with psi4 (complex),
+    inv (complex, I = Q_ij Q^ij / 2), E and B (6 packed components each),
+    all padded-layout arrays; origin = coordinates of interior point (0,0,0)."""
+    nx, ny, nz, vs = _check_state(u, g)
+    shape = u.shape[1:]
+    pr, pi, ir, ii = (np.zeros(shape) for _ in range(4))
+    E = np.zeros((6,) + shape)
+    B = np.zeros((6,) + shape)
+    hx, hy, hz = (h, h, h) if np.isscalar(h) else h
+    rc = lib().oracle_psi4(nx, ny, nz, g, hx, hy, hz, vs, fd_order, float(origin[0]), float(origin[1]),
+                           float(origin[2]), _ptr(u), _ptr(pr), _ptr(pi), _ptr(ir), _ptr(ii), _ptr(E), _ptr(B))
+    if rc < 0:
+        raise ValueError("oracle_psi4: invalid arguments")
+    return dict(psi4=pr + 1j * pi, inv=ir + 1j * ii, E=E, B=B, finite=(rc == 0))
 
 
 def flop_counts(fd_order):

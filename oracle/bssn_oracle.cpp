@@ -684,6 +684,155 @@ void constraints_point(const T u[NVAR], const Derivs<T>& D, T out[7]) {
   for (int i = 0; i < 3; ++i) out[4 + i] = u[V_GAM1 + i] - Q.Gd[i];
 }
 
+// Electric and magnetic parts of the Weyl tensor and Psi_4 at one point, for
+// the gravitational-wave extraction the paper runs on the GPU beside the
+// evolution (Sec. 3.3, WeylScal4). Vacuum, from the BSSN variables:
+//   gamma_ij = gt_ij / W^2,  K_ij = (At_ij + gt_ij K / 3) / W^2,
+//   E_ij = R_ij + K K_ij - K_ik K^k_j,
+//   B_ij = 1/2 (eps_i^kl D_k K_lj + eps_j^kl D_k K_li),
+//     eps^mkl = [mkl] / sqrt(det gamma),  D the covariant derivative of gamma,
+//   Q_ij = E_ij - i B_ij,
+//   Psi_4 = Q_ij mbar^i mbar^j,  m = (e_theta + i e_phi) / sqrt(2),
+//   I = Q_ij Q^ij / 2   (= 3 Psi_2^2 for a type-D field),
+// with (e_r, e_theta, e_phi) the gamma-orthonormal triad that Gram-Schmidt
+// makes of the coordinate directions r = (x, y, z), theta ~ (xz, yz,
+// -(x^2+y^2)), phi = (-y, x, 0) about the coordinate origin, in that order.
+// Where x = y = 0 the triad is undefined and Psi_4 is set to 0.
+// out: E[6], B[6] (packed 11 12 13 22 23 33), psi4[2], inv[2] (re, im).
+template <typename T>
+void weyl_point(const T u[NVAR], const Derivs<T>& D, const double xyz[3], T E6[6], T B6[6], T psi4[2],
+                T inv[2]) {
+  Geom<T> Q;
+  geometry<T>(u, D, Q);
+  const T W = Q.W, K = Q.K;
+  const T W2 = W * W;
+  T gam[3][3], gamu[3][3], Kd[3][3], Km[3][3], E[3][3], Bm[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      gam[i][j] = Q.gt[i][j] / W2;
+      gamu[i][j] = W2 * Q.gtu[i][j];
+      Kd[i][j] = (Q.At[i][j] + Q.gt[i][j] * K / T(3.0)) / W2;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      T s = T(0.0);
+      for (int k = 0; k < 3; ++k) s = s + gamu[i][k] * Kd[k][j];
+      Km[i][j] = s;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      T s = T(0.0);
+      for (int k = 0; k < 3; ++k) s = s + Kd[i][k] * Km[k][j];
+      E[i][j] = Q.Ric[i][j] + K * Kd[i][j] - s;
+    }
+  // physical Christoffels: Gamma^k_ij = Gt^k_ij - (d^k_i d_j W + d^k_j d_i W - gt_ij gt^kl d_l W) / W
+  T Gp[3][3][3];
+  for (int k = 0; k < 3; ++k) {
+    T up = T(0.0);
+    for (int l = 0; l < 3; ++l) up = up + Q.gtu[k][l] * D.dW[l];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        T t = -Q.gt[i][j] * up;
+        if (k == i) t = t + D.dW[j];
+        if (k == j) t = t + D.dW[i];
+        Gp[k][i][j] = Q.Gam[k][i][j] - t / W;
+      }
+  }
+  // d_k K_ij and D_k K_ij
+  T DK[3][3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        const T num = Q.At[i][j] + Q.gt[i][j] * K / T(3.0);
+        const T dnum = D.dAt[k][i][j] + D.dgt[k][i][j] * K / T(3.0) + Q.gt[i][j] * D.dK[k] / T(3.0);
+        T d = dnum / W2 - T(2.0) * num * D.dW[k] / (W2 * W);
+        for (int m = 0; m < 3; ++m) d = d - Gp[m][k][i] * Kd[m][j] - Gp[m][k][j] * Kd[i][m];
+        DK[k][i][j] = d;
+      }
+  // det gamma = det(gt) / W^6
+  const T detgt = Q.gt[0][0] * (Q.gt[1][1] * Q.gt[2][2] - Q.gt[1][2] * Q.gt[2][1]) -
+                  Q.gt[0][1] * (Q.gt[1][0] * Q.gt[2][2] - Q.gt[1][2] * Q.gt[2][0]) +
+                  Q.gt[0][2] * (Q.gt[1][0] * Q.gt[2][1] - Q.gt[1][1] * Q.gt[2][0]);
+  const T isq = T(1.0) / std::sqrt(detgt / (W2 * W2 * W2));
+  auto lc = [](int a, int b, int c) {  // Levi-Civita symbol [abc]
+    if (a == b || b == c || a == c) return 0.0;
+    return ((a == 0 && b == 1) || (a == 1 && b == 2) || (a == 2 && b == 0)) ? 1.0 : -1.0;
+  };
+  T C[3][3];  // C_ij = eps_i^kl D_k K_lj = gamma_im eps^mkl D_k K_lj
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      T s = T(0.0);
+      for (int m = 0; m < 3; ++m)
+        for (int k = 0; k < 3; ++k)
+          for (int l = 0; l < 3; ++l) {
+            const double e = lc(m, k, l);
+            if (e != 0.0) s = s + gam[i][m] * T(e) * isq * DK[k][l][j];
+          }
+      C[i][j] = s;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Bm[i][j] = T(0.5) * (C[i][j] + C[j][i]);
+  for (int i = 0; i < 3; ++i)
+    for (int j = i; j < 3; ++j) {
+      E6[SYM[i][j]] = E[i][j];
+      B6[SYM[i][j]] = Bm[i][j];
+    }
+  // I = (E.E - B.B) / 2 - i E.B, contractions with gamma^ij
+  T EE = T(0.0), BB = T(0.0), EB = T(0.0);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) {
+          const T g2 = gamu[i][k] * gamu[j][l];
+          EE = EE + g2 * E[i][j] * E[k][l];
+          BB = BB + g2 * Bm[i][j] * Bm[k][l];
+          EB = EB + g2 * E[i][j] * Bm[k][l];
+        }
+  inv[0] = T(0.5) * (EE - BB);
+  inv[1] = -EB;
+  // triad
+  const double x = xyz[0], y = xyz[1], z = xyz[2];
+  if (x * x + y * y == 0.0) {
+    psi4[0] = T(0.0);
+    psi4[1] = T(0.0);
+    return;
+  }
+  const double vr[3] = {x, y, z}, vt[3] = {x * z, y * z, -(x * x + y * y)}, vp[3] = {-y, x, 0.0};
+  auto dot = [&](const T* a, const T* b) {
+    T s = T(0.0);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) s = s + gam[i][j] * a[i] * b[j];
+    return s;
+  };
+  T er[3], et[3], ep[3];
+  for (int i = 0; i < 3; ++i) {
+    er[i] = T(vr[i]);
+    et[i] = T(vt[i]);
+    ep[i] = T(vp[i]);
+  }
+  T nr = std::sqrt(dot(er, er));
+  for (int i = 0; i < 3; ++i) er[i] = er[i] / nr;
+  T c = dot(et, er);
+  for (int i = 0; i < 3; ++i) et[i] = et[i] - c * er[i];
+  T nt = std::sqrt(dot(et, et));
+  for (int i = 0; i < 3; ++i) et[i] = et[i] / nt;
+  T c1 = dot(ep, er), c2 = dot(ep, et);
+  for (int i = 0; i < 3; ++i) ep[i] = ep[i] - c1 * er[i] - c2 * et[i];
+  T np_ = std::sqrt(dot(ep, ep));
+  for (int i = 0; i < 3; ++i) ep[i] = ep[i] / np_;
+  auto proj = [&](T M[3][3], const T* a, const T* b) {
+    T s = T(0.0);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) s = s + M[i][j] * a[i] * b[j];
+    return s;
+  };
+  const T Ett = proj(E, et, et), Epp = proj(E, ep, ep), Etp = proj(E, et, ep);
+  const T Btt = proj(Bm, et, et), Bpp = proj(Bm, ep, ep), Btp = proj(Bm, et, ep);
+  // Q mbar mbar = ((Q_tt - Q_pp) - 2 i Q_tp) / 2 with Q = E - i B
+  psi4[0] = T(0.5) * ((Ett - Epp) - T(2.0) * Btp);
+  psi4[1] = T(0.5) * (-(Btt - Bpp) - T(2.0) * Etp);
+}
+
 Params make_params(int fd_order, double ko_eps, int lapse, int shift, double shift_coeff, double eta,
                    int advect_gauge) {
   Params P;
@@ -1077,6 +1226,44 @@ int oracle_constraints(int nx, int ny, int nz, int g, double dx, double dy, doub
     }
     l2[q] = std::sqrt(s / (double)npts);
     mx[q] = m;
+  }
+  return bad ? 1 : 0;
+}
+
+// Weyl diagnostics at interior points (see weyl_point): psi4 re/im, the
+// invariant I re/im (each a padded-layout array, nullable), and E, B (6
+// padded-layout arrays each, nullable). (x0, y0, z0) is the coordinate of
+// interior point (0,0,0); the triad is taken about the coordinate origin.
+// Returns 0, 1 if a value is not finite, -1 for invalid arguments.
+int oracle_psi4(int nx, int ny, int nz, int g, double dx, double dy, double dz, long long vs, int fd_order,
+                double x0, double y0, double z0, const double* state, double* psi_re, double* psi_im,
+                double* inv_re, double* inv_im, double* E, double* B) {
+  if ((fd_order != 4 && fd_order != 8) || g < required_ghost(fd_order)) return -1;
+  Grid G = make_grid(nx, ny, nz, g, dx, dy, dz, vs);
+  const Stencils S = make_stencils(fd_order);
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+  for (int k = 0; k < nz; ++k) {
+    Derivs<double> D;
+    double u[NVAR], e6[6], b6[6], ps[2], iv[2];
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const long long p = G.idx(i, j, k);
+        for (int v = 0; v < NVAR; ++v) u[v] = state[v * vs + p];
+        gather_derivs<double>(S, G, state, p, false, true, D);
+        const double xyz[3] = {x0 + i * dx, y0 + j * dy, z0 + k * dz};
+        weyl_point<double>(u, D, xyz, e6, b6, ps, iv);
+        if (psi_re) psi_re[p] = ps[0];
+        if (psi_im) psi_im[p] = ps[1];
+        if (inv_re) inv_re[p] = iv[0];
+        if (inv_im) inv_im[p] = iv[1];
+        for (int q = 0; q < 6; ++q) {
+          if (E) E[q * vs + p] = e6[q];
+          if (B) B[q * vs + p] = b6[q];
+          if (!std::isfinite(e6[q]) || !std::isfinite(b6[q])) bad = 1;
+        }
+        if (!std::isfinite(ps[0]) || !std::isfinite(ps[1])) bad = 1;
+      }
   }
   return bad ? 1 : 0;
 }

@@ -51,11 +51,20 @@ def _pack(W, gt, trK, At, Gt, alpha, beta_up, B=None):
 
 
 # ---------------------------------------------------------------- Kerr-Schild
-def _ks_parts(xyz, M):
+def ks_radius(xyz, a):
+    """Kerr-Schild (= Boyer-Lindquist) r: the root of
+    (x^2 + y^2) / (r^2 + a^2) + z^2 / r^2 = 1."""
     x, y, z = xyz
-    r = np.sqrt(x * x + y * y + z * z)
-    H = M / r
-    l = [x / r, y / r, z / r]
+    rho2 = x * x + y * y + z * z
+    q = rho2 - a * a
+    return np.sqrt(0.5 * q + np.sqrt(0.25 * q * q + a * a * z * z))
+
+
+def _ks_parts(xyz, M, a=0.0):
+    x, y, z = xyz
+    r = ks_radius(xyz, a)
+    H = M * r ** 3 / (r ** 4 + a * a * z * z)
+    l = [(r * x + a * y) / (r * r + a * a), (r * y - a * x) / (r * r + a * a), z / r]
     gam = [[(1.0 if i == j else 0.0) + 2 * H * l[i] * l[j] for j in range(3)] for i in range(3)]
     gamu = [[(1.0 if i == j else 0.0) - 2 * H * l[i] * l[j] / (1 + 2 * H) for j in range(3)] for i in range(3)]
     det = 1 + 2 * H
@@ -65,17 +74,18 @@ def _ks_parts(xyz, M):
     return gam, gamu, det, alpha, beta_dn, beta_up
 
 
-def kerr_schild(Xm, Ym, Zm, M=1.0):
-    """Schwarzschild in Kerr-Schild coordinates with its own (stationary)
-    lapse and shift: gamma_ij = delta_ij + 2 H l_i l_j, H = M/r, l_i = x_i/r,
-    alpha = (1+2H)^(-1/2), beta_i = 2 H l_i. The extrinsic curvature follows
-    from d_t gamma_ij = 0 = -2 alpha K_ij + D_i beta_j + D_j beta_i.
-    Returns the 24-variable state (B = 0)."""
+def kerr_schild(Xm, Ym, Zm, M=1.0, a=0.0):
+    """Kerr (spin a along z; a = 0: Schwarzschild) in Kerr-Schild coordinates
+    with its own (stationary) lapse and shift: gamma_ij = delta_ij + 2 H l_i
+    l_j, H = M r^3 / (r^4 + a^2 z^2), l = ((r x + a y), (r y - a x)) / (r^2 +
+    a^2), z / r), alpha = (1+2H)^(-1/2), beta_i = 2 H l_i. The extrinsic
+    curvature follows from d_t gamma_ij = 0 = -2 alpha K_ij + D_i beta_j +
+    D_j beta_i. Returns the 24-variable state (B = 0)."""
     xyz = [Xm, Ym, Zm]
-    gam, gamu, det, alpha, beta_dn, beta_up = _ks_parts(xyz, M)
-    dgam = [[[_cstep(lambda p, i=i, j=j: _ks_parts(p, M)[0][i][j], xyz, k) for j in range(3)] for i in range(3)]
+    gam, gamu, det, alpha, beta_dn, beta_up = _ks_parts(xyz, M, a)
+    dgam = [[[_cstep(lambda p, i=i, j=j: _ks_parts(p, M, a)[0][i][j], xyz, k) for j in range(3)] for i in range(3)]
             for k in range(3)]  # dgam[k][i][j] = d_k gamma_ij
-    dbeta = [[_cstep(lambda p, j=j: _ks_parts(p, M)[4][j], xyz, i) for j in range(3)] for i in range(3)]
+    dbeta = [[_cstep(lambda p, j=j: _ks_parts(p, M, a)[4][j], xyz, i) for j in range(3)] for i in range(3)]
     Kdn = [[None] * 3 for _ in range(3)]
     for i in range(3):
         for j in range(3):
@@ -90,17 +100,17 @@ def kerr_schild(Xm, Ym, Zm, M=1.0):
     At = [[W * W * (Kdn[i][j] - trK * gam[i][j] / 3) for j in range(3)] for i in range(3)]
 
     def gtu(p, i, j):
-        _, gu, dt_, _, _, _ = _ks_parts(p, M)
+        _, gu, dt_, _, _, _ = _ks_parts(p, M, a)
         return dt_ ** (1.0 / 3.0) * gu[i][j]
 
     Gt = [-sum(_cstep(lambda p, i=i, j=j: gtu(p, i, j), xyz, j) for j in range(3)) for i in range(3)]
     return _pack(W, gt, trK, At, Gt, alpha, beta_up)
 
 
-def kerr_schild_check(Xm, Ym, Zm, M=1.0):
+def kerr_schild_check(Xm, Ym, Zm, M=1.0, a=0.0):
     """Max |gamma gamma^-1 - I| and |det gamma - (1+2H)|: checks the closed
     forms used above."""
-    gam, gamu, det, *_ = _ks_parts([Xm, Ym, Zm], M)
+    gam, gamu, det, *_ = _ks_parts([Xm, Ym, Zm], M, a)
     g = np.array(gam)
     gu = np.array(gamu)
     prod = np.einsum("ij...,jk...->ik...", g, gu)
