@@ -609,6 +609,32 @@ def run_gpu(args):
     if not args.no_batched:
         batched["batched_fp64"] = run_batched(B.FP64)
         batched["batched_fp32_rhs"] = run_batched(B.FP32_RHS)
+    # gravitational-wave extraction (Weyl scalar Psi_4, E, B, invariant) on the
+    # evolved 128^3 state, timed like the stage kernel
+    vs = grid.var_stride
+    wout = torch.empty(16 * vs, dtype=torch.float64, device=dev)
+    st = f64["state"]
+    origin = (LO + 0.5 * h,) * 3
+
+    def psi4_once():
+        B.psi4(grid, p, st, origin, work, psi_re=wout[0:vs], psi_im=wout[vs:2 * vs], inv_re=wout[2 * vs:3 * vs],
+               inv_im=wout[3 * vs:4 * vs], E=wout[4 * vs:10 * vs], B=wout[10 * vs:16 * vs])
+
+    for _ in range(args.warmup):
+        psi4_once()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        psi4_once()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_psi4 = e0.elapsed_time(e1) / args.steps
+    batched["psi4_fp64"] = {"ms_per_evaluation": ms_psi4, "points_per_s": n ** 3 / (ms_psi4 * 1e-3),
+                            "share_of_rk4_step_if_every_step": ms_psi4 / (ms_psi4 + f64["ms"] / args.steps),
+                            "outputs": "Psi_4 (re, im), invariant I (re, im), E_ij, B_ij at every interior point"}
+    del wout
     batched["rk3_fp64"] = run_rk3(B.FP64)
     batched["rk3_fp32_rhs"] = run_rk3(B.FP32_RHS)
     if not args.no_fp32_config:

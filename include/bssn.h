@@ -349,6 +349,27 @@ bssn_status_t bssn_constraints(const bssn_grid_t* grid, const bssn_params_t* par
                                double* ham, double* mom, double* gcon, double* out_l2, double* out_max,
                                void* work, unsigned long long work_bytes, void* stream);
 
+/* Gravitational-wave extraction beside the evolution (the WeylScal4 kernel
+ * the paper runs on the GPU, Sec. 3.3), FP64, at interior points of `state`
+ * (DEVICE, ghosts filled): from the BSSN variables
+ *   gamma_ij = gt_ij / W^2,  K_ij = (At_ij + gt_ij K / 3) / W^2,
+ *   E_ij = R_ij + K K_ij - K_ik K^k_j,
+ *   B_ij = sym(gamma_im eps^mkl D_k K_lj),  eps^mkl = [mkl] / sqrt(det gamma),
+ *   Psi_4 = Q_ij mbar^i mbar^j with Q = E - i B, m = (e_th + i e_ph)/sqrt(2),
+ *   I = Q_ij Q^ij / 2  (= 3 Psi_2^2 for a type-D field),
+ * with (e_r, e_th, e_ph) the gamma-orthonormal triad made by Gram-Schmidt of
+ * the coordinate directions (x,y,z), (xz, yz, -(x^2+y^2)), (-y, x, 0) about
+ * the coordinate origin (Psi_4 = 0 where x = y = 0). Derivatives at the
+ * grid's fd_order. origin: HOST double[3], the coordinate of interior point
+ * (0,0,0). Outputs (DEVICE, nullable, state's padded layout, interior
+ * written): psi_re, psi_im, inv_re, inv_im one array each; E, B six arrays
+ * each (var_stride apart, packed 11 12 13 22 23 33). With this sign
+ * convention Kerr gives I = 3 M^2 / (r - i a cos(theta))^6. work: >=
+ * bssn_work_bytes(). Asynchronous; non-finite values are not reported. */
+bssn_status_t bssn_psi4(const bssn_grid_t* grid, const bssn_params_t* params, const double* state,
+                        const double* origin, double* psi_re, double* psi_im, double* inv_re, double* inv_im,
+                        double* E, double* B, void* work, unsigned long long work_bytes, void* stream);
+
 /* Measured issue rates of this device's floating-point pipes (a short
  * microbenchmark, ~20 ms). out[0] = FP64 FMA/s, out[1] = FP32 FMA/s,
  * out[2] = FP64 add/s. HOST array. Synchronizes the device. */

@@ -362,6 +362,22 @@ def prolong(coarse_grid, coarse_state, fine_grid, fine_state, stream=None):
                                         _ptr(fine_state), _stream(stream)), "prolong")
 
 
+def psi4(grid, params, state, origin, work, psi_re=None, psi_im=None, inv_re=None, inv_im=None, E=None, B=None,
+         stream=None):
+    """Weyl diagnostics (E, B, Psi_4, invariant I) at interior points;
+    outputs are device tensors in the state layout (E, B: 6 arrays each)."""
+    L = lib()
+    if not getattr(L, "_psi4_typed", False):
+        L.bssn_psi4.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Params), _p, ctypes.POINTER(ctypes.c_double),
+                                _p, _p, _p, _p, _p, _p, _p, ctypes.c_ulonglong, _p]
+        L.bssn_psi4.restype = ctypes.c_int
+        L._psi4_typed = True
+    o = (ctypes.c_double * 3)(*[float(v) for v in origin])
+    _check(L.bssn_psi4(ctypes.byref(grid), ctypes.byref(params), _ptr(state), o, _ptr(psi_re), _ptr(psi_im),
+                       _ptr(inv_re), _ptr(inv_im), _ptr(E), _ptr(B), _ptr(work), _nbytes(work), _stream(stream)),
+           "psi4")
+
+
 def probe_mma_rate(n=32):
     """Measured TFLOP/s of back-to-back M=128 K=16 BF16 MMAs with N = n."""
     L = _corr_lib()

@@ -393,6 +393,34 @@ bssn_status_t bssn_rk3_step(const bssn_grid_t* grid, const bssn_params_t* params
   return latch(e);
 }
 
+bssn_status_t bssn_psi4(const bssn_grid_t* grid, const bssn_params_t* params, const double* state,
+                        const double* origin, double* psi_re, double* psi_im, double* inv_re, double* inv_im,
+                        double* E, double* B, void* work, unsigned long long work_bytes, void* stream) {
+  if (!grid_ok(grid) || !params_ok(grid, params) || !origin) return BSSN_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(origin[a])) return BSSN_ERR_INVALID_ARG;
+  if (!aligned16(state) || !aligned16(work)) return BSSN_ERR_INVALID_ARG;
+  double* outs[6] = {psi_re, psi_im, inv_re, inv_im, E, B};
+  for (double* o : outs)
+    if (o && (!aligned16(o) || o == state)) return BSSN_ERR_INVALID_ARG;
+  if (work_bytes < work_layout(*grid, *params).total_bytes) return BSSN_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Layout L = make_layout(*grid);
+  const WorkPtrs w = work_ptrs(work, *grid, *params, BSSN_FP64);
+  const double h[3] = {grid->dx, grid->dy, grid->dz};
+  cudaError_t e = cudaMemsetAsync(w.flag, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) e = run_diffs(params->fd_order, BSSN_FP64, *grid, state, w, s);
+  if (e == cudaSuccess) {
+    if (params->fd_order == 4)
+      e = launch_psi4<4>(L, make_coef<4, double>(*grid, 0.0), state, w.dX64, w.dY64, origin, h, psi_re, psi_im,
+                         inv_re, inv_im, E, B, w.flag, s);
+    else
+      e = launch_psi4<8>(L, make_coef<8, double>(*grid, 0.0), state, w.dX64, w.dY64, origin, h, psi_re, psi_im,
+                         inv_re, inv_im, E, B, w.flag, s);
+  }
+  return latch(e);
+}
+
 bssn_status_t bssn_constraints(const bssn_grid_t* grid, const bssn_params_t* params, const double* state, double* ham,
                                double* mom, double* gcon, double* out_l2, double* out_max, void* work,
                                unsigned long long work_bytes, void* stream) {

@@ -34,6 +34,11 @@ cudaError_t launch_constraints(const Layout& L, const Coef<double>& C, const dou
                                const double* dY, double* ham, double* mom, double* gcon, double* part,
                                unsigned int* flag, cudaStream_t s);
 
+template <int P>
+cudaError_t launch_psi4(const Layout& L, const Coef<double>& C, const double* u, const double* dX, const double* dY,
+                        const double origin[3], const double h[3], double* psi_re, double* psi_im, double* inv_re,
+                        double* inv_im, double* E, double* B, unsigned int* flag, cudaStream_t s);
+
 cudaError_t launch_to_f32(const Layout& L, const double* u, float* f, cudaStream_t s);
 
 constexpr int STAGE_THREADS = 128;

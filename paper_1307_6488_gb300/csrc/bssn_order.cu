@@ -1,6 +1,7 @@
 // Instantiates the kernels and launchers for one finite-difference order,
 // selected at compile time with -DBSSN_ORDER=4 or -DBSSN_ORDER=8.
 #include "bssn_kernels.cuh"
+#include "bssn_weyl.cuh"
 #include "bssn_launch.h"
 
 #ifndef BSSN_ORDER
@@ -64,6 +65,17 @@ cudaError_t launch_constraints<BSSN_ORDER>(const Layout& L, const Coef<double>& 
                                            double* gcon, double* part, unsigned int* flag, cudaStream_t s) {
   k_constraints<BSSN_ORDER><<<(unsigned int)con_blocks(L), CON_THREADS, 0, s>>>(L, C, u, dX, dY, ham, mom, gcon,
                                                                                part, flag);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_psi4<BSSN_ORDER>(const Layout& L, const Coef<double>& C, const double* u, const double* dX,
+                                    const double* dY, const double origin[3], const double h[3], double* psi_re,
+                                    double* psi_im, double* inv_re, double* inv_im, double* E, double* B,
+                                    unsigned int* flag, cudaStream_t s) {
+  k_psi4<BSSN_ORDER><<<blocks_for(L.npts, 128), 128, 0, s>>>(L, C, u, dX, dY, origin[0], origin[1], origin[2], h[0],
+                                                             h[1], h[2], psi_re, psi_im, inv_re, inv_im, E, B,
+                                                             flag);
   return cudaGetLastError();
 }
 

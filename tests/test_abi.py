@@ -178,3 +178,25 @@ def test_rk3_rejects_invalid_arguments(L):
                            None) == B.ERR_INVALID_ARG  # static boundary needs ghost_src
     assert L.bssn_rk3_step(ctypes.byref(g), ctypes.byref(p), B.FP64, float("nan"), 0, None, fake, other, fake, big,
                            None) == B.ERR_INVALID_ARG
+
+
+def test_psi4_rejects_invalid_arguments(L):
+    g = B.make_grid(8, ghost=3, dx=0.1)
+    p = B.make_params(fd_order=4)
+    fake = ctypes.c_void_p(4096)
+    big = ctypes.c_ulonglong(1 << 40)
+    L.bssn_psi4.argtypes = [ctypes.POINTER(B.Grid), ctypes.POINTER(B.Params), ctypes.c_void_p,
+                            ctypes.POINTER(ctypes.c_double)] + [ctypes.c_void_p] * 7 + [ctypes.c_ulonglong,
+                                                                                        ctypes.c_void_p]
+    ok = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    nan = (ctypes.c_double * 3)(0.0, float("nan"), 0.0)
+    call = lambda origin, out, work=fake: L.bssn_psi4(ctypes.byref(g), ctypes.byref(p), fake, origin, out, None,
+                                                      None, None, None, None, work, big, None)
+    assert call(None, ctypes.c_void_p(8192)) == B.ERR_INVALID_ARG  # origin required
+    assert call(nan, ctypes.c_void_p(8192)) == B.ERR_INVALID_ARG
+    assert call(ok, fake) == B.ERR_INVALID_ARG  # output may not be the state
+    assert call(ok, ctypes.c_void_p(8200)) == B.ERR_INVALID_ARG  # misaligned output
+    bad8 = B.make_grid(8, ghost=4, dx=0.1)
+    p8 = B.make_params(fd_order=8)
+    assert L.bssn_psi4(ctypes.byref(bad8), ctypes.byref(p8), fake, ok, None, None, None, None, None, None, fake,
+                       big, None) == B.ERR_INVALID_ARG  # ghost 4 < 5 at 8th order
