@@ -209,3 +209,84 @@ def smooth_perturbation(u, g, amplitude, seed, h, periodic=False):
     if periodic:
         periodic_wrap(u, g)
     return u
+
+
+# ------------------------------------------------------------------ patches of a refined hierarchy
+def box_coords(origin, n, g, h, xlo):
+    """Cell-centre coordinates (x, y, z) of the padded points of a patch whose
+    interior is cells [origin, origin + n) of a level with spacing h
+    (scalar or 3) over a domain whose lower corner is xlo."""
+    hh = (h, h, h) if np.isscalar(h) else h
+    return [xlo[a] + (origin[a] + np.arange(-g, n[a] + g) + 0.5) * hh[a] for a in range(3)]
+
+
+def gauge_wave_box(origin, n, g, h, xlo, amplitude=0.01, wavelength=1.0, t=0.0):
+    """The gauge-wave closed form of gauge_wave() at every padded point of a
+    patch (ghosts included, no noise)."""
+    x = box_coords(origin, n, g, h, xlo)[0]
+    A, d = amplitude, wavelength
+    th = 2 * np.pi * (x - t) / d
+    H = 1 - A * np.sin(th)
+    dxH = -(2 * np.pi * A / d) * np.cos(th)
+    Kxx = -(np.pi * A / d) * np.cos(th) / np.sqrt(H)
+    u = empty_state(n[0], n[1], n[2], g)
+
+    def put(name, f1d):
+        u[IDX[name]] = np.broadcast_to(f1d[None, None, :], u.shape[1:])
+
+    put("W", H ** (-1.0 / 6.0))
+    put("gt11", H ** (2.0 / 3.0))
+    put("gt22", H ** (-1.0 / 3.0))
+    put("gt33", H ** (-1.0 / 3.0))
+    put("trK", Kxx / H)
+    put("At11", (2.0 / 3.0) * H ** (-1.0 / 3.0) * Kxx)
+    put("At22", -(1.0 / 3.0) * H ** (-4.0 / 3.0) * Kxx)
+    put("At33", -(1.0 / 3.0) * H ** (-4.0 / 3.0) * Kxx)
+    put("Gt1", (2.0 / 3.0) * H ** (-5.0 / 3.0) * dxH)
+    put("alpha", np.sqrt(H))
+    return u
+
+
+def brill_lindquist_box(origin, n, g, h, xlo, masses=(0.5, 0.5), centers=((-1.5, 0, 0), (1.5, 0, 0))):
+    """Brill-Lindquist data (W = alpha = psi^-2, gt = delta) at every padded
+    point of a patch."""
+    x, y, z = box_coords(origin, n, g, h, xlo)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    psi = np.ones_like(X)
+    for m, c in zip(masses, centers):
+        psi += m / (2 * np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2))
+    u = empty_state(n[0], n[1], n[2], g)
+    u[IDX["W"]] = psi ** -2.0
+    u[IDX["alpha"]] = psi ** -2.0
+    for i in range(3):
+        u[IDX["gt11"] + SYM[i][i]] = 1.0
+    return u
+
+
+def bl_hierarchy(n0=96, nested=4, fine_half=24, split=2, extent=96.0,
+                 centers=((-1.5, 0.0, 0.0), (1.5, 0.0, 0.0))):
+    """Geometry of a properly nested refinement hierarchy for two punctures:
+    level 0 is n0^3 cells over [-extent/2, extent/2]^3 (h0 = extent/n0);
+    each level l = 1 .. nested-1 is n0^3 cells covering the middle half of
+    level l-1; every level is cut into split^3 equal patches. Level `nested`
+    has one box of (2 fine_half)^3 cells per puncture, centred on the
+    puncture's cell (origins even). Returns (ncells, xlo, h0, list of
+    (level, origin, n)); origins are in each level's cell index space."""
+    h0 = extent / n0
+    xlo = (-extent / 2,) * 3
+    out = []
+    s = n0 // split
+    for lev in range(nested):
+        off = (n0 // 2) * (2 ** lev - 1)  # the middle half of every coarser level
+        for k in range(split):
+            for j in range(split):
+                for i in range(split):
+                    out.append((lev, (off + i * s, off + j * s, off + k * s), (s, s, s)))
+    hl = h0 / 2 ** nested
+    for c in centers:
+        org = []
+        for a in range(3):
+            cell = int(np.floor((c[a] - xlo[a]) / hl))
+            org.append(2 * ((cell - fine_half) // 2))
+        out.append((nested, tuple(org), (2 * fine_half,) * 3))
+    return (n0, n0, n0), xlo, h0, out
