@@ -342,6 +342,54 @@ def run_gpu(args):
                 "fd_order": 4, "dt": dtb, "graph_launches_per_step": 1,
                 "kernel_nodes_per_step": 13 if prec == B.FP64 else 17}
 
+    def run_amr(prec):
+        """Berger-Oliger hierarchy around the two punctures: 5 levels, 96^3
+        cells per level on levels 0-3 (h = 1 .. 1/8, each the middle half of
+        the one above, 8 patches each) and two 48^3 boxes at h = 1/16 around
+        the punctures; [-48, 48]^3 with a radiative outer boundary; 8th order,
+        5 ghosts, dt0 = h0/4 with every finer level subcycled by 2. One step
+        is one coarse step (one graph launch): 16.8 M interior updates."""
+        ncells, xlo, h0, geo = inputs.bl_hierarchy()
+        pa = B.make_params(fd_order=ORDER, ko_eps=0.1, lapse=0, shift=0, eta=2.0)
+        states, grids = [], []
+        for (lev, o, nn) in geo:
+            gq = B.make_grid(*nn, ghost=G, dx=h0 / 2 ** lev)
+            st = B.upload(inputs.brill_lindquist_box(o, nn, G, h0 / 2 ** lev, xlo), gq, device=dev)
+            states.append(st)
+            grids.append(gq)
+        t_c = time.perf_counter()
+        h = B.amr_create([(lev, o, nn, gq.var_stride, st, None) for (lev, o, nn), gq, st in zip(geo, grids, states)],
+                         ncells, xlo, h0, G, 2, 0.25 * h0, pa, prec)
+        t_c = time.perf_counter() - t_c
+        try:
+            for _ in range(args.warmup):
+                B.amr_step(h)
+            torch.cuda.synchronize()
+            barrier(world)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                B.amr_step(h)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+            info = B.amr_info(h)
+        finally:
+            B.amr_destroy(h)
+        fine = len(geo) - 2  # first box on the finest level
+        wk = B.alloc_work(grids[fine], pa, device=dev)
+        l2, mx, st = B.constraints(grids[fine], pa, states[fine], wk)
+        del states, wk
+        torch.cuda.empty_cache()
+        return {"value": world * info["updates_per_step"] * args.steps / (ms * 1e-3), "unit": UNIT,
+                "ms_per_step": ms / args.steps, "levels": info["levels"], "patches": len(geo),
+                "updates_per_coarse_step": info["updates_per_step"], "graph_nodes_per_step": info["graph_nodes"],
+                "ghost_entries": info["entries"], "create_s": t_c, "fd_order": ORDER, "boundary": "radiative",
+                "ham_l2_finest_after": float(l2[0]), "steps_after": args.warmup + args.steps,
+                "workload": "Brill-Lindquist (m=0.5 at x=+-1.5), [-48,48]^3, 5 ratio-2 levels (96^3 cells on "
+                            "levels 0-3, 2 x 48^3 at h=1/16), Berger-Oliger subcycling, RK4, 8th order, 5 ghosts"}
+
     def run_rk3(prec):
         """The paper's own integrator (third-order Runge-Kutta, Shu-Osher
         SSP form) on the same 128^3 workload: three fused stages per step,
@@ -642,6 +690,9 @@ def run_gpu(args):
                             "share_of_rk4_step_if_every_step": ms_psi4 / (ms_psi4 + f64["ms"] / args.steps),
                             "outputs": "Psi_4 (re, im), invariant I (re, im), E_ij, B_ij at every interior point"}
     del wout
+    if not args.no_amr:
+        batched["amr_fp64"] = run_amr(B.FP64)
+        batched["amr_fp32_rhs"] = run_amr(B.FP32_RHS)
     batched["rk3_fp64"] = run_rk3(B.FP64)
     batched["rk3_fp32_rhs"] = run_rk3(B.FP32_RHS)
     if not args.no_fp32_config:
@@ -731,6 +782,7 @@ def main():
     ap.add_argument("--grid", type=int, default=N, help="interior points per axis (profiling: smaller cases)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 192-patch batched workload")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-corrector form")
+    ap.add_argument("--no-amr", action="store_true", help="skip the refined-hierarchy (Berger-Oliger) form")
     ap.add_argument("--no-fp32-config", action="store_true",
                     help="skip the FP32-RHS 256^3 throughput and 96^3 100-step accuracy runs")
     ap.add_argument("--learned-pairs", type=int, default=200,

@@ -273,6 +273,89 @@ bssn_status_t bssn_restrict(const bssn_grid_t* fine, const double* fine_state, c
 bssn_status_t bssn_prolong(const bssn_grid_t* coarse, const double* coarse_state, const bssn_grid_t* fine,
                            double* fine_state, void* stream);
 
+/* ---------------------------------------------------------------- refined hierarchy (Berger-Oliger)
+ * Time stepping of a hierarchy of patches refined by 2 per level in space
+ * and time, the block-structured adaptive refinement the paper runs through
+ * Carpet and plans for its GPU framework (Sec. 1.1, Sec. 4). Level l has
+ * spacing h0/2^l and cells [0, ncells * 2^l) per axis; cell I of level l is
+ * centred at xlo + (I + 1/2) h_l, so fine cells 2c, 2c+1 lie in coarse cell
+ * c. A patch is the box of cells [o, o+n) of one level plus `ghost` ghost
+ * cells on every side, stored like any state (interior point (0,0,0) = cell
+ * o). One bssn_amr_step advances level 0 by dt0 with classic RK4 and every
+ * finer level by two steps of half its parent's (recursively), then
+ * restricts each level into its parent.
+ *
+ * Ghost cells, decided once at creation (first rule that applies):
+ *   1. level 0 of a bounded domain, cell outside it: boundary 1 (static)
+ *      copies the patch's ghost_src value; boundary 2 (radiative) evolves it
+ *      with the stages by the Sommerfeld condition
+ *        d_t u = -v (x^i/r) d_i u - v (u - u_inf)/r,
+ *      r from the coordinate origin, d_i second-order differences (centred,
+ *      one-sided on the faces of the patch's padded box), u_inf flat space,
+ *      v = sqrt(2) for alpha and trK under 1+log slicing, else 1;
+ *   2. a copy from the first patch of the same level (input order, itself
+ *      included, periodic images for boundary 0) whose interior holds it;
+ *   3. level >= 1: tricubic prolongation from the first coarser patch whose
+ *      interior holds the 4 x 4 x 4 coarse stencil, else the first whose
+ *      padded box does, applied to that patch's RK4 stage states so that
+ *      each fine stage input gets the value RK4 makes there (a Taylor
+ *      expansion of RK4's third-order continuous extension);
+ *   4. otherwise the hierarchy is not properly nested: creation fails with
+ *      BSSN_ERR_INVALID_ARG.
+ * Restriction: a coarse interior cell whose fine stencil 2c-1..2c+2 lies in
+ * the interior of one finer patch (the first such) takes the tricubic value
+ * at its centre (1D weights (-1,9,9,-1)/16).
+ */
+typedef struct bssn_amr bssn_amr_t;
+
+typedef struct {
+  int level;                 /* 0 = coarsest; levels must be contiguous from 0   */
+  int ox, oy, oz;            /* first interior cell in the level's index space  */
+  int nx, ny, nz;            /* interior cells, >= 1, inside the level's domain */
+  long long var_stride;      /* elements between variables (even, >= padded)    */
+  double* state;             /* DEVICE, caller-owned, 16-B aligned: initial data
+                                with ghosts in, the evolved state out            */
+  const double* ghost_src;   /* DEVICE; boundary 1 on level 0: the patch's t = 0
+                                state (ghost values); otherwise ignored (NULL)   */
+} bssn_amr_patch_t;
+
+typedef struct {
+  int ncells[3];             /* level-0 domain cells per axis                   */
+  double xlo[3];             /* lower corner of the domain                      */
+  double h0[3];              /* level-0 spacing                                 */
+  int ghost;                 /* >= 3 (4th order) or >= 5 (8th order), <= 16     */
+  int boundary;              /* 0 periodic, 1 static, 2 radiative (Sommerfeld)  */
+  double dt0;                /* level-0 time step; level l steps dt0 / 2^l      */
+} bssn_amr_desc_t;
+
+/* Builds the hierarchy's ghost/restriction maps and allocates, per patch,
+ * three stage buffers (five on levels that have a finer level) and the
+ * difference tables. The caller keeps ownership of every state and
+ * ghost_src, which must stay valid until bssn_amr_destroy. Synchronizes.
+ * BSSN_ERR_NOMEM if the device allocations fail. */
+bssn_status_t bssn_amr_create(bssn_amr_t** out, const bssn_amr_patch_t* patches, int npatches,
+                              const bssn_amr_desc_t* desc, const bssn_params_t* params, bssn_precision_t prec);
+/* One level-0 step (and 2^l steps of every level l) on `stream`, as one CUDA
+ * graph launch (captured at the first call on a private stream). */
+bssn_status_t bssn_amr_step(bssn_amr_t* amr, void* stream);
+/* HOST outputs (nullable): interior point updates per step (sum of n 2^l),
+ * number of levels, entry counts {ghost copies, prolonged ghosts, static
+ * ghosts, radiative ghosts, restricted cells}, and the graph's node count
+ * (0 before the first step). */
+bssn_status_t bssn_amr_info(const bssn_amr_t* amr, long long* updates_per_step, int* nlevels, long long* entries,
+                            long long* graph_nodes);
+/* Frees everything the hierarchy owns (synchronizes the device). */
+bssn_status_t bssn_amr_destroy(bssn_amr_t* amr);
+
+/* The Sommerfeld right-hand side above, evaluated at every point (interior
+ * and ghost) of one grid: rhs[v] = -v (x^i/r) d_i state[v] - v (state[v] -
+ * u_inf[v])/r, where x of padded point (i,j,k) is xyz0 + (i dx, j dy, k dz)
+ * (xyz0: HOST array of 3, the coordinates of padded point (0,0,0)). The
+ * boundary kernel of Sec. 3.3 in radiative form; the paper does not name the
+ * condition. The origin must not be a grid point. */
+bssn_status_t bssn_sommerfeld_rhs(const bssn_grid_t* grid, const bssn_params_t* params, const double* xyz0,
+                                  const double* state, double* rhs, void* stream);
+
 /* ---------------------------------------------------------------- learned corrector
  * A 3D convolutional network that corrects a coarse-grid RK4 step towards
  * the restricted fine-grid step: 5 layers of 3x3x3 convolutions, channels

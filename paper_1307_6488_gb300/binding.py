@@ -482,3 +482,69 @@ def upload(state_np, grid, out=None, device="cuda"):
 
 def download(flat, grid, nvar=NVAR):
     return view4(flat, grid, nvar).cpu().numpy()
+
+
+# ------------------------------------------------------------------ refined hierarchy (Berger-Oliger)
+class AmrPatch(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int), ("ox", ctypes.c_int), ("oy", ctypes.c_int), ("oz", ctypes.c_int),
+                ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("var_stride", ctypes.c_longlong),
+                ("state", ctypes.c_void_p), ("ghost_src", ctypes.c_void_p)]
+
+
+class AmrDesc(ctypes.Structure):
+    _fields_ = [("ncells", ctypes.c_int * 3), ("xlo", ctypes.c_double * 3), ("h0", ctypes.c_double * 3),
+                ("ghost", ctypes.c_int), ("boundary", ctypes.c_int), ("dt0", ctypes.c_double)]
+
+
+def _amr_lib():
+    L = lib()
+    if not getattr(L, "_amr_typed", False):
+        L.bssn_amr_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(AmrPatch), ctypes.c_int,
+                                      ctypes.POINTER(AmrDesc), ctypes.POINTER(Params), ctypes.c_int]
+        L.bssn_amr_step.argtypes = [_p, _p]
+        L.bssn_amr_info.argtypes = [_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int), _p,
+                                    ctypes.POINTER(ctypes.c_longlong)]
+        L.bssn_amr_destroy.argtypes = [_p]
+        L.bssn_sommerfeld_rhs.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Params), _p, _p, _p, _p]
+        for n in ("bssn_amr_create", "bssn_amr_step", "bssn_amr_info", "bssn_amr_destroy", "bssn_sommerfeld_rhs"):
+            getattr(L, n).restype = ctypes.c_int
+        L._amr_typed = True
+    return L
+
+
+def amr_create(patches, ncells, xlo, h0, ghost, boundary, dt0, params, prec=FP64):
+    """patches: list of (level, origin (3), n (3), var_stride, state, ghost_src
+    or None) with device tensors/addresses. Returns an opaque handle (int)."""
+    arr = (AmrPatch * len(patches))(*[AmrPatch(lv, o[0], o[1], o[2], n[0], n[1], n[2], vs, _ptr(s), _ptr(src))
+                                      for (lv, o, n, vs, s, src) in patches])
+    h0 = (h0,) * 3 if np.isscalar(h0) else tuple(h0)
+    d = AmrDesc((ctypes.c_int * 3)(*ncells), (ctypes.c_double * 3)(*xlo), (ctypes.c_double * 3)(*h0), ghost,
+                boundary, dt0)
+    h = ctypes.c_void_p()
+    _check(_amr_lib().bssn_amr_create(ctypes.byref(h), arr, len(patches), ctypes.byref(d), ctypes.byref(params),
+                                      prec), "amr_create")
+    return h.value
+
+
+def amr_step(amr, stream=None):
+    _check(_amr_lib().bssn_amr_step(amr, _stream(stream)), "amr_step")
+
+
+def amr_info(amr):
+    upd, nodes = ctypes.c_longlong(), ctypes.c_longlong()
+    nlev = ctypes.c_int()
+    ent = np.zeros(5, dtype=np.int64)
+    _check(_amr_lib().bssn_amr_info(amr, ctypes.byref(upd), ctypes.byref(nlev), ent.ctypes.data_as(_p),
+                                    ctypes.byref(nodes)), "amr_info")
+    return dict(updates_per_step=upd.value, levels=nlev.value, graph_nodes=nodes.value,
+                entries=dict(zip(["copy", "prolong", "static", "radiative", "restrict"], (int(x) for x in ent))))
+
+
+def amr_destroy(amr):
+    _check(_amr_lib().bssn_amr_destroy(amr), "amr_destroy")
+
+
+def sommerfeld_rhs(grid, params, xyz0, state, out, stream=None):
+    xyz = np.ascontiguousarray(xyz0, dtype=np.float64)
+    _check(_amr_lib().bssn_sommerfeld_rhs(ctypes.byref(grid), ctypes.byref(params), xyz.ctypes.data_as(_p),
+                                          _ptr(state), _ptr(out), _stream(stream)), "sommerfeld_rhs")

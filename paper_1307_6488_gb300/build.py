@@ -23,6 +23,7 @@ UNITS = [
     ("bssn_batch.cu", "bssn_batch.o", []),
     ("bssn_corrector.cu", "bssn_corrector.o", []),
     ("bssn_transfer.cu", "bssn_transfer.o", []),
+    ("bssn_amr.cu", "bssn_amr.o", []),
 ]
 
 

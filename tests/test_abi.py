@@ -200,3 +200,44 @@ def test_psi4_rejects_invalid_arguments(L):
     p8 = B.make_params(fd_order=8)
     assert L.bssn_psi4(ctypes.byref(bad8), ctypes.byref(p8), fake, ok, None, None, None, None, None, None, fake,
                        big, None) == B.ERR_INVALID_ARG  # ghost 4 < 5 at 8th order
+
+
+def test_amr_rejects_invalid_arguments(L):
+    """Host-side checks of the refined-hierarchy entry points: each call is
+    invalid for a reason checked before any allocation or launch."""
+    p4 = B.make_params(fd_order=4)
+    g = 4
+    vs = (8 + 2 * g) ** 3
+
+    def create(patches, ncells=(8, 8, 8), ghost=g, boundary=2, dt0=0.1, params=p4, prec=B.FP64, h0=1.0):
+        with pytest.raises(B.BssnError) as e:
+            B.amr_create(patches, ncells, (-4.0, -4.0, -4.0), h0, ghost, boundary, dt0, params, prec)
+        return e.value.status
+
+    good = (0, (0, 0, 0), (8, 8, 8), vs, FAKE, None)
+    E = B.ERR_INVALID_ARG
+    assert create([good], ghost=2) == E                              # ghost < 3 at 4th order
+    assert create([good], ghost=4, params=B.make_params(fd_order=8)) == E  # ghost < 5 at 8th order
+    assert create([good], boundary=3) == E
+    assert create([good], dt0=float("nan")) == E
+    assert create([good], h0=0.0) == E
+    assert create([good], prec=4) == E
+    assert create([good], params=B.make_params(fd_order=6)) == E
+    assert create([(0, (1, 0, 0), (8, 8, 8), vs, FAKE, None)]) == E   # outside the level-0 domain
+    assert create([good, (1, (12, 4, 4), (8, 8, 8), vs, FAKE, None)]) == E  # outside the level-1 domain
+    assert create([good, (2, (8, 8, 8), (8, 8, 8), vs, FAKE, None)]) == E   # level 1 missing
+    assert create([(0, (0, 0, 0), (8, 8, 8), vs - 2, FAKE, None)]) == E     # var_stride too small
+    assert create([(0, (0, 0, 0), (8, 8, 8), vs, FAKE + 8, None)]) == E     # misaligned state
+    assert create([good], boundary=1) == E                           # static boundary needs ghost_src
+    assert create([(0, (0, 0, 0), (8, 8, 8), vs, FAKE, FAKE)], boundary=1) == E  # ghost_src is the state
+    assert create([]) == E
+    assert L.bssn_amr_destroy(None) == E
+    assert L.bssn_amr_step(None, None) == E
+    grid = B.make_grid(8, ghost=3, dx=0.1)
+    with pytest.raises(B.BssnError) as e:
+        B.sommerfeld_rhs(grid, p4, (1.0, 2.0, 3.0), FAKE, FAKE, stream=0)  # output is the state
+    assert e.value.status == E
+    with pytest.raises(B.BssnError) as e:
+        B.sommerfeld_rhs(B.make_grid(8, ghost=0, dx=0.1), p4, (1.0, 2.0, 3.0), FAKE, FAKE * 2, stream=0)
+    assert e.value.status == E
+    assert B.last_error() == B.OK
