@@ -35,10 +35,12 @@ Ghost points (global index G of a ghost cell of patch b at level l)
      same stage.
   3. otherwise (l >= 1), prolongation from level l-1: the tricubic Lagrange
      interpolant through the 4 nearest coarse centres per axis (fine G sits
-     at coarse coordinate G/2 - 1/4) of the first coarse patch whose
-     interior fits the 4-cell run on every axis, else of the first whose
-     padded box does, applied to the parent's RK4 stage states of its
-     latest step (see "Ghost values in time").
+     at coarse coordinate G/2 - 1/4), applied to the parent level's RK4
+     stage states of its latest step (see "Ghost values in time"). The
+     parent level is read as one field on cells: coarse cell C takes its
+     value from the first level-(l-1) patch whose interior fits C, else from
+     the first whose padded box does (where a padded box holds a ghost copy
+     of another patch's interior cell, both give the same value).
   4. anything else is an error (the hierarchy is not properly nested).
 
 Ghost values in time. The parent's step t -> t + dt keeps its stage states
@@ -230,6 +232,7 @@ class Hierarchy:
             if np.any(q.o < 0) or np.any(q.o + q.n > top) or np.any(q.n < 1):
                 raise ValueError("every patch must lie inside its level's domain")
         self.speeds = radiative_speeds(params)
+        self._pcache = {}
         self.plans = [self._ghost_plan(b) for b in range(len(self.P))]
         self.rplans = [self._restrict_plan(b) for b in range(len(self.P))]
 
@@ -270,29 +273,49 @@ class Hierarchy:
                 todo &= ~ok
         if l >= 1 and todo.any():
             base = np.where(G % 2 == 0, G // 2 - 2, G // 2 - 1)
-            cper = self.period(l - 1)
-            for padded in (False, True):
-                for s in self.at[l - 1]:
-                    if not todo.any():
-                        break
-                    r = self.P[s]
-                    ok = todo.copy()
-                    lo_idx = []
-                    for a in range(3):
-                        blo = r.o[a] - (g if padded else 0)
-                        bhi = r.o[a] + r.n[a] + (g if padded else 0)
-                        fit, sh = _fit(base[a], 4, blo, bhi, None if cper is None else cper[a])
-                        ok &= fit
-                        lo_idx.append(sh - r.o[a] + g)
-                    if ok.any():
-                        # coarse coordinate of the fine centre, relative to the first node
-                        x = [(0.5 * G[a][ok] - 0.25) - base[a][ok] for a in range(3)]
-                        w = [lagrange_weights(x[a], [0.0, 1.0, 2.0, 3.0]) for a in range(3)]
-                        plan["prolong"].append((s, ok, [lo_idx[a][ok] for a in range(3)], w))
-                        todo &= ~ok
+            sel = todo.copy()
+            Gs, bs = G[:, sel], base[:, sel]
+            # 64 stencil cells per ghost point: source patch and padded index
+            cells = []
+            ok = np.ones(Gs.shape[1], dtype=bool)
+            for a3 in range(4):
+                for a2 in range(4):
+                    for a1 in range(4):
+                        C = np.stack([bs[0] + a1, bs[1] + a2, bs[2] + a3])
+                        src, idx = self._coarse_cells(l - 1, C)
+                        ok &= src >= 0
+                        cells.append((src, idx))
+            if not ok.all():
+                raise ValueError(f"patch {b}: ghost points whose coarse stencil has no source (not properly nested)")
+            x = [(0.5 * Gs[a] - 0.25) - bs[a] for a in range(3)]
+            w = [lagrange_weights(x[a], [0.0, 1.0, 2.0, 3.0]) for a in range(3)]
+            plan["prolong"].append((sel, cells, w))
+            todo &= ~sel
         if todo.any():
             raise ValueError(f"patch {b}: {int(todo.sum())} ghost points have no source (not properly nested)")
         return plan
+
+    def _coarse_cells(self, l, C):
+        """Source of level-l cells C (3, count): the first patch whose
+        interior fits the cell, else the first whose padded box does.
+        Returns (patch index or -1, padded (z, y, x) indices)."""
+        g = self.g
+        per = self.period(l)
+        src = np.full(C.shape[1], -1, dtype=np.int64)
+        idx = np.zeros((3, C.shape[1]), dtype=np.int64)
+        for pad in (0, g):
+            for s in self.at[l]:
+                r = self.P[s]
+                ok = src < 0
+                loc = []
+                for a in range(3):
+                    fit, sh = _fit(C[a], 1, r.o[a] - pad, r.o[a] + r.n[a] + pad, None if per is None else per[a])
+                    ok &= fit
+                    loc.append(sh - r.o[a] + g)
+                src[ok] = s
+                for a in range(3):
+                    idx[2 - a][ok] = loc[a][ok]
+        return src, idx
 
     def _restrict_plan(self, b):
         """Coarse interior cells of patch b and their fine sources (level l+1)."""
@@ -335,6 +358,26 @@ class Hierarchy:
                     s = s + (np.asarray(wz[a]) * np.asarray(wy[bb]) * np.asarray(wx[c])) * u[:, lz + a, ly + bb, lx + c]
         return s
 
+    def _prolong(self, cells, w, j):
+        """Tricubic interpolant of stage state j of the parent level (j = 0:
+        y0; j = 1..4: D_j = S_j - y0, formed cell by cell) at the fine
+        points; cells[a3*16 + a2*4 + a1] = (source patch, (z, y, x))."""
+        wx, wy, wz = w
+        out = 0.0
+        for a3 in range(4):
+            for a2 in range(4):
+                for a1 in range(4):
+                    src, (iz, iy, ix) = cells[a3 * 16 + a2 * 4 + a1]
+                    v = np.empty((24, src.size))
+                    for s in np.unique(src):
+                        m = src == s
+                        st = self.P[s].stages
+                        v[:, m] = st[0][:, iz[m], iy[m], ix[m]]
+                        if j > 0:
+                            v[:, m] = st[j][:, iz[m], iy[m], ix[m]] - v[:, m]
+                    out = out + (wz[a3] * wy[a2] * wx[a1]) * v
+        return out
+
     def _fill(self, l, arrays, m, s):
         """Set the ghosts of level l's arrays (list indexed like self.P) for
         the input of fine stage s (0..3) of half m of the parent's step, or
@@ -350,12 +393,16 @@ class Hierarchy:
                 u[:, gz[ok], gy[ok], gx[ok]] = arrays[sib][:, src[0], src[1], src[2]]
             if pl["prolong"]:
                 d = fine_ghost_coeffs(m, s)
-                for par, ok, lo, w in pl["prolong"]:
-                    st = self.P[par].stages
-                    val = self._interp(st[0], lo, w)
+                for gi, (ok, cells, w) in enumerate(pl["prolong"]):
+                    # P[y0], P[D2..D5] depend only on the parent level's latest step
+                    key = (b, gi)
+                    if key not in self._pcache:
+                        self._pcache[key] = [self._prolong(cells, w, j) for j in range(5)]
+                    Pj = self._pcache[key]
+                    val = Pj[0]
                     for j in range(4):
                         if d[j] != 0.0:
-                            val = val + d[j] * self._interp(st[j + 1] - st[0], lo, w)
+                            val = val + d[j] * Pj[j + 1]
                     u[:, gz[ok], gy[ok], gx[ok]] = val
 
     def _restrict(self, l):
@@ -409,6 +456,9 @@ class Hierarchy:
         if l + 1 < self.nlev:
             for b in bs:
                 self.P[b].stages = tuple(kept[b]) + (self.P[b].state.copy(),)
+            for b in self.at[l + 1]:
+                for key in [k for k in self._pcache if k[0] == b]:
+                    del self._pcache[key]
             self._advance(l + 1, 0)
             self._advance(l + 1, 1)
             self._restrict(l)
