@@ -248,7 +248,7 @@ def run_gpu(args):
     yb = B.alloc_state(grid, device=dev)
     acc = B.alloc_state(grid, device=dev)
     work = B.alloc_work(grid, p, device=dev)
-    rates = None if (args.profile or args.corrector_only) else B.probe_fp_rates()
+    rates = None if (args.profile or args.corrector_only or args.amr_only) else B.probe_fp_rates()
 
     def run_form(prec, sample_clocks):
         state = state0.clone()
@@ -412,6 +412,53 @@ def run_gpu(args):
         del bufs, wk
         return {"value": world * n ** 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "stages_per_step": 3,
                 "ham_l2_after": float(l2[0]), "steps": args.steps + args.warmup}
+
+    def run_paper_shape(nn, lo, hi, prec, method, steps):
+        """A uniform Brill-Lindquist grid in one of the paper's own shapes,
+        8th order, 5 ghosts, static boundary, timed through bssn_rk3_step
+        (method 3, the paper's integrator) or bssn_rk4_step (method 4)."""
+        uu, hh = inputs.brill_lindquist(nn, G, lo=lo, hi=hi)
+        gq = B.make_grid(nn, ghost=G, dx=hh)
+        st = B.upload(uu, gq, device=dev)
+        src = st.clone()
+        del uu
+        bufs = torch.empty((2 if method == 3 else 3) * 24 * gq.var_stride, dtype=torch.float64, device=dev)
+        wk = B.alloc_work(gq, p, prec, device=dev)
+        stepf = B.rk3_step if method == 3 else B.rk4_step
+        dtq = 0.25 * hh
+        for _ in range(args.warmup):
+            stepf(gq, p, prec, dtq, 1, src, st, bufs, wk)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            stepf(gq, p, prec, dtq, 1, src, st, bufs, wk)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        del st, src, bufs, wk
+        torch.cuda.empty_cache()
+        return ms
+
+    def run_paper_shapes():
+        """The paper's two GPU configurations with Brill-Lindquist data in
+        place of its QC-0 data: its single-GPU benchmark, 100^3 evolved
+        points + 5 ghosts at 8th order (Sec. 4), and its binary-black-hole
+        grid, 270^3 points on [-6.75, 6.75]^3, 8th order, RK3 (Sec. 3.3), which
+        the paper spread over 27 GPUs and which fits one GB300."""
+        out = {}
+        ms = run_paper_shape(100, -8.0, 8.0, B.FP64, 3, args.steps)
+        rhs_flops = flops["rhs"]
+        out["benchmark_100^3_rk3_fp64"] = {
+            "value": world * 100 ** 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "rhs_gflops": world * 3 * rhs_flops * 100 ** 3 / (ms * 1e-3) / 1e9,
+            "paper_context": "25 GFlop/s on one NVIDIA M2050 (Fermi), same grid shape, McLachlan's own flop count"}
+        for prec, name in ((B.FP64, "fp64"), (B.FP32_RHS, "fp32_rhs")):
+            ms = run_paper_shape(270, -6.75, 6.75, prec, 3, max(1, min(args.steps, 3)))
+            out[f"bbh_270^3_rk3_{name}"] = {"value": world * 270 ** 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                                           "paper_context": "27 NVIDIA M2050 GPUs at 90^3 points each"}
+        return out
 
     def run_fp32_config():
         """FP32-RHS against FP64 as stated for that form: throughput of both at
@@ -652,6 +699,13 @@ def run_gpu(args):
                               "ms_per_forward_1_sample": ms_fwd}))
         return
 
+    if args.amr_only:
+        # the refined-hierarchy forms alone (for ncu launch lists)
+        res = {"amr_fp64": run_amr(B.FP64), "amr_fp32_rhs": run_amr(B.FP32_RHS)}
+        if rank == 0:
+            print(json.dumps({"amr_only": True, **res}))
+        return
+
     f64 = run_form(B.FP64, not args.profile)
     f32 = run_form(B.FP32_RHS, False)
     if args.profile:
@@ -690,6 +744,7 @@ def run_gpu(args):
                             "share_of_rk4_step_if_every_step": ms_psi4 / (ms_psi4 + f64["ms"] / args.steps),
                             "outputs": "Psi_4 (re, im), invariant I (re, im), E_ij, B_ij at every interior point"}
     del wout
+    batched["paper_shapes"] = run_paper_shapes()
     if not args.no_amr:
         batched["amr_fp64"] = run_amr(B.FP64)
         batched["amr_fp32_rhs"] = run_amr(B.FP32_RHS)
@@ -783,6 +838,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 192-patch batched workload")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-corrector form")
     ap.add_argument("--no-amr", action="store_true", help="skip the refined-hierarchy (Berger-Oliger) form")
+    ap.add_argument("--amr-only", action="store_true",
+                    help="run only the refined-hierarchy forms (FP64 and FP32-RHS) and print their numbers")
     ap.add_argument("--no-fp32-config", action="store_true",
                     help="skip the FP32-RHS 256^3 throughput and 96^3 100-step accuracy runs")
     ap.add_argument("--learned-pairs", type=int, default=200,

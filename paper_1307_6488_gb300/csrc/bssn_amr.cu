@@ -312,12 +312,12 @@ __global__ void __launch_bounds__(ENTRY_THREADS) ka_restrict(const RestrictEntry
 // --- Sommerfeld outer boundary -------------------------------------------------------------
 
 // Second-order first difference along one axis at padded index i of e
-// points: centred inside, one-sided on the two faces (stored-value
+// points, times 2h: centred inside, one-sided on the two faces (stored-value
 // differences first, so a constant gives exactly zero).
-__device__ __forceinline__ double diff2(const double* u, long long p, int i, int e, long long s, double h) {
-  if (i == 0) return (4.0 * (u[p + s] - u[p]) - (u[p + 2 * s] - u[p])) / (2.0 * h);
-  if (i == e - 1) return -(4.0 * (u[p - s] - u[p]) - (u[p - 2 * s] - u[p])) / (2.0 * h);
-  return (u[p + s] - u[p - s]) / (2.0 * h);
+__device__ __forceinline__ double diff2(const double* u, long long p, int i, int e, long long s) {
+  if (i == 0) return 4.0 * (u[p + s] - u[p]) - (u[p + 2 * s] - u[p]);
+  if (i == e - 1) return -(4.0 * (u[p - s] - u[p]) - (u[p - 2 * s] - u[p]));
+  return u[p + s] - u[p - s];
 }
 
 // Asymptotic (flat) value of variable v: 1 for W, gt11, gt22, gt33, alpha.
@@ -325,16 +325,16 @@ __device__ __forceinline__ double flat_value(int v) {
   return (v == V_W || v == V_GT11 || v == V_GT22 || v == V_GT33 || v == V_ALPHA) ? 1.0 : 0.0;
 }
 
-// d_t u = -v (x^i/r) d_i u - v (u - u_inf)/r of variable v at padded (i,j,k).
+// d_t u = -v (x^i/r) d_i u - v (u - u_inf)/r of variable v at padded (i,j,k);
+// the reciprocals 1/(2h) per axis and 1/r are passed in (no FP64 division).
 __device__ __forceinline__ double sommerfeld_point(const double* u, const Layout& L, int i, int j, int k, double x,
-                                                   double y, double z, double hx, double hy, double hz,
-                                                   double speed, double uinf) {
+                                                   double y, double z, double i2hx, double i2hy, double i2hz,
+                                                   double inv_r, double speed, double uinf) {
   const long long p = i + j * L.sy + k * L.sz;
-  const double dx = diff2(u, p, i, L.nx + 2 * L.g, 1, hx);
-  const double dy = diff2(u, p, j, L.ny + 2 * L.g, L.sy, hy);
-  const double dz = diff2(u, p, k, L.nz + 2 * L.g, L.sz, hz);
-  const double r = sqrt(x * x + y * y + z * z);
-  return -speed * (x * dx + y * dy + z * dz) / r - speed * (u[p] - uinf) / r;
+  const double dx = diff2(u, p, i, L.nx + 2 * L.g, 1) * i2hx;
+  const double dy = diff2(u, p, j, L.ny + 2 * L.g, L.sy) * i2hy;
+  const double dz = diff2(u, p, k, L.nz + 2 * L.g, L.sz) * i2hz;
+  return -speed * ((x * dx + y * dy + z * dz) + (u[p] - uinf)) * inv_r;
 }
 
 // Radiative ghosts of level 0 advanced as one RK4 stage (same combination
@@ -347,12 +347,13 @@ __global__ void __launch_bounds__(ENTRY_THREADS) ka_radiative(const RadEntry* __
     const PatchDev& D = P[e.patch];
     const Layout& L = D.L;
     const long long p = e.i + e.j * L.sy + e.k * L.sz;
+    const double inv_r = 1.0 / sqrt(e.x * e.x + e.y * e.y + e.z * e.z);
 #pragma unroll 1
     for (int v = 0; v < NV; ++v) {
       const long long o = v * L.vs;
       const double speed = (v == V_ALPHA || v == V_TRK) ? v_gauge : 1.0;
-      const double kv = sommerfeld_point(D.buf[in] + o, L, e.i, e.j, e.k, e.x, e.y, e.z, hx, hy, hz, speed,
-                                         flat_value(v));
+      const double kv = sommerfeld_point(D.buf[in] + o, L, e.i, e.j, e.k, e.x, e.y, e.z, 0.5 / hx, 0.5 / hy, 0.5 / hz,
+                                         inv_r, speed, flat_value(v));
       const double y0 = D.buf[0][o + p];
       double* acc = D.buf[3] + o + p;
       double* yn = D.buf[out] + o + p;
@@ -382,9 +383,11 @@ __global__ void __launch_bounds__(ENTRY_THREADS) ka_sommerfeld_grid(Layout L, co
     const int j = (int)((t / ex) % ey);
     const int k = (int)(t / (ex * ey));
     const double x = x0 + i * hx, y = y0 + j * hy, z = z0 + k * hz;
+    const double inv_r = 1.0 / sqrt(x * x + y * y + z * z);
     for (int v = 0; v < NV; ++v) {
       const double speed = (v == V_ALPHA || v == V_TRK) ? v_gauge : 1.0;
-      rhs[v * L.vs + t] = sommerfeld_point(u + v * L.vs, L, i, j, k, x, y, z, hx, hy, hz, speed, flat_value(v));
+      rhs[v * L.vs + t] = sommerfeld_point(u + v * L.vs, L, i, j, k, x, y, z, 0.5 / hx, 0.5 / hy, 0.5 / hz, inv_r,
+                                           speed, flat_value(v));
     }
   }
 }
