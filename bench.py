@@ -248,7 +248,7 @@ def run_gpu(args):
     yb = B.alloc_state(grid, device=dev)
     acc = B.alloc_state(grid, device=dev)
     work = B.alloc_work(grid, p, device=dev)
-    rates = None if (args.profile or args.corrector_only or args.amr_only) else B.probe_fp_rates()
+    rates = None if (args.profile or args.corrector_only or args.amr_only or args.cfd_only) else B.probe_fp_rates()
 
     def run_form(prec, sample_clocks):
         state = state0.clone()
@@ -459,6 +459,63 @@ def run_gpu(args):
             out[f"bbh_270^3_rk3_{name}"] = {"value": world * 270 ** 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
                                            "paper_context": "27 NVIDIA M2050 GPUs at 90^3 points each"}
         return out
+
+    def run_cfd():
+        """The paper's CFD benchmark shape (Sec. 4): incompressible Navier-Stokes
+        by SOLA in single precision on 256^3 cells, three kernels (velocity,
+        4 red-black mass-conservation iterations, boundary after each). Here a
+        lid-driven cavity (no-slip walls, lid speed 1, nu = 1e-3, i.e. Re =
+        1000 on the unit box), dt = h/4, omega = 1.7, donor fraction 0.3,
+        starting from rest. One step is one bssn_cfd_step call."""
+        Nc = 256
+        hc = 1.0 / Nc
+        d = B.make_cfd((Nc, Nc, Nc), hc, (0, 0, 0), nu=1e-3, dt=0.25 * hc, omega=1.7, alpha=0.3, lid=1.0)
+        npts = B.cfd_points(d)
+        u_, v_, w_, p_ = (torch.zeros(npts, dtype=torch.float32, device=dev) for _ in range(4))
+        scratch = torch.zeros(3 * ((npts + 3) // 4 * 4), dtype=torch.float32, device=dev)
+        iters = 4
+        for _ in range(args.warmup):
+            B.cfd_step(d, iters, u_, v_, w_, p_, scratch)
+        torch.cuda.synchronize()
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            B.cfd_step(d, iters, u_, v_, w_, p_, scratch)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), world, dev) / args.steps
+        # the dominant kernel alone: mass-conservation half-sweeps, CUDA events
+        # on the launching stream
+        ev = []
+        for it in range(2 * args.steps):
+            ev.append(torch.cuda.Event(enable_timing=True))
+            ev[-1].record(stream)
+            B.cfd_mass(d, it % 2, u_, v_, w_, p_)
+            ev.append(torch.cuda.Event(enable_timing=True))
+            ev[-1].record(stream)
+        torch.cuda.synchronize()
+        mass_ms = float(np.mean([ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(len(ev) // 2)]))
+        cells = Nc ** 3
+        # algorithmic bytes per cell and half-sweep: u, v, w read and every face
+        # written once (12 + 12), p read and written for half the cells (2 + 2)
+        mass_bytes = 28.0 * cells
+        hbm = MEASURED.get("hbm_gbs")
+        fin = bool(torch.isfinite(u_).all() and torch.isfinite(p_).all())
+        umax = float(u_.view(Nc + 2, Nc + 2, Nc + 2)[1:-1, 1:-1, 1:-1].abs().max())  # interior (the lid ghost is 2U - u)
+        del u_, v_, w_, p_, scratch
+        torch.cuda.empty_cache()
+        return {"value": world * cells / (ms * 1e-3), "unit": "cell updates/s", "ms_per_step": ms,
+                "mass_iterations_per_step": iters, "gflops_algorithmic": world * 295 * cells / (ms * 1e-3) / 1e9,
+                "flops_per_cell_step": 295, "finite": fin, "max_abs_u_interior": umax,
+                "roofline": {"bound": "hbm", "kernel": "k_cfd_mass (one red-black half-sweep)",
+                             "achieved": mass_bytes / (mass_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                             "frac": (mass_bytes / (mass_ms * 1e-3) / 1e9 / hbm) if hbm else None,
+                             "launch_ms": mass_ms, "bytes_per_cell": 28},
+                "paper_context": "90.5 GFlop/s (Chemora) and 43 GFlop/s (Physis) on one NVIDIA M2050, 256^3, "
+                                 "the paper's own flop count",
+                "workload": "lid-driven cavity 256^3, FP32, Re 1000, SOLA, 4 mass iterations per step"}
 
     def run_fp32_config():
         """FP32-RHS against FP64 as stated for that form: throughput of both at
@@ -699,6 +756,12 @@ def run_gpu(args):
                               "ms_per_forward_1_sample": ms_fwd}))
         return
 
+    if args.cfd_only:
+        res = run_cfd()
+        if rank == 0:
+            print(json.dumps({"cfd_only": True, **res}))
+        return
+
     if args.amr_only:
         # the refined-hierarchy forms alone (for ncu launch lists)
         res = {"amr_fp64": run_amr(B.FP64), "amr_fp32_rhs": run_amr(B.FP32_RHS)}
@@ -745,6 +808,8 @@ def run_gpu(args):
                             "outputs": "Psi_4 (re, im), invariant I (re, im), E_ij, B_ij at every interior point"}
     del wout
     batched["paper_shapes"] = run_paper_shapes()
+    if not args.no_cfd:
+        batched["cfd_sola_256"] = run_cfd()
     if not args.no_amr:
         batched["amr_fp64"] = run_amr(B.FP64)
         batched["amr_fp32_rhs"] = run_amr(B.FP32_RHS)
@@ -838,6 +903,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 192-patch batched workload")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-corrector form")
     ap.add_argument("--no-amr", action="store_true", help="skip the refined-hierarchy (Berger-Oliger) form")
+    ap.add_argument("--no-cfd", action="store_true", help="skip the CFD (SOLA Navier-Stokes) benchmark form")
+    ap.add_argument("--cfd-only", action="store_true", help="run only the CFD benchmark form and print its numbers")
     ap.add_argument("--amr-only", action="store_true",
                     help="run only the refined-hierarchy forms (FP64 and FP32-RHS) and print their numbers")
     ap.add_argument("--no-fp32-config", action="store_true",

@@ -356,6 +356,57 @@ bssn_status_t bssn_amr_destroy(bssn_amr_t* amr);
 bssn_status_t bssn_sommerfeld_rhs(const bssn_grid_t* grid, const bssn_params_t* params, const double* xyz0,
                                   const double* state, double* rhs, void* stream);
 
+/* ---------------------------------------------------------------- CFD benchmark (SOLA Navier-Stokes)
+ * The paper's second workload (Sec. 4, "CFD with Chemora and Physis"): the
+ * incompressible Navier-Stokes equations by the SOLA scheme in single
+ * precision, as three stencil kernels - explicit velocity update, iterative
+ * mass conservation, boundary condition. Arrays u, v, w, p are DEVICE
+ * floats of bssn_cfd_points() elements ((nx+2)(ny+2)(nz+2), x fastest, one
+ * ghost layer, 16-byte aligned, caller-owned): element (i+1, j+1, k+1)
+ * belongs to cell (i,j,k) - p at its centre, u on its face i+1/2, v on
+ * j+1/2, w on k+1/2. Each axis is periodic (even cell count) or closed by
+ * no-slip walls, whose normal wall faces (-1 and n-1) hold zero velocity.
+ * Velocity: u~ = u + dt [(p_i - p_i+1)/dx + g_x - advection + nu lap u] on
+ * every non-wall face, advection in SOLA's flux form blending centred and
+ * donor-cell differences by alpha (0..1). Mass conservation: a half-sweep
+ * over the cells of one colour (i+j+k) mod 2: D = div u, dp = -beta D,
+ * beta = omega / (dt sum over the cell's movable faces of 1/h^2), p += dp,
+ * each movable face moves by dt dp / h. Boundary: ghosts axis by axis
+ * (periodic wrap, or zero normal wall faces, tangential ghosts
+ * 2 U_wall - interior with U_wall = lid for u on the top z wall, zero
+ * normal pressure gradient). All asynchronous on `stream`. */
+typedef struct {
+  int n[3];                  /* cells per axis, >= 2 (even when periodic)       */
+  double h[3];               /* cell size, > 0                                  */
+  int periodic[3];           /* 1 periodic, 0 walls                             */
+  double nu;                 /* kinematic viscosity, >= 0                       */
+  double dt;                 /* time step, > 0                                  */
+  double omega;              /* over-relaxation of the mass iteration, (0, 2)   */
+  double alpha;              /* donor-cell fraction of the advection, [0, 1]    */
+  double lid;                /* x-velocity of the top z wall (walls only)       */
+  double g[3];               /* body force (gravity)                            */
+} bssn_cfd_t;
+
+/* Elements per array, or 0 for an invalid description. */
+unsigned long long bssn_cfd_points(const bssn_cfd_t* desc);
+/* Boundary kernel on all four arrays (in place). */
+bssn_status_t bssn_cfd_boundary(const bssn_cfd_t* desc, float* u, float* v, float* w, float* p, void* stream);
+/* Velocity kernel: un, vn, wn (distinct from each other and from u, v, w)
+ * receive every interior entry - the advanced non-wall faces, and the wall
+ * faces' own values; their ghost layers are untouched. The ghosts of u, v,
+ * w, p must be set. */
+bssn_status_t bssn_cfd_velocity(const bssn_cfd_t* desc, const float* u, const float* v, const float* w,
+                                const float* p, float* un, float* vn, float* wn, void* stream);
+/* Mass-conservation kernel: one half-sweep over the cells of `colour` (0 or
+ * 1), in place on u, v, w, p. One iteration is colour 0 then colour 1. */
+bssn_status_t bssn_cfd_mass(const bssn_cfd_t* desc, int colour, float* u, float* v, float* w, float* p,
+                            void* stream);
+/* One time step in place: boundary, velocity, boundary, then `iterations`
+ * times (mass colour 0, mass colour 1, boundary). scratch: DEVICE, 16-byte
+ * aligned, 3 * round_up(bssn_cfd_points(), 4) floats. */
+bssn_status_t bssn_cfd_step(const bssn_cfd_t* desc, int iterations, float* u, float* v, float* w, float* p,
+                            float* scratch, void* stream);
+
 /* ---------------------------------------------------------------- learned corrector
  * A 3D convolutional network that corrects a coarse-grid RK4 step towards
  * the restricted fine-grid step: 5 layers of 3x3x3 convolutions, channels

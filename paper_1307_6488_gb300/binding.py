@@ -548,3 +548,56 @@ def sommerfeld_rhs(grid, params, xyz0, state, out, stream=None):
     xyz = np.ascontiguousarray(xyz0, dtype=np.float64)
     _check(_amr_lib().bssn_sommerfeld_rhs(ctypes.byref(grid), ctypes.byref(params), xyz.ctypes.data_as(_p),
                                           _ptr(state), _ptr(out), _stream(stream)), "sommerfeld_rhs")
+
+
+# ------------------------------------------------------------------ CFD benchmark (SOLA Navier-Stokes)
+class CfdDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("h", ctypes.c_double * 3), ("periodic", ctypes.c_int * 3),
+                ("nu", ctypes.c_double), ("dt", ctypes.c_double), ("omega", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("lid", ctypes.c_double), ("g", ctypes.c_double * 3)]
+
+
+def make_cfd(n, h, periodic, nu, dt, omega=1.7, alpha=0.3, lid=0.0, g=(0.0, 0.0, 0.0)):
+    h = (h,) * 3 if np.isscalar(h) else tuple(h)
+    return CfdDesc((ctypes.c_int * 3)(*n), (ctypes.c_double * 3)(*h), (ctypes.c_int * 3)(*[int(x) for x in periodic]),
+                   nu, dt, omega, alpha, lid, (ctypes.c_double * 3)(*g))
+
+
+def _cfd_lib():
+    L = lib()
+    if not getattr(L, "_cfd_typed", False):
+        D = ctypes.POINTER(CfdDesc)
+        L.bssn_cfd_points.argtypes = [D]
+        L.bssn_cfd_points.restype = ctypes.c_ulonglong
+        L.bssn_cfd_boundary.argtypes = [D, _p, _p, _p, _p, _p]
+        L.bssn_cfd_velocity.argtypes = [D, _p, _p, _p, _p, _p, _p, _p, _p]
+        L.bssn_cfd_mass.argtypes = [D, ctypes.c_int, _p, _p, _p, _p, _p]
+        L.bssn_cfd_step.argtypes = [D, ctypes.c_int, _p, _p, _p, _p, _p, _p]
+        for n in ("bssn_cfd_boundary", "bssn_cfd_velocity", "bssn_cfd_mass", "bssn_cfd_step"):
+            getattr(L, n).restype = ctypes.c_int
+        L._cfd_typed = True
+    return L
+
+
+def cfd_points(desc):
+    return _cfd_lib().bssn_cfd_points(ctypes.byref(desc))
+
+
+def cfd_boundary(desc, u, v, w, p, stream=None):
+    _check(_cfd_lib().bssn_cfd_boundary(ctypes.byref(desc), _ptr(u), _ptr(v), _ptr(w), _ptr(p), _stream(stream)),
+           "cfd_boundary")
+
+
+def cfd_velocity(desc, u, v, w, p, un, vn, wn, stream=None):
+    _check(_cfd_lib().bssn_cfd_velocity(ctypes.byref(desc), _ptr(u), _ptr(v), _ptr(w), _ptr(p), _ptr(un), _ptr(vn),
+                                        _ptr(wn), _stream(stream)), "cfd_velocity")
+
+
+def cfd_mass(desc, colour, u, v, w, p, stream=None):
+    _check(_cfd_lib().bssn_cfd_mass(ctypes.byref(desc), colour, _ptr(u), _ptr(v), _ptr(w), _ptr(p),
+                                    _stream(stream)), "cfd_mass")
+
+
+def cfd_step(desc, iterations, u, v, w, p, scratch, stream=None):
+    _check(_cfd_lib().bssn_cfd_step(ctypes.byref(desc), iterations, _ptr(u), _ptr(v), _ptr(w), _ptr(p), _ptr(scratch),
+                                    _stream(stream)), "cfd_step")

@@ -24,6 +24,7 @@ UNITS = [
     ("bssn_corrector.cu", "bssn_corrector.o", []),
     ("bssn_transfer.cu", "bssn_transfer.o", []),
     ("bssn_amr.cu", "bssn_amr.o", []),
+    ("bssn_cfd.cu", "bssn_cfd.o", []),
 ]
 
 

@@ -241,3 +241,30 @@ def test_amr_rejects_invalid_arguments(L):
         B.sommerfeld_rhs(B.make_grid(8, ghost=0, dx=0.1), p4, (1.0, 2.0, 3.0), FAKE, FAKE * 2, stream=0)
     assert e.value.status == E
     assert B.last_error() == B.OK
+
+
+def test_cfd_rejects_invalid_arguments(L):
+    """Host-side checks of the CFD entry points (no kernel is reached)."""
+    ok = B.make_cfd((8, 8, 8), 0.1, (1, 0, 0), nu=0.01, dt=0.001)
+    assert B.cfd_points(ok) == 10 ** 3
+    bad = [B.make_cfd((7, 8, 8), 0.1, (1, 0, 0), nu=0.01, dt=0.001),      # odd periodic axis
+           B.make_cfd((1, 8, 8), 0.1, (0, 0, 0), nu=0.01, dt=0.001),      # too few cells
+           B.make_cfd((8, 8, 8), 0.1, (0, 0, 0), nu=0.01, dt=0.0),        # dt
+           B.make_cfd((8, 8, 8), 0.1, (0, 0, 0), nu=0.01, dt=0.1, omega=2.0),
+           B.make_cfd((8, 8, 8), 0.1, (0, 0, 0), nu=0.01, dt=0.1, alpha=1.5),
+           B.make_cfd((8, 8, 8), 0.1, (2, 0, 0), nu=0.01, dt=0.1)]
+    for d in bad:
+        assert B.cfd_points(d) == 0
+        with pytest.raises(B.BssnError) as e:
+            B.cfd_boundary(d, FAKE, FAKE * 2, FAKE * 3, FAKE * 4, stream=0)
+        assert e.value.status == B.ERR_INVALID_ARG
+    with pytest.raises(B.BssnError) as e:
+        B.cfd_mass(ok, 2, FAKE, FAKE * 2, FAKE * 3, FAKE * 4, stream=0)  # colour
+    assert e.value.status == B.ERR_INVALID_ARG
+    with pytest.raises(B.BssnError) as e:
+        B.cfd_velocity(ok, FAKE, FAKE * 2, FAKE * 3, FAKE * 4, FAKE, FAKE * 5, FAKE * 6, stream=0)  # un is u
+    assert e.value.status == B.ERR_INVALID_ARG
+    with pytest.raises(B.BssnError) as e:
+        B.cfd_step(ok, 4, FAKE, FAKE * 2, FAKE * 3, FAKE * 4, FAKE + 4, stream=0)  # misaligned scratch
+    assert e.value.status == B.ERR_INVALID_ARG
+    assert B.last_error() == B.OK
