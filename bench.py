@@ -58,16 +58,24 @@ except (OSError, ValueError):
 TRAFFIC = {"src_sha": "6a5ea8a3413abd9d", "bytes_per_launch_128": (3.645846272e9 + 1.758921984e9) * 128 ** 3 / 96 ** 3}
 
 
+# DRAM traffic of one k_cfd_mass half-sweep at 256^3 (ncu dram__bytes_read.sum
+# + dram__bytes_write.sum: 271.2 MB + 214.4 MB), for the source it was taken on.
+CFD_TRAFFIC = {"src_sha": "d178fa7f0bde38d3", "bytes_per_launch": 271207168 + 214392320}
+
 # the sources that make up the fused FP64 stage kernel k_stage<8,0,double>
 STAGE_SOURCES = ("bssn_common.cuh", "bssn_point.cuh", "bssn_kernels.cuh", "bssn_order.cu")
 
 
-def kernel_src_sha():
+def src_sha(files):
     h = hashlib.sha256()
-    for f in STAGE_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, "paper_1307_6488_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def kernel_src_sha():
+    return src_sha(STAGE_SOURCES)
 
 
 def algorithmic_flops(order=ORDER):
@@ -512,7 +520,9 @@ def run_gpu(args):
                 "roofline": {"bound": "hbm", "kernel": "k_cfd_mass (one red-black half-sweep)",
                              "achieved": mass_bytes / (mass_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                              "frac": (mass_bytes / (mass_ms * 1e-3) / 1e9 / hbm) if hbm else None,
-                             "launch_ms": mass_ms, "bytes_per_cell": 28},
+                             "launch_ms": mass_ms, "bytes_per_cell": 28,
+                             "traffic": CFD_TRAFFIC["bytes_per_launch"] if CFD_TRAFFIC["src_sha"] == src_sha(
+                                 ("bssn_cfd.cu",)) else None},
                 "paper_context": "90.5 GFlop/s (Chemora) and 43 GFlop/s (Physis) on one NVIDIA M2050, 256^3, "
                                  "the paper's own flop count",
                 "workload": "lid-driven cavity 256^3, FP32, Re 1000, SOLA, 4 mass iterations per step"}

@@ -129,6 +129,41 @@ def test_three_levels_bl(order, bc):
     _check(got, want, g, STEPS_TOL)
 
 
+def test_one_static_patch_equals_uniform_step():
+    """A hierarchy of one level-0 patch with the static boundary is the
+    uniform grid: bit for bit the result of bssn_rk4_step."""
+    torch = need_gpu()
+    g, n = 5, (14, 11, 9)
+    h0 = 0.3
+    xlo = (-2.0, -1.6, -1.3)
+    u = _bl_patch((0, 0, 0), n, g, h0, xlo, seed=77)
+    p = B.make_params(fd_order=8, ko_eps=0.1, lapse=0, shift=0, eta=2.0)
+    grid = B.make_grid(*n, ghost=g, dx=h0)
+    a = B.upload(u, grid)
+    src = B.upload(u, grid)
+    h = B.amr_create([(0, (0, 0, 0), n, grid.var_stride, a, src)], n, xlo, h0, g, 1, 0.25 * h0, p)
+    try:
+        for _ in range(3):
+            B.amr_step(h)
+    finally:
+        B.amr_destroy(h)
+    b = B.upload(u, grid)
+    bufs = B.alloc_state(grid, n=3)
+    work = B.alloc_work(grid, p)
+    for _ in range(3):
+        B.rk4_step(grid, p, B.FP64, 0.25 * h0, 1, src, b, bufs, work)
+    torch.cuda.synchronize()
+    assert np.array_equal(B.download(a, grid), B.download(b, grid))
+
+
+def test_three_levels_bl_fp32_rhs():
+    g = 5
+    ncells, xlo, h0, geo = inputs.bl_hierarchy(n0=16, nested=2, fine_half=4, split=2, extent=16.0)
+    p = B.make_params(fd_order=8, ko_eps=0.1, lapse=0, shift=0, eta=2.0)
+    got, want, info = run_both(geo, ncells, xlo, h0, g, 2, p, 0.25 * h0, 2, prec=B.FP32_RHS)
+    _check(got, want, g, 1e-3)
+
+
 def test_flat_space_exact_full_benchmark_hierarchy():
     """The benchmark's own hierarchy (96^3 cells per level, 5 levels, 34
     patches, 8th order, radiative boundary): flat space stays bit-for-bit
