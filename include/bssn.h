@@ -346,6 +346,20 @@ bssn_status_t bssn_amr_info(const bssn_amr_t* amr, long long* updates_per_step, 
                             long long* graph_nodes);
 /* Frees everything the hierarchy owns (synchronizes the device). */
 bssn_status_t bssn_amr_destroy(bssn_amr_t* amr);
+/* Regridding (the step that lets refined boxes follow the solution, e.g.
+ * moving punctures): a new hierarchy on the patch list `patches`, with the
+ * old one's domain, parameters and precision, filled at the current time.
+ * Level 0 is not regridded: its patches must be the old level-0 boxes in the
+ * same order with the same var_stride (their state arrays may be the old
+ * ones, kept, or new ones, copied). Every cell of a new patch's padded box
+ * on a level >= 1 takes the value of the first old patch of that level
+ * (input order) whose interior holds it, else the tricubic prolongation of
+ * the new, already filled, coarser level (read cell by cell as for ghosts).
+ * New level >= 1 state arrays must not alias old ones. The old hierarchy is
+ * left intact (destroy it afterwards). Synchronizes `stream`. A new patch
+ * whose prolongation has no source: BSSN_ERR_INVALID_ARG. */
+bssn_status_t bssn_amr_regrid(const bssn_amr_t* old, const bssn_amr_patch_t* patches, int npatches,
+                              bssn_amr_t** out, void* stream);
 
 /* The Sommerfeld right-hand side above, evaluated at every point (interior
  * and ghost) of one grid: rhs[v] = -v (x^i/r) d_i state[v] - v (state[v] -

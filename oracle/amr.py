@@ -469,3 +469,68 @@ class Hierarchy:
 
     def updates_per_step(self):
         return sum(int(np.prod(q.n)) * 2 ** q.level for q in self.P)
+
+    # -------------------------------------------------------------- regridding
+    def regrid(self, geometry):
+        """A new hierarchy at the current time on the patch boxes `geometry`
+        (list of (level, origin, n)). Level 0 is not regridded: its boxes must
+        be the current ones, in the same order, and keep their states. Every
+        cell of a new patch's padded box on a level l >= 1 takes the value of
+        the first current level-l patch (input order) whose interior holds it
+        (periodic images included), else the tricubic prolongation of the new
+        level l-1 read as one field on cells (the rule of the ghost cells),
+        levels filled in increasing order. Returns the new Hierarchy."""
+        g = self.g
+        old0 = [(tuple(q.o), tuple(q.n)) for q in self.P if q.level == 0]
+        new0 = [(tuple(o), tuple(n)) for lv, o, n in geometry if lv == 0]
+        if old0 != new0:
+            raise ValueError("level 0 is not regridded: its boxes must stay the same")
+        pts = []
+        it0 = iter([q for q in self.P if q.level == 0])
+        for lv, o, n in geometry:
+            if lv == 0:
+                q = next(it0)
+                pts.append(Patch(0, o, n, q.state.copy(), ghost_src=q.ghost_src))
+            else:
+                pts.append(Patch(lv, o, n, np.zeros((24, n[2] + 2 * g, n[1] + 2 * g, n[0] + 2 * g))))
+        H = Hierarchy(pts, g, self.N, self.xlo, self.h0, self.bc, self.p, self.dt0)
+        for l in range(1, H.nlev):
+            old = [q for q in self.P if q.level == l]
+            per = H.period(l)
+            for b in H.at[l]:
+                q = H.P[b]
+                shape = q.state.shape[1:]
+                kk, jj, ii = np.meshgrid(*(np.arange(s) for s in shape), indexing="ij")
+                kk, jj, ii = kk.ravel(), jj.ravel(), ii.ravel()
+                G = np.stack([ii + q.o[0] - g, jj + q.o[1] - g, kk + q.o[2] - g])
+                todo = np.ones(G.shape[1], dtype=bool)
+                for r in old:
+                    ok = todo.copy()
+                    src = []
+                    for a in range(3):
+                        fit, sh = _fit(G[a], 1, r.o[a], r.o[a] + r.n[a], None if per is None else per[a])
+                        ok &= fit
+                        src.append(sh - r.o[a] + g)
+                    if ok.any():
+                        q.state[:, kk[ok], jj[ok], ii[ok]] = r.state[:, src[2][ok], src[1][ok], src[0][ok]]
+                        todo &= ~ok
+                if todo.any():
+                    Gs = G[:, todo]
+                    base = np.where(Gs % 2 == 0, Gs // 2 - 2, Gs // 2 - 1)
+                    x = [(0.5 * Gs[a] - 0.25) - base[a] for a in range(3)]
+                    w = [lagrange_weights(x[a], [0.0, 1.0, 2.0, 3.0]) for a in range(3)]
+                    val = 0.0
+                    for a3 in range(4):
+                        for a2 in range(4):
+                            for a1 in range(4):
+                                C = np.stack([base[0] + a1, base[1] + a2, base[2] + a3])
+                                srcp, (iz, iy, ix) = H._coarse_cells(l - 1, C)
+                                if np.any(srcp < 0):
+                                    raise ValueError("regridded patch not properly nested")
+                                v = np.empty((24, srcp.size))
+                                for s in np.unique(srcp):
+                                    m = srcp == s
+                                    v[:, m] = H.P[s].state[:, iz[m], iy[m], ix[m]]
+                                val = val + (w[2][a3] * w[1][a2] * w[0][a1]) * v
+                    q.state[:, kk[todo], jj[todo], ii[todo]] = val
+        return H

@@ -506,7 +506,9 @@ def _amr_lib():
                                     ctypes.POINTER(ctypes.c_longlong)]
         L.bssn_amr_destroy.argtypes = [_p]
         L.bssn_sommerfeld_rhs.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Params), _p, _p, _p, _p]
-        for n in ("bssn_amr_create", "bssn_amr_step", "bssn_amr_info", "bssn_amr_destroy", "bssn_sommerfeld_rhs"):
+        L.bssn_amr_regrid.argtypes = [_p, ctypes.POINTER(AmrPatch), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), _p]
+        for n in ("bssn_amr_create", "bssn_amr_step", "bssn_amr_info", "bssn_amr_destroy", "bssn_sommerfeld_rhs",
+                  "bssn_amr_regrid"):
             getattr(L, n).restype = ctypes.c_int
         L._amr_typed = True
     return L
@@ -523,6 +525,16 @@ def amr_create(patches, ncells, xlo, h0, ghost, boundary, dt0, params, prec=FP64
     h = ctypes.c_void_p()
     _check(_amr_lib().bssn_amr_create(ctypes.byref(h), arr, len(patches), ctypes.byref(d), ctypes.byref(params),
                                       prec), "amr_create")
+    return h.value
+
+
+def amr_regrid(amr, patches, stream=None):
+    """New hierarchy on `patches` (same tuples as amr_create) filled from
+    the hierarchy `amr` at the current time; returns its handle."""
+    arr = (AmrPatch * len(patches))(*[AmrPatch(lv, o[0], o[1], o[2], n[0], n[1], n[2], vs, _ptr(s), _ptr(src))
+                                      for (lv, o, n, vs, s, src) in patches])
+    h = ctypes.c_void_p()
+    _check(_amr_lib().bssn_amr_regrid(amr, arr, len(patches), ctypes.byref(h), _stream(stream)), "amr_regrid")
     return h.value
 
 

@@ -169,7 +169,9 @@ __device__ __forceinline__ long long stencil_base(long long G, int* odd) {
 }
 
 // Once per parent step, pass 1: gather the parent level's stage states at
-// the box's coarse cells and interpolate along x.
+// the box's coarse cells and interpolate along x (STAGES = false: the
+// parent level's current state only, one field, for regridding).
+template <bool STAGES>
 __global__ void __launch_bounds__(ENTRY_THREADS) ka_prolong_x(const ProlongBox* __restrict__ Bx, const long long* __restrict__ x1s,
                                                               int nbox, long long n1, const GatherSrc* __restrict__ map,
                                                               const PatchDev* __restrict__ P, double* __restrict__ X1) {
@@ -199,23 +201,27 @@ __global__ void __launch_bounds__(ENTRY_THREADS) ka_prolong_x(const ProlongBox* 
         for (int c = 0; c < 4; ++c) {
           const PatchDev& C = P[src[c].patch];
           const long long o = v * C.L.vs + src[c].off;
-          const double y0 = __ldg(C.buf[5] + o);
-          acc[0] = fma(w[c], y0, acc[0]);
-          acc[1] = fma(w[c], __ldg(C.buf[1] + o) - y0, acc[1]);
-          acc[2] = fma(w[c], __ldg(C.buf[2] + o) - y0, acc[2]);
-          acc[3] = fma(w[c], __ldg(C.buf[4] + o) - y0, acc[3]);
-          acc[4] = fma(w[c], __ldg(C.buf[0] + o) - y0, acc[4]);
+          if (STAGES) {
+            const double y0 = __ldg(C.buf[5] + o);
+            acc[0] = fma(w[c], y0, acc[0]);
+            acc[1] = fma(w[c], __ldg(C.buf[1] + o) - y0, acc[1]);
+            acc[2] = fma(w[c], __ldg(C.buf[2] + o) - y0, acc[2]);
+            acc[3] = fma(w[c], __ldg(C.buf[4] + o) - y0, acc[3]);
+            acc[4] = fma(w[c], __ldg(C.buf[0] + o) - y0, acc[4]);
+          } else {
+            acc[0] = fma(w[c], __ldg(C.buf[0] + o), acc[0]);
+          }
         }
       }
 #pragma unroll
-      for (int f = 0; f < 5; ++f) X1[(long long)(f * NV + v) * n1 + t] = acc[f];
+      for (int f = 0; f < (STAGES ? 5 : 1); ++f) X1[(long long)(f * NV + v) * n1 + t] = acc[f];
     }
   }
 }
 
 // Pass 2: along y, for every fine padded row j of the box.
 __global__ void __launch_bounds__(ENTRY_THREADS) ka_prolong_y(const ProlongBox* __restrict__ Bx, const long long* __restrict__ x2s,
-                                                              int nbox, long long n1, long long n2,
+                                                              int nbox, long long n1, long long n2, int nf,
                                                               const double* __restrict__ X1, double* __restrict__ X2) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2; t += (long long)gridDim.x * blockDim.x) {
     const int b = find_box(x2s, nbox, t);
@@ -230,7 +236,7 @@ __global__ void __launch_bounds__(ENTRY_THREADS) ka_prolong_y(const ProlongBox* 
     prolong_w(odd, w);
     const long long p1 = B.x1_0 + ((long long)cz * B.nc[1] + cy) * B.fx[0] + i;
 #pragma unroll 4
-    for (int f = 0; f < 5 * NV; ++f) {
+    for (int f = 0; f < nf * NV; ++f) {
       const double* x = X1 + (long long)f * n1 + p1;
       X2[(long long)f * n2 + t] =
           fma(w[3], __ldg(x + 3 * B.fx[0]), fma(w[2], __ldg(x + 2 * B.fx[0]), fma(w[1], __ldg(x + B.fx[0]), w[0] * __ldg(x))));
@@ -257,6 +263,49 @@ __global__ void __launch_bounds__(ENTRY_THREADS) ka_prolong_z(const ProlongEntry
       pb[(long long)f * n + t] =
           fma(w[3], __ldg(x + 3 * plane), fma(w[2], __ldg(x + 2 * plane), fma(w[1], __ldg(x + plane), w[0] * __ldg(x))));
     }
+  }
+}
+
+// Regridding: pass 3 along z for the prolonged cells of a new patch,
+// written straight into its state (one field: the current state).
+__global__ void __launch_bounds__(ENTRY_THREADS) ka_regrid_z(const ProlongEntry* __restrict__ E, long long n,
+                                                             const ProlongBox* __restrict__ Bx, long long n2,
+                                                             const double* __restrict__ X2,
+                                                             const PatchDev* __restrict__ P) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const ProlongEntry e = E[t];
+    const ProlongBox& B = Bx[e.box];
+    int odd;
+    const int cz = (int)(stencil_base(B.fo[2] + e.k, &odd) - B.cb[2]);
+    double w[4];
+    prolong_w(odd, w);
+    const long long plane = (long long)B.fx[1] * B.fx[0];
+    const long long p2 = B.x2_0 + (cz * (long long)B.fx[1] + e.j) * B.fx[0] + e.i;
+    const PatchDev& D = P[e.dst];
+#pragma unroll 4
+    for (int v = 0; v < NV; ++v) {
+      const double* x = X2 + (long long)v * n2 + p2;
+      D.buf[0][v * D.L.vs + e.dst_off] =
+          fma(w[3], __ldg(x + 3 * plane), fma(w[2], __ldg(x + 2 * plane), fma(w[1], __ldg(x + plane), w[0] * __ldg(x))));
+    }
+  }
+}
+
+struct RegridCopy {
+  int dst;
+  long long dst_off;
+  const double* src;        // the old patch's cell (variable 0)
+  long long src_vs;
+};
+
+// Regridding: cells a current patch of the same level holds are copied.
+__global__ void __launch_bounds__(ENTRY_THREADS) ka_regrid_copy(const RegridCopy* __restrict__ E, long long n,
+                                                                const PatchDev* __restrict__ P) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const RegridCopy e = E[t];
+    const PatchDev& D = P[e.dst];
+#pragma unroll 4
+    for (int v = 0; v < NV; ++v) D.buf[0][v * D.L.vs + e.dst_off] = __ldg(e.src + v * e.src_vs);
   }
 }
 
@@ -488,6 +537,9 @@ struct bssn_amr {
   cudaStream_t cap = nullptr;
   long long updates = 0, nodes = 0;
   long long counts[5] = {0, 0, 0, 0, 0};
+  std::vector<HostPatch> geo;   // per patch: level, first cell, size, layout
+  std::vector<std::vector<GatherSrc>> gmaps;  // host copies of the levels' gather maps
+  std::vector<std::vector<ProlongBox>> hboxes;
 };
 
 namespace {
@@ -540,6 +592,21 @@ GatherSrc coarse_src(const bssn_amr* A, const std::vector<HostPatch>& H, int lc,
   return GatherSrc{-1, 0};
 }
 
+// Does every cell of the 4 x 4 x 4 coarse stencil of fine cell G have a
+// source in the box's gather map?
+bool stencil_has_sources(const ProlongBox& B, const std::vector<GatherSrc>& gmap, const long long G[3]) {
+  long long c0[3];
+  for (int a = 0; a < 3; ++a) {
+    const long long c = floor_div(G[a], 2);
+    c0[a] = ((G[a] - 2 * c) == 1 ? c - 1 : c - 2) - B.cb[a];
+  }
+  for (int cz = 0; cz < 4; ++cz)
+    for (int cy = 0; cy < 4; ++cy)
+      for (int cx = 0; cx < 4; ++cx)
+        if (gmap[B.map0 + ((c0[2] + cz) * B.nc[1] + c0[1] + cy) * B.nc[0] + c0[0] + cx].patch < 0) return false;
+  return true;
+}
+
 bool build_maps(bssn_amr* A, const std::vector<HostPatch>& H, int l, std::vector<CopyEntry>& copy,
                 std::vector<StaticEntry>& stat, std::vector<ProlongEntry>& pro, std::vector<RadEntry>& rad,
                 std::vector<ProlongBox>& boxes, std::vector<GatherSrc>& gmap, long long* n1, long long* n2) {
@@ -547,7 +614,29 @@ bool build_maps(bssn_amr* A, const std::vector<HostPatch>& H, int l, std::vector
   *n1 = *n2 = 0;
   for (int b : A->lev[l].ids) {
     const HostPatch& q = H[b];
-    int box = -1;  // this patch's prolongation box, made at its first prolonged ghost
+    int box = -1;  // this patch's prolongation box (every patch of a level >= 1 has one)
+    if (l >= 1) {
+      ProlongBox B;
+      for (int a = 0; a < 3; ++a) {
+        B.fo[a] = q.o[a] - g;
+        B.fx[a] = (int)(q.n[a] + 2 * g);
+        B.cb[a] = floor_div(B.fo[a], 2) - 2;
+        B.nc[a] = (int)(floor_div(B.fo[a] + B.fx[a] - 1, 2) + 2 - B.cb[a] + 1);
+      }
+      B.map0 = (long long)gmap.size();
+      B.x1_0 = *n1;
+      B.x2_0 = *n2;
+      *n1 += (long long)B.nc[2] * B.nc[1] * B.fx[0];
+      *n2 += (long long)B.nc[2] * B.fx[1] * B.fx[0];
+      for (int cz = 0; cz < B.nc[2]; ++cz)
+        for (int cy = 0; cy < B.nc[1]; ++cy)
+          for (int cx = 0; cx < B.nc[0]; ++cx) {
+            const long long C[3] = {B.cb[0] + cx, B.cb[1] + cy, B.cb[2] + cz};
+            gmap.push_back(coarse_src(A, H, l - 1, C));
+          }
+      box = (int)boxes.size();
+      boxes.push_back(B);
+    }
     const long long ex = q.n[0] + 2 * g, ey = q.n[1] + 2 * g, ez = q.n[2] + 2 * g;
     for (long long k = 0; k < ez; ++k)
       for (long long j = 0; j < ey; ++j)
@@ -591,41 +680,7 @@ bool build_maps(bssn_amr* A, const std::vector<HostPatch>& H, int l, std::vector
           }
           if (done) continue;
           if (l >= 1) {
-            if (box < 0) {
-              ProlongBox B;
-              for (int a = 0; a < 3; ++a) {
-                B.fo[a] = q.o[a] - g;
-                B.fx[a] = (int)(q.n[a] + 2 * g);
-                B.cb[a] = floor_div(B.fo[a], 2) - 2;
-                B.nc[a] = (int)(floor_div(B.fo[a] + B.fx[a] - 1, 2) + 2 - B.cb[a] + 1);
-              }
-              B.map0 = (long long)gmap.size();
-              B.x1_0 = *n1;
-              B.x2_0 = *n2;
-              *n1 += (long long)B.nc[2] * B.nc[1] * B.fx[0];
-              *n2 += (long long)B.nc[2] * B.fx[1] * B.fx[0];
-              for (int cz = 0; cz < B.nc[2]; ++cz)
-                for (int cy = 0; cy < B.nc[1]; ++cy)
-                  for (int cx = 0; cx < B.nc[0]; ++cx) {
-                    const long long C[3] = {B.cb[0] + cx, B.cb[1] + cy, B.cb[2] + cz};
-                    gmap.push_back(coarse_src(A, H, l - 1, C));
-                  }
-              box = (int)boxes.size();
-              boxes.push_back(B);
-            }
-            // every cell of the 4 x 4 x 4 coarse stencil needs a source
-            const ProlongBox& B = boxes[box];
-            long long c0[3];
-            for (int a = 0; a < 3; ++a) {
-              const long long c = floor_div(G[a], 2);
-              c0[a] = ((G[a] - 2 * c) == 1 ? c - 1 : c - 2) - B.cb[a];
-            }
-            bool ok = true;
-            for (int cz = 0; cz < 4 && ok; ++cz)
-              for (int cy = 0; cy < 4 && ok; ++cy)
-                for (int cx = 0; cx < 4 && ok; ++cx)
-                  ok = gmap[B.map0 + ((c0[2] + cz) * B.nc[1] + c0[1] + cy) * B.nc[0] + c0[0] + cx].patch >= 0;
-            if (ok) {
+            if (stencil_has_sources(boxes[box], gmap, G)) {
               pro.push_back(ProlongEntry{b, box, off, (int)i, (int)j, (int)k});
               done = true;
             }
@@ -751,9 +806,10 @@ cudaError_t enqueue_level(bssn_amr* A, int l, int m, cudaStream_t s) {
     Level& F = A->lev[l + 1];
     if (F.pro.n) {
       const int nb = (int)F.box.n;
-      ka_prolong_x<<<entry_grid(A, F.n1), ENTRY_THREADS, 0, s>>>(F.box.ptr, F.d_x1s, nb, F.n1, F.map.ptr, A->all,
-                                                                 A->X1);
-      ka_prolong_y<<<entry_grid(A, F.n2), ENTRY_THREADS, 0, s>>>(F.box.ptr, F.d_x2s, nb, F.n1, F.n2, A->X1, A->X2);
+      ka_prolong_x<true><<<entry_grid(A, F.n1), ENTRY_THREADS, 0, s>>>(F.box.ptr, F.d_x1s, nb, F.n1, F.map.ptr,
+                                                                       A->all, A->X1);
+      ka_prolong_y<<<entry_grid(A, F.n2), ENTRY_THREADS, 0, s>>>(F.box.ptr, F.d_x2s, nb, F.n1, F.n2, 5, A->X1,
+                                                                 A->X2);
       ka_prolong_z<<<entry_grid(A, F.pro.n), ENTRY_THREADS, 0, s>>>(F.pro.ptr, F.pro.n, F.box.ptr, F.n2, A->X2,
                                                                     F.pbuf);
       A->nodes += 3;
@@ -902,6 +958,8 @@ bssn_status_t bssn_amr_create(bssn_amr_t** out, const bssn_amr_patch_t* patches,
     std::vector<GatherSrc> gmap;
     Level& L = A->lev[l];
     nested = build_maps(A, H, l, copy, stat, pro, rad, boxes, gmap, &L.n1, &L.n2);
+    A->gmaps.push_back(gmap);
+    A->hboxes.push_back(boxes);
     if (!nested) break;
     if (l + 1 < nlev) build_restrict(A, H, l, res);
     e = upload_list(A, copy, &L.copy);
@@ -1001,6 +1059,7 @@ bssn_status_t bssn_amr_create(bssn_amr_t** out, const bssn_amr_patch_t* patches,
   }
   A->grid_stage = std::max(1, occ) * std::max(1, sms);
   A->grid_other = 8 * std::max(1, sms);
+  A->geo = H;
   if (e != cudaSuccess || !nested) {
     amr_free(A);
     delete A;
@@ -1045,6 +1104,128 @@ bssn_status_t bssn_amr_destroy(bssn_amr_t* A) {
   cudaDeviceSynchronize();
   amr_free(A);
   delete A;
+  return BSSN_OK;
+}
+
+bssn_status_t bssn_amr_regrid(const bssn_amr_t* old, const bssn_amr_patch_t* patches, int npatches,
+                              bssn_amr_t** out, void* stream) {
+  if (!old || !patches || !out || npatches < 1) return BSSN_ERR_INVALID_ARG;
+  *out = nullptr;
+  // level 0 is not regridded: same boxes, same order, same layout
+  std::vector<int> old0, new0;
+  for (int b = 0; b < old->np; ++b)
+    if (old->geo[b].level == 0) old0.push_back(b);
+  for (int b = 0; b < npatches; ++b)
+    if (patches[b].level == 0) new0.push_back(b);
+  if (old0.size() != new0.size()) return BSSN_ERR_INVALID_ARG;
+  for (size_t i = 0; i < old0.size(); ++i) {
+    const HostPatch& q = old->geo[old0[i]];
+    const bssn_amr_patch_t& P = patches[new0[i]];
+    if (q.o[0] != P.ox || q.o[1] != P.oy || q.o[2] != P.oz || q.n[0] != P.nx || q.n[1] != P.ny || q.n[2] != P.nz ||
+        q.L.vs != P.var_stride)
+      return BSSN_ERR_INVALID_ARG;
+  }
+  bssn_amr_desc_t d;
+  for (int a = 0; a < 3; ++a) {
+    d.ncells[a] = (int)old->N[a];
+    d.xlo[a] = old->xlo[a];
+    d.h0[a] = old->h0[a];
+  }
+  d.ghost = old->g;
+  d.boundary = old->bc;
+  d.dt0 = old->dt0;
+  bssn_amr_t* A = nullptr;
+  const bssn_status_t st = bssn_amr_create(&A, patches, npatches, &d, &old->params, old->prec);
+  if (st != BSSN_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < old0.size() && e == cudaSuccess; ++i) {
+    double* dst = A->host[new0[i]].buf[0];
+    const double* src = old->host[old0[i]].buf[0];
+    if (dst != src) e = cudaMemcpyAsync(dst, src, sizeof(double) * NV * A->host[new0[i]].L.vs, cudaMemcpyDeviceToDevice, s);
+  }
+  std::vector<void*> tmp;
+  bool nested = true;
+  const int g = A->g;
+  for (int l = 1; l < A->nlev && e == cudaSuccess && nested; ++l) {
+    std::vector<RegridCopy> cp;
+    std::vector<ProlongEntry> pr;
+    Level& L = A->lev[l];
+    for (size_t bi = 0; bi < L.ids.size() && nested; ++bi) {
+      const int b = L.ids[bi];
+      const HostPatch& q = A->geo[b];
+      const ProlongBox& Bx = A->hboxes[l][bi];
+      for (long long k = 0; k < q.n[2] + 2 * g && nested; ++k)
+        for (long long j = 0; j < q.n[1] + 2 * g && nested; ++j)
+          for (long long i = 0; i < q.n[0] + 2 * g; ++i) {
+            const long long G[3] = {q.o[0] + i - g, q.o[1] + j - g, q.o[2] + k - g};
+            const long long off = i + j * q.L.sy + k * q.L.sz;
+            bool done = false;
+            if (l < old->nlev) {
+              for (int sidx : old->lev[l].ids) {
+                const HostPatch& r = old->geo[sidx];
+                long long sh[3];
+                bool ok = true;
+                for (int a = 0; a < 3 && ok; ++a)
+                  ok = fit(G[a], 1, r.o[a], r.o[a] + r.n[a], period_of(A, l, a), &sh[a]);
+                if (!ok) continue;
+                const long long soff =
+                    (sh[0] - r.o[0] + g) + (sh[1] - r.o[1] + g) * r.L.sy + (sh[2] - r.o[2] + g) * r.L.sz;
+                cp.push_back(RegridCopy{b, off, old->host[sidx].buf[0] + soff, r.L.vs});
+                done = true;
+                break;
+              }
+            }
+            if (done) continue;
+            if (!stencil_has_sources(Bx, A->gmaps[l], G)) {
+              nested = false;
+              break;
+            }
+            pr.push_back(ProlongEntry{b, (int)bi, off, (int)i, (int)j, (int)k});
+          }
+    }
+    if (!nested) break;
+    void* dcp = nullptr;
+    void* dpr = nullptr;
+    if (!cp.empty()) {
+      e = cudaMalloc(&dcp, sizeof(RegridCopy) * cp.size());
+      if (e == cudaSuccess) {
+        tmp.push_back(dcp);
+        e = cudaMemcpy(dcp, cp.data(), sizeof(RegridCopy) * cp.size(), cudaMemcpyHostToDevice);
+      }
+    }
+    if (e == cudaSuccess && !pr.empty()) {
+      e = cudaMalloc(&dpr, sizeof(ProlongEntry) * pr.size());
+      if (e == cudaSuccess) {
+        tmp.push_back(dpr);
+        e = cudaMemcpy(dpr, pr.data(), sizeof(ProlongEntry) * pr.size(), cudaMemcpyHostToDevice);
+      }
+    }
+    if (e == cudaSuccess && !cp.empty()) {
+      ka_regrid_copy<<<entry_grid(A, (long long)cp.size()), ENTRY_THREADS, 0, s>>>((const RegridCopy*)dcp,
+                                                                                  (long long)cp.size(), A->all);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && !pr.empty()) {
+      // the new level l-1 is complete: prolong its current state separably
+      const int nb = (int)L.box.n;
+      ka_prolong_x<false><<<entry_grid(A, L.n1), ENTRY_THREADS, 0, s>>>(L.box.ptr, L.d_x1s, nb, L.n1, L.map.ptr,
+                                                                        A->all, A->X1);
+      ka_prolong_y<<<entry_grid(A, L.n2), ENTRY_THREADS, 0, s>>>(L.box.ptr, L.d_x2s, nb, L.n1, L.n2, 1, A->X1,
+                                                                 A->X2);
+      ka_regrid_z<<<entry_grid(A, (long long)pr.size()), ENTRY_THREADS, 0, s>>>(
+          (const ProlongEntry*)dpr, (long long)pr.size(), L.box.ptr, L.n2, A->X2, A->all);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  for (void* q : tmp) cudaFree(q);
+  if (e != cudaSuccess || !nested) {
+    bssn_amr_destroy(A);
+    if (!nested) return BSSN_ERR_INVALID_ARG;
+    return e == cudaErrorMemoryAllocation ? BSSN_ERR_NOMEM : BSSN_ERR_CUDA;
+  }
+  *out = A;
   return BSSN_OK;
 }
 

@@ -268,3 +268,9 @@ def test_cfd_rejects_invalid_arguments(L):
         B.cfd_step(ok, 4, FAKE, FAKE * 2, FAKE * 3, FAKE * 4, FAKE + 4, stream=0)  # misaligned scratch
     assert e.value.status == B.ERR_INVALID_ARG
     assert B.last_error() == B.OK
+
+
+def test_amr_regrid_rejects_null(L):
+    L.bssn_amr_regrid.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    out = ctypes.c_void_p()
+    assert L.bssn_amr_regrid(None, None, 1, ctypes.byref(out), None) == B.ERR_INVALID_ARG

@@ -17,7 +17,10 @@ oracle follows Berger & Oliger with time-interpolated prolongation. Pins:
     cells the fine interior covers;
   * flat space stays exactly flat through a three-level step with the
     radiative boundary;
-  * a two-level evolution of the gauge wave converges to the exact solution.
+  * a two-level evolution of the gauge wave converges to the exact solution;
+  * regridding onto the same boxes changes nothing, and onto moved boxes it
+    copies the cells the old boxes cover and prolongs the rest exactly on
+    tricubic data.
 """
 import math
 
@@ -278,3 +281,44 @@ def test_gauge_wave_two_levels_converges():
     orders = [math.log2(e[i] / e[i + 1]) for i in range(2)]
     assert e[0] < 1e-4, e
     assert min(orders) > 2.0, (e, orders)
+
+
+def _geo_regrid(fine):
+    return [(0, (0, 0, 0), (16, 16, 16)), (1, fine[0], fine[1])]
+
+
+def test_regrid_same_boxes_is_identity():
+    H, xlo, h0 = _two_levels()
+    rng = np.random.default_rng(0)
+    for q in H.P:
+        q.state[...] = rng.standard_normal(q.state.shape)
+    R = H.regrid(_geo_regrid(((8, 8, 8), (16, 16, 16))))
+    for a, b in zip(H.P, R.P):
+        # the interiors and every ghost the old patch holds are copied
+        np.testing.assert_array_equal(a.state[:, 4:-4, 4:-4, 4:-4], b.state[:, 4:-4, 4:-4, 4:-4])
+    np.testing.assert_array_equal(H.P[0].state, R.P[0].state)
+
+
+def test_regrid_moved_box_copies_and_prolongs_exactly():
+    """The fine box moves by (4, 2, 0) fine cells: cells still inside the old
+    box are copied (bit for bit), the others are the tricubic prolongation of
+    the parent, exact on tricubic data."""
+    H, xlo, h0 = _two_levels()
+    g = H.g
+    par = H.P[0]
+    x, y, z = inputs.box_coords(par.o, par.n, g, h0, xlo)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    par.state[...] = _poly(X, Y, Z)
+    fine = H.P[1]
+    fine.state[...] = 3.25  # distinguishable from the polynomial
+    R = H.regrid(_geo_regrid(((12, 10, 8), (16, 16, 16))))
+    q = R.P[1]
+    xf, yf, zf = inputs.box_coords(q.o, q.n, g, h0 / 2, xlo)
+    Zf, Yf, Xf = np.meshgrid(zf, yf, xf, indexing="ij")
+    G = [np.arange(-g, 16 + g) + q.o[a] for a in range(3)]
+    inside = ((G[0] >= 8) & (G[0] < 24))[None, None, :] & ((G[1] >= 8) & (G[1] < 24))[None, :, None] & \
+        ((G[2] >= 8) & (G[2] < 24))[:, None, None]
+    assert np.all(q.state[3][inside] == 3.25)
+    np.testing.assert_allclose(q.state[3][~inside], _poly(Xf, Yf, Zf)[~inside], rtol=0, atol=1e-13)
+    with pytest.raises(ValueError):
+        H.regrid([(0, (0, 0, 0), (8, 16, 16))])
