@@ -14,7 +14,7 @@ import oracle
 from paper_1307_6488_gb300 import binding as B
 from paper_1307_6488_gb300 import inputs
 
-from gpu_common import grid_for, interior, need_gpu, oracle_params, perturbed_bl, rel_err_tensor
+from gpu_common import TENSORS, grid_for, interior, need_gpu, oracle_params, perturbed_bl, rel_err_tensor
 
 pytestmark = pytest.mark.gpu
 
@@ -109,3 +109,44 @@ def test_fp32_stage_split_matches_fused_call():
         B.rk4_stage_fused(grid, p, prec, 0, 0.02, y0, y0, a2, n2, work)
         torch.cuda.synchronize()
         assert torch.equal(n1, n2) and torch.equal(a1, a2)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("n,prec", [(128, B.FP32_RHS), (256, B.FP32_RHS), (256, B.FP64)])
+def test_full_size_sampled(n, prec):
+    """The throughput grids of the precision comparison - 128^3 and 256^3
+    Brill-Lindquist (bare masses 0.5 at x = +-1.5) with the 8th-order stencil
+    and 5 ghosts, plus a seeded 1e-3 perturbation - one fused RK4 stage 0 in
+    the benchmark's launch configuration, checked at 4096 sampled points
+    against the oracle's right-hand side: FP64 per variable at 1e-12, the
+    FP32-RHS form per tensor field within its bound."""
+    torch = need_gpu()
+    g = 5
+    u, h = inputs.brill_lindquist(n, g, lo=-8.0, hi=8.0)
+    inputs.smooth_perturbation(u, g, 1e-3, 4243 + n, h)
+    p = B.make_params(fd_order=8)
+    grid = grid_for(u, g, h)
+    y0 = B.upload(u, grid)
+    acc = B.alloc_state(grid)
+    ynext = B.alloc_state(grid)
+    work = B.alloc_work(grid, p, prec)
+    dt = 0.25 * h
+    B.rk4_stage(grid, p, prec, 0, dt, y0, y0, acc, ynext, work)
+    torch.cuda.synchronize()
+    del ynext, work
+    rng = np.random.default_rng(n + prec)
+    lin = np.unique(rng.integers(0, n ** 3, 4096))
+    k = oracle.rhs_points(u, g, h, oracle_params(p), lin, ko=True)  # (npts, 24)
+    gi = interior(B.download(acc, grid), g).reshape(24, -1)[:, lin].T
+    want = dt / 6 * k
+    if prec == B.FP64:
+        scale = np.max(np.abs(want), axis=0) + 1e-300
+        err = np.max(np.abs(gi - want), axis=0) / scale
+        assert np.max(err) < 1e-12, dict(zip(inputs.VARS, err))
+    else:
+        mag = np.max(np.abs(want), axis=0)
+        scale = np.zeros_like(mag)
+        for grp in TENSORS:
+            scale[grp] = np.max(mag[grp])
+        err = np.max(np.abs(gi - want), axis=0) / np.maximum(scale, 1e-300)
+        assert np.max(err) < FP32_RHS_TOL, dict(zip(inputs.VARS, err))
