@@ -52,11 +52,11 @@ except (OSError, ValueError):
 
 # DRAM traffic of the fused stage kernel per launch, from one ncu capture of
 # the same source (profiles/); ignored when the kernel source has changed.
-# Captured at 96^3 (884,736 points: 2.289 GB read + 1.728 GB written per
+# Captured at 96^3 (884,736 points: 2.287 GB read + 1.728 GB written per
 # launch, 4.54 kB per point, rows traversed in bricks) and scaled to 128^3 by
 # the point count, since the traffic is per point (state, tables and the
 # per-thread stack).
-TRAFFIC = {"src_sha": "5bc2af9737b47902", "bytes_per_launch_128": (2.289371904e9 + 1.7279616e9) * 128 ** 3 / 96 ** 3}
+TRAFFIC = {"src_sha": "b4f935a8646d3309", "bytes_per_launch_128": (2.287486976e9 + 1.728307712e9) * 128 ** 3 / 96 ** 3}
 
 
 # DRAM traffic of one k_cfd_mass half-sweep at 256^3 (ncu dram__bytes_read.sum

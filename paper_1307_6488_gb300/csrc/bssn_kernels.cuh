@@ -593,7 +593,8 @@ __global__ void __launch_bounds__(128) k_constraints(Layout L, Coef<double> C, c
   bool bad = false;
   if (lin < L.npts) {
     int i, j, k;
-    point_coords(L, lin, i, j, k);
+    i = (int)(lin % L.nx);
+    brick_row<STAGE_BRICK_Y64, STAGE_BRICK_Z64>(lin / L.nx, L.ny, L.nz, j, k);  // rows in brick order, as k_stage
     const long long p = L.off0 + i + j * L.sy + k * L.sz;
     PointIn<double> Q;
     gather<P, false, false, double>(L, C, u, dX, dY, p, Q, nullptr);
