@@ -52,11 +52,17 @@ except (OSError, ValueError):
 
 # DRAM traffic of the fused stage kernel per launch, from one ncu capture of
 # the same source (profiles/); ignored when the kernel source has changed.
-# Captured at 96^3 (884,736 points: 2.287 GB read + 1.728 GB written per
-# launch, 4.54 kB per point, rows traversed in bricks) and scaled to 128^3 by
+# Captured at 96^3 (884,736 points: 3.264 GB read + 2.787 GB written per
+# launch, 6.84 kB per point at 4 blocks/SM, rows traversed in bricks) and
+# scaled to 128^3 by
 # the point count, since the traffic is per point (state, tables and the
 # per-thread stack).
-TRAFFIC = {"src_sha": "b4f935a8646d3309", "bytes_per_launch_128": (2.287486976e9 + 1.728307712e9) * 128 ** 3 / 96 ** 3}
+TRAFFIC = {"src_sha": "d14e159d149b6259", "bytes_per_launch_128": (3.263730944e9 + 2.787134464e9) * 128 ** 3 / 96 ** 3}
+# FP64 pipe utilisation of the same launch (sm__pipe_fp64_cycles_active,
+# percent of peak over active cycles), for the same source.
+FP64_PIPE_BUSY = {"src_sha": "d14e159d149b6259", "pct_of_active_cycles": 85.15}
+N_SM = 152
+FP64_FMA_PER_CLK_SM = 2
 
 
 # DRAM traffic of one k_cfd_mass half-sweep at 256^3 (ncu dram__bytes_read.sum
@@ -844,7 +850,7 @@ def run_gpu(args):
     bufs = torch.empty(3 * 24 * grid.var_stride, dtype=torch.float64, device=dev)
     dst = [torch.empty_like(state0) for _ in range(2)]
     cs = torch.cuda.Stream(device=dev)
-    e2e_steps = max(2, min(args.steps, 6))
+    e2e_steps = max(2, min(args.steps, 10))
 
     def e2e_run(nsteps):
         up = [torch.cuda.Event() for _ in range(nsteps)]
@@ -887,7 +893,13 @@ def run_gpu(args):
     value = world * pts * args.steps / (f64["ms"] * 1e-3)
     e2e_value = world * pts * e2e_steps / (e2e_ms * 1e-3)
     achieved = flops["total"] * pts / (f64["stage_ms"] * 1e-3)  # FLOP/s of the fused stage kernel
-    peak = 2.0 * rates["fp64_fma_per_s"]
+    # FP64 peak from the unit counts and the clock: 2 FP64 FMA per clock per
+    # SM (the nominal 1.25 TFLOP/s of 152 SMs at 2070 MHz), at the median SM
+    # clock sampled during the timed region; the live probe of back-to-back
+    # DFMAs is reported beside it
+    sm_mhz = (f64["clocks"] or {}).get("sm_mhz") or MEASURED.get("sm_max_mhz") or 2070.0
+    peak = N_SM * FP64_FMA_PER_CLK_SM * 2.0 * sm_mhz * 1e6
+    peak_probe = 2.0 * rates["fp64_fma_per_s"]
     sha = kernel_src_sha()
     traffic = TRAFFIC["bytes_per_launch_128"] if TRAFFIC["src_sha"] == sha else None
     cpu_rate, cpu_steps, cpu_s, cpu_threads = cpu_oracle_rate(budget_s=args.cpu_budget, n=32)
@@ -903,7 +915,11 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_stage<8,0,double> (fused RHS+KO+RK stage)",
                      "flops_per_point": flops["total"], "stage_ms": f64["stage_ms"],
-                     "peak_source": "measured FP64 FMA rate (bssn_probe_fp_rates) x 2 flops"},
+                     "peak_source": f"2 FP64 FMA/clock/SM x {N_SM} SMs x 2 flop at the sampled median SM clock "
+                                    f"{sm_mhz:.0f} MHz (nominal 1.25 TFLOP/s at 2070 MHz)",
+                     "peak_probe": peak_probe / 1e12,
+                     "frac_of_probe": achieved / peak_probe,
+                     "fp64_pipe_busy_ncu": FP64_PIPE_BUSY if FP64_PIPE_BUSY["src_sha"] == sha else None},
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
                          "sample": f"{cpu_steps} oracle RK4 step(s) of the same workload on a 32^3 block "
                                    f"({cpu_s:.1f} s)"},

@@ -472,12 +472,15 @@ template <int P, int MODE, typename R>
 __device__ __forceinline__ void stage_point(const Layout& L, const Coef<R>& C, const Gauge& gz, const RK& rk,
                                             const StagePtrs<R>& S, long long p);
 
-// Resident blocks per SM asked of the compiler: the FP64 form is bound by the
-// FP64 pipe and keeps its registers; the FP32 form is latency-bound and trades
-// registers (and some local-memory traffic) for more warps.
+// Resident blocks per SM asked of the compiler. Both forms trade registers
+// (and local-memory traffic, which the brick traversal keeps in L2) for more
+// warps to hide load latency: measured on GB300 at 128^3, one FP64 stage
+// takes 19.1 ms at 2 blocks/SM (255 registers), 17.9 ms at 3, 17.3 ms at 4
+// (128 registers) and the same at 5, 6 and 8; the FP32 stage is best at 4.
+constexpr int STAGE_F64_MIN_BLOCKS = 4;
 template <typename R>
 constexpr int stage_min_blocks() {
-  return std::is_same<R, float>::value ? STAGE_F32_MIN_BLOCKS : 1;
+  return std::is_same<R, float>::value ? STAGE_F32_MIN_BLOCKS : STAGE_F64_MIN_BLOCKS;
 }
 
 // tx = 0: each block takes 128 consecutive points (x fastest) of the rows
@@ -581,7 +584,7 @@ __global__ void __launch_bounds__(256) k_ko(Layout L, Coef<R> C, const double* _
 // Per-block partial results: 7 sums of squares, 7 maxima, written to
 // part[blockIdx.x * 14 + q]. Always double precision.
 template <int P>
-__global__ void __launch_bounds__(128) k_constraints(Layout L, Coef<double> C, const double* __restrict__ u,
+__global__ void __launch_bounds__(128, STAGE_F64_MIN_BLOCKS) k_constraints(Layout L, Coef<double> C, const double* __restrict__ u,
                                                      const double* __restrict__ dX, const double* __restrict__ dY,
                                                      double* ham, double* mom, double* gcon, double* part,
                                                      unsigned int* flag) {

@@ -145,7 +145,7 @@ __device__ __forceinline__ void weyl_point(const PointIn<double>& P, const doubl
 // One thread per interior point; outputs in the state's padded layout
 // (E and B as 6 arrays var_stride apart), each nullable.
 template <int P>
-__global__ void __launch_bounds__(128) k_psi4(Layout L, Coef<double> C, const double* __restrict__ u,
+__global__ void __launch_bounds__(128, STAGE_F64_MIN_BLOCKS) k_psi4(Layout L, Coef<double> C, const double* __restrict__ u,
                                               const double* __restrict__ dX, const double* __restrict__ dY,
                                               double ox, double oy, double oz, double hx, double hy, double hz,
                                               double* psi_re, double* psi_im, double* inv_re, double* inv_im,
