@@ -428,6 +428,62 @@ def run_gpu(args):
         return {"value": world * n ** 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "stages_per_step": 3,
                 "ham_l2_after": float(l2[0]), "steps": args.steps + args.warmup}
 
+    def run_gauge_wave_24():
+        """The small periodic configuration: 24^3 gauge wave (A = 0.01 along x,
+        seeded 1e-10 noise, seed 1307) on [-0.5, 0.5]^3, 4th order, 3 ghosts,
+        1+log + Gamma-driver, KO 0.1, dt = dx/4, 10 RK4 steps through
+        bssn_rk4_step. 13,824 points: launch-latency bound, so the 10 steps
+        (130 launches) are also replayed as one captured CUDA graph."""
+        ug, hg = inputs.gauge_wave(24, 3, amplitude=0.01, noise=1e-10, seed=1307)
+        gq = B.make_grid(24, ghost=3, dx=hg)
+        pg = B.make_params(fd_order=4, ko_eps=0.1, lapse=0, shift=0, eta=2.0)
+        st = B.upload(ug, gq, device=dev)
+        s0 = st.clone()
+        bufs = torch.empty(3 * 24 * gq.var_stride, dtype=torch.float64, device=dev)
+        wk = B.alloc_work(gq, pg, device=dev)
+        dtg = 0.25 * hg
+
+        def ten():
+            for _ in range(10):
+                B.rk4_step(gq, pg, B.FP64, dtg, 0, None, st, bufs, wk)
+
+        for _ in range(args.warmup):
+            ten()
+        torch.cuda.synchronize()
+        reps = 5
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ten()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_eager = e0.elapsed_time(e1) / reps
+        # the same 10 steps captured once and replayed
+        cg = torch.cuda.CUDAGraph()
+        st.copy_(s0)
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            ten()  # warm the side stream before capture
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(cg, stream=side):
+            ten()
+        for _ in range(args.warmup):
+            cg.replay()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            cg.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_graph = e0.elapsed_time(e1) / reps
+        del bufs, wk
+        return {"value": world * 10 * 24 ** 3 / (ms_graph * 1e-3), "unit": UNIT, "ms_per_10_steps_graph": ms_graph,
+                "ms_per_10_steps_eager": ms_eager, "launches_per_10_steps": 130,
+                "workload": "24^3 gauge wave + 1e-10 noise, periodic, 4th order, 3 ghosts, 10 RK4 steps"}
+
     def run_paper_shape(nn, lo, hi, prec, method, steps):
         """A uniform Brill-Lindquist grid in one of the paper's own shapes,
         8th order, 5 ghosts, static boundary, timed through bssn_rk3_step
@@ -824,6 +880,7 @@ def run_gpu(args):
                             "share_of_rk4_step_if_every_step": ms_psi4 / (ms_psi4 + f64["ms"] / args.steps),
                             "outputs": "Psi_4 (re, im), invariant I (re, im), E_ij, B_ij at every interior point"}
     del wout
+    batched["gauge_wave_24"] = run_gauge_wave_24()
     batched["paper_shapes"] = run_paper_shapes()
     if not args.no_cfd:
         batched["cfd_sola_256"] = run_cfd()
