@@ -991,6 +991,13 @@ def run_gpu(args):
             "fp32_rhs": {"value": world * pts * args.steps / (f32["ms"] * 1e-3), "unit": UNIT,
                          "ms_per_step": f32["ms"] / args.steps, "stage_ms": f32["stage_ms"],
                          "achieved_tflops": achieved32 / 1e12, "frac_of_fp32_peak": achieved32 / peak32,
+                         # algorithmic bytes of the stage kernel per point and stage, averaged over
+                         # the four stages: FP32 stencil input 96, FP32 tables 88, FP64 W 8, y0 192,
+                         # acc read 144 and written 144, ynext 192
+                         "hbm": {"bytes_per_point_stage": 864,
+                                 "achieved_gbs": 864 * pts / (f32["stage_ms"] * 1e-3) / 1e9,
+                                 "frac": (864 * pts / (f32["stage_ms"] * 1e-3) / 1e9 / MEASURED["hbm_gbs"])
+                                 if MEASURED.get("hbm_gbs") else None},
                          "err_vs_fp64_max_rel_per_tensor": float(np.max(err32)),
                          "err_vs_fp64_per_var": [float(x) for x in err32],
                          "ham_l2_after": float(f32["l2"][0]), "gpu_launches": f32["launches"],
