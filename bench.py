@@ -196,6 +196,20 @@ def cpu_oracle_rate(budget_s=15.0, n=32, max_steps=None):
     return n ** 3 * steps / el, steps, el, threads
 
 
+def cpu_oracle_rate_single_thread(budget_s=4.0, n=16):
+    """The same oracle timing with one OpenMP thread, in a child process (the
+    thread count is fixed when the oracle library loads); returns
+    (updates/s, steps, seconds) or None if the child fails."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "r = bench.cpu_oracle_rate(budget_s=%r, n=%d); print(json.dumps(r[:3]))" % (ROOT, budget_s, n))
+    env = dict(os.environ, OMP_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+        return tuple(json.loads(out.stdout.strip().splitlines()[-1]))
+    except Exception:  # noqa: BLE001 - a baseline that could not be taken is reported as missing
+        return None
+
+
 def run_reference(args):
     # under torchrun only rank 0 times the oracle; the other ranks leave at
     # once (no process group: nothing is exchanged)
@@ -960,6 +974,7 @@ def run_gpu(args):
     sha = kernel_src_sha()
     traffic = TRAFFIC["bytes_per_launch_128"] if TRAFFIC["src_sha"] == sha else None
     cpu_rate, cpu_steps, cpu_s, cpu_threads = cpu_oracle_rate(budget_s=args.cpu_budget, n=32)
+    cpu_one = cpu_oracle_rate_single_thread()
     achieved32 = flops["total"] * pts / (f32["stage_ms"] * 1e-3)
     peak32 = 2.0 * rates["fp32_fma_per_s"]
     line = {
@@ -979,7 +994,10 @@ def run_gpu(args):
                      "fp64_pipe_busy_ncu": FP64_PIPE_BUSY if FP64_PIPE_BUSY["src_sha"] == sha else None},
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
                          "sample": f"{cpu_steps} oracle RK4 step(s) of the same workload on a 32^3 block "
-                                   f"({cpu_s:.1f} s)"},
+                                   f"({cpu_s:.1f} s)",
+                         "single_thread": None if cpu_one is None else {
+                             "value": cpu_one[0], "cores": 1,
+                             "sample": f"{cpu_one[1]} oracle RK4 step(s) on a 16^3 block ({cpu_one[2]:.1f} s)"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": flat_bytes, "d2h_bytes_per_step": flat_bytes,
                 "steps": e2e_steps, "overlap": "independent steps; uploads and downloads on a copy stream overlap "
                                               "the neighbouring steps' compute (two device states)"},
