@@ -991,6 +991,13 @@ def run_gpu(args):
                                     f"{sm_mhz:.0f} MHz (nominal 1.25 TFLOP/s at 2070 MHz)",
                      "peak_probe": peak_probe / 1e12,
                      "frac_of_probe": achieved / peak_probe,
+                     # the HBM side of the same kernel: algorithmic bytes per point and stage,
+                     # averaged over the four stages: ys 192, difference tables 704, y0 192,
+                     # acc read 144 and written 144, ynext 192
+                     "hbm": {"bytes_per_point_stage": 1568,
+                             "achieved_gbs": 1568 * pts / (f64["stage_ms"] * 1e-3) / 1e9,
+                             "frac": (1568 * pts / (f64["stage_ms"] * 1e-3) / 1e9 / MEASURED["hbm_gbs"])
+                             if MEASURED.get("hbm_gbs") else None},
                      "fp64_pipe_busy_ncu": FP64_PIPE_BUSY if FP64_PIPE_BUSY["src_sha"] == sha else None},
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
                          "sample": f"{cpu_steps} oracle RK4 step(s) of the same workload on a 32^3 block "
