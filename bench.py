@@ -57,10 +57,13 @@ except (OSError, ValueError):
 # scaled to 128^3 by
 # the point count, since the traffic is per point (state, tables and the
 # per-thread stack).
-TRAFFIC = {"src_sha": "d14e159d149b6259", "bytes_per_launch_128": (3.263730944e9 + 2.787134464e9) * 128 ** 3 / 96 ** 3}
+TRAFFIC = {"src_sha": "4dc52511f4f9e9aa", "bytes_per_launch_128": (3.263100928e9 + 2.787525376e9) * 128 ** 3 / 96 ** 3}
 # FP64 pipe utilisation of the same launch (sm__pipe_fp64_cycles_active,
 # percent of peak over active cycles), for the same source.
-FP64_PIPE_BUSY = {"src_sha": "d14e159d149b6259", "pct_of_active_cycles": 85.15}
+FP64_PIPE_BUSY = {"src_sha": "4dc52511f4f9e9aa", "pct_of_active_cycles": 85.14}
+# The same for the FP32-RHS stage kernel k_stage<8,0,float> (one launch at
+# 96^3: 0.581 GB read + 0.707 GB written, 1.46 kB per point), scaled to 128^3.
+TRAFFIC_F32 = {"src_sha": "4dc52511f4f9e9aa", "bytes_per_launch_128": (0.580835328e9 + 0.707021312e9) * 128 ** 3 / 96 ** 3}
 N_SM = 152
 FP64_FMA_PER_CLK_SM = 2
 
@@ -972,7 +975,7 @@ def run_gpu(args):
     peak = N_SM * FP64_FMA_PER_CLK_SM * 2.0 * sm_mhz * 1e6
     peak_probe = 2.0 * rates["fp64_fma_per_s"]
     sha = kernel_src_sha()
-    traffic = TRAFFIC["bytes_per_launch_128"] if TRAFFIC["src_sha"] == sha else None
+    traffic = TRAFFIC["bytes_per_launch_128"] if TRAFFIC["src_sha"] == sha and n == N else None
     cpu_rate, cpu_steps, cpu_s, cpu_threads = cpu_oracle_rate(budget_s=args.cpu_budget, n=32)
     cpu_one = cpu_oracle_rate_single_thread()
     achieved32 = flops["total"] * pts / (f32["stage_ms"] * 1e-3)
@@ -1022,7 +1025,9 @@ def run_gpu(args):
                          "hbm": {"bytes_per_point_stage": 864,
                                  "achieved_gbs": 864 * pts / (f32["stage_ms"] * 1e-3) / 1e9,
                                  "frac": (864 * pts / (f32["stage_ms"] * 1e-3) / 1e9 / MEASURED["hbm_gbs"])
-                                 if MEASURED.get("hbm_gbs") else None},
+                                 if MEASURED.get("hbm_gbs") else None,
+                                 "traffic": TRAFFIC_F32["bytes_per_launch_128"]
+                                 if TRAFFIC_F32["src_sha"] == sha and n == N else None},
                          "err_vs_fp64_max_rel_per_tensor": float(np.max(err32)),
                          "err_vs_fp64_per_var": [float(x) for x in err32],
                          "ham_l2_after": float(f32["l2"][0]), "gpu_launches": f32["launches"],

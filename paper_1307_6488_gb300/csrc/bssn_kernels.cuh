@@ -336,16 +336,39 @@ __device__ __forceinline__ void gather(const Layout& L, const Coef<R>& C, const 
 // chosen by the sign of beta^d through selects, mirrored for beta^d < 0).
 // Mixed derivatives are first derivatives of the D_x / D_y tables (k_d1tab).
 // About 1000 loads per point instead of the ~2450 of the exact-grouped gather.
+// The output is the lean per-point set: second derivatives of gt_ij and
+// beta^i are contracted with gt^ij as they are produced, and ext[v] carries
+// the advection (weighted as the gauge's right-hand side takes it) plus the
+// dissipation, so that fewer values stay live per thread.
 template <int P, bool WITH_KO, bool WITH_ADV>
-__device__ __forceinline__ void gather_lines(const Layout& L, const Coef<float>& C, const float* __restrict__ u,
-                                             const float* __restrict__ dX, const float* __restrict__ dY,
-                                             long long p, PointIn<float>& Q, float* ko_out) {
+__device__ __forceinline__ void gather_lines(const Layout& L, const Coef<float>& C, const Gauge& gz,
+                                             const float* __restrict__ u, const float* __restrict__ dX,
+                                             const float* __restrict__ dY, long long p, PointLean<float>& Q,
+                                             float* ext) {
   using F = FD<P>;
   constexpr int H = F::H, RR = F::R;
   const long long vs = L.vs;
   const long long st[3] = {1, L.sy, L.sz};
 #pragma unroll
   for (int v = 0; v < NV; ++v) Q.u[v] = __ldg(u + v * vs + p);
+  // contraction weights: hgu = -1/2 gt^lm and gu2 = gt^lm, off-diagonals doubled
+  float hgu[6], gu2[6];
+  {
+    float gu[6];
+    inverse_metric<float>(Q.u + V_GT11, gu);
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+      const bool off = s == 1 || s == 2 || s == 4;
+      gu2[s] = off ? gu[s] + gu[s] : gu[s];
+      hgu[s] = off ? -gu[s] : -0.5f * gu[s];
+    }
+  }
+  // advection weight of the gauge variables (0 where their right-hand side is frozen)
+  const float ag = gz.advect_gauge ? 1.f : 0.f;
+  const float w_alpha = gz.lapse == 2 ? 0.f : ag;
+  const float w_shift = gz.shift == 0 ? ag : 0.f;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) Q.dddb[j] = 0.f;
   bool neg[3];
   float ab[3];
 #pragma unroll
@@ -396,8 +419,10 @@ __device__ __forceinline__ void gather_lines(const Layout& L, const Coef<float>&
         adv = d == 0 ? ab[0] * w : fmaf(ab[d], w, adv);
       }
     }
-    if (WITH_KO) ko_out[var] = ko;
-    Q.adv[var] = WITH_ADV ? adv : 0.f;
+    {
+      const float wa = var == V_ALPHA ? w_alpha : (var >= V_BETA1 ? w_shift : 1.f);
+      ext[var] = (WITH_ADV ? wa * adv : 0.f) + (WITH_KO ? ko : 0.f);
+    }
     if (!need_d1) continue;
     if (var == V_TRK) {
 #pragma unroll
@@ -436,32 +461,33 @@ __device__ __forceinline__ void gather_lines(const Layout& L, const Coef<float>&
     } else if (m <= 6) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) Q.dg[d][m - 1] = d1v[d];
+      float r = hgu[0] * d2s[0];
 #pragma unroll
-      for (int q = 0; q < 6; ++q) Q.ddg[m - 1][q] = d2s[q];
+      for (int q = 1; q < 6; ++q) r = fmaf(hgu[q], d2s[q], r);
+      Q.lapg[m - 1] = r;
     } else if (m == 7) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) Q.da[d] = d1v[d];
 #pragma unroll
       for (int q = 0; q < 6; ++q) Q.dda[q] = d2s[q];
     } else {
+      const int i = m - 8;  // beta^i
 #pragma unroll
-      for (int d = 0; d < 3; ++d) Q.db[d][m - 8] = d1v[d];
+      for (int d = 0; d < 3; ++d) Q.db[d][i] = d1v[d];
+      float r = gu2[0] * d2s[0];
 #pragma unroll
-      for (int q = 0; q < 6; ++q) Q.ddb[m - 8][q] = d2s[q];
+      for (int q = 1; q < 6; ++q) r = fmaf(gu2[q], d2s[q], r);
+      Q.lapb[i] = r;
+      // d_j d_i beta^i, summed over i as the shift components arrive
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Q.dddb[j] += d2s[sym(j, i)];
     }
   }
 }
 
 // 1/W: always computed in double precision (the conformal-factor division
 // that dominates near punctures)
-template <typename R>
-__device__ __forceinline__ R inv_w(const PointIn<R>& Q, const double* ys64, long long p, long long vs);
-template <>
-__device__ __forceinline__ double inv_w<double>(const PointIn<double>& Q, const double*, long long, long long) {
-  return 1.0 / Q.u[V_W];
-}
-template <>
-__device__ __forceinline__ float inv_w<float>(const PointIn<float>&, const double* ys64, long long p, long long) {
+__device__ __forceinline__ float inv_w(const double* ys64, long long p) {
   return __double2float_rn(1.0 / __ldg(ys64 + p));  // W is variable 0
 }
 
@@ -515,15 +541,25 @@ __global__ void __launch_bounds__(128, stage_min_blocks<R>()) k_stage(Layout L, 
 template <int P, int MODE, typename R>
 __device__ __forceinline__ void stage_point(const Layout& L, const Coef<R>& C, const Gauge& gz, const RK& rk,
                                             const StagePtrs<R>& S, long long p) {
-  PointIn<R> Q;
+  // FP64: the full per-point set, ko = dissipation. FP32: the lean set
+  // (contracted second derivatives), ko = advection + dissipation.
+  using PT = typename std::conditional<std::is_same<R, float>::value, PointLean<R>, PointIn<R>>::type;
+  PT Q;
   R ko[NV];
-  if constexpr (std::is_same<R, float>::value)
-    gather_lines<P, MODE == 0, true>(L, C, S.ys, S.dX, S.dY, p, Q, ko);
-  else
-    gather<P, MODE == 0, true, R>(L, C, S.ys, S.dX, S.dY, p, Q, ko);
   R rhs[NV];
-  const R iW = inv_w<R>(Q, S.ys64, p, L.vs);
-  rhs_point<R>(Q, gz, iW, rhs);
+  if constexpr (std::is_same<R, float>::value) {
+    gather_lines<P, MODE == 0, true>(L, C, gz, S.ys, S.dX, S.dY, p, Q, ko);
+    const R iW = inv_w(S.ys64, p);
+    rhs_point<R>(Q, gz, iW, rhs);
+    if (MODE == 1) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) rhs[v] += ko[v];
+    }
+  } else {
+    gather<P, MODE == 0, true, R>(L, C, S.ys, S.dX, S.dY, p, Q, ko);
+    const R iW = R(1) / Q.u[V_W];
+    rhs_point<R>(Q, gz, iW, rhs);
+  }
   const long long vs = L.vs;
   if (MODE == 1) {
 #pragma unroll

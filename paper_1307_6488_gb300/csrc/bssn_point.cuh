@@ -40,6 +40,75 @@ struct PointIn {
   R adv[NV];     // beta^k dhat_k u_v
 };
 
+// The FP32-RHS form's per-point set. The second derivatives of gt_ij and of
+// beta^i enter the right-hand side only through contractions with gt^ij, so
+// the gather forms those contractions as each derivative is produced and
+// keeps 12 values instead of 54; advection enters additively and is carried
+// by the caller together with the dissipation.
+template <typename R>
+struct PointLean {
+  R u[NV];
+  R dW[3], dK[3], da[3];
+  R dg[3][6];
+  R dGam[3][3];
+  R db[3][3];
+  R ddW[6], dda[6];
+  R lapg[6];  // -1/2 gt^lm d_l d_m gt_s
+  R lapb[3];  // gt^jk d_j d_k beta^i
+  R dddb[3];  // d_j d_k beta^k
+};
+
+// inverse conformal metric gt^ij from gt_ij (packed xx, xy, xz, yy, yz, zz)
+template <typename R>
+__device__ __forceinline__ void inverse_metric(const R* g, R gu[6]) {
+  const R c0 = g[3] * g[5] - g[4] * g[4];
+  const R c1 = g[2] * g[4] - g[1] * g[5];
+  const R c2 = g[1] * g[4] - g[2] * g[3];
+  const R c3 = g[0] * g[5] - g[2] * g[2];
+  const R c4 = g[1] * g[2] - g[0] * g[4];
+  const R c5 = g[0] * g[3] - g[1] * g[1];
+  const R idet = R(1) / (g[0] * c0 + g[1] * c1 + g[2] * c2);
+  gu[0] = c0 * idet; gu[1] = c1 * idet; gu[2] = c2 * idet;
+  gu[3] = c3 * idet; gu[4] = c4 * idet; gu[5] = c5 * idet;
+}
+
+// -1/2 gt^lm d_l d_m gt_s, given hgu = -1/2 gt^lm with the off-diagonal
+// entries doubled
+template <typename R>
+__device__ __forceinline__ R metric_laplacian(const PointIn<R>& P, const R hgu[6], int s) {
+  R r = hgu[0] * P.ddg[s][0];
+#pragma unroll
+  for (int t = 1; t < 6; ++t) r += hgu[t] * P.ddg[s][t];
+  return r;
+}
+template <typename R>
+__device__ __forceinline__ R metric_laplacian(const PointLean<R>& P, const R*, int s) { return P.lapg[s]; }
+
+// gt^jk d_j d_k beta^i (gu2: gt^jk with the off-diagonal entries doubled)
+template <typename R>
+__device__ __forceinline__ R shift_laplacian(const PointIn<R>& P, const R gu2[6], int i) {
+  R t3 = gu2[0] * P.ddb[i][0];
+#pragma unroll
+  for (int s = 1; s < 6; ++s) t3 += gu2[s] * P.ddb[i][s];
+  return t3;
+}
+template <typename R>
+__device__ __forceinline__ R shift_laplacian(const PointLean<R>& P, const R*, int i) { return P.lapb[i]; }
+
+// d_j d_k beta^k
+template <typename R>
+__device__ __forceinline__ R grad_div_shift(const PointIn<R>& P, int j) {
+  return P.ddb[0][sym(j, 0)] + P.ddb[1][sym(j, 1)] + P.ddb[2][sym(j, 2)];
+}
+template <typename R>
+__device__ __forceinline__ R grad_div_shift(const PointLean<R>& P, int j) { return P.dddb[j]; }
+
+// advection of variable v, or 0 where the caller adds it
+template <typename R>
+__device__ __forceinline__ R advection(const PointIn<R>& P, int v) { return P.adv[v]; }
+template <typename R>
+__device__ __forceinline__ R advection(const PointLean<R>&, int) { return R(0); }
+
 // Geometry shared by the right-hand side and the constraints.
 template <typename R>
 struct Geo {
@@ -52,19 +121,9 @@ struct Geo {
   R dWu[3];       // gt^kl d_l W
 };
 
-template <typename R>
-__device__ __forceinline__ void geometry(const PointIn<R>& P, R iW, Geo<R>& G) {
-  const R* g = P.u + V_GT11;
-  // inverse conformal metric
-  const R c0 = g[3] * g[5] - g[4] * g[4];
-  const R c1 = g[2] * g[4] - g[1] * g[5];
-  const R c2 = g[1] * g[4] - g[2] * g[3];
-  const R c3 = g[0] * g[5] - g[2] * g[2];
-  const R c4 = g[1] * g[2] - g[0] * g[4];
-  const R c5 = g[0] * g[3] - g[1] * g[1];
-  const R idet = R(1) / (g[0] * c0 + g[1] * c1 + g[2] * c2);
-  G.gu[0] = c0 * idet; G.gu[1] = c1 * idet; G.gu[2] = c2 * idet;
-  G.gu[3] = c3 * idet; G.gu[4] = c4 * idet; G.gu[5] = c5 * idet;
+template <typename R, template <typename> class PT>
+__device__ __forceinline__ void geometry(const PT<R>& P, R iW, Geo<R>& G) {
+  inverse_metric<R>(P.u + V_GT11, G.gu);
 #pragma unroll
   for (int s = 0; s < 6; ++s) G.gu2[s] = (s == 1 || s == 2 || s == 4) ? G.gu[s] + G.gu[s] : G.gu[s];
 
@@ -128,9 +187,7 @@ __device__ __forceinline__ void geometry(const PointIn<R>& P, R iW, Geo<R>& G) {
   for (int s = 0; s < 6; ++s) {
     const int i = sym_i(s), j = sym_j(s);
     // -1/2 gt^lm d_l d_m gt_ij
-    R r = hgu[0] * P.ddg[s][0];
-#pragma unroll
-    for (int t = 1; t < 6; ++t) r += hgu[t] * P.ddg[s][t];
+    R r = metric_laplacian<R>(P, hgu, s);
     // 1/2 (gt_ki d_j Gt^k + gt_kj d_i Gt^k) + 1/2 Gd^k (Gt_{i,jk} + Gt_{j,ik})
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -164,10 +221,10 @@ __device__ __forceinline__ void geometry(const PointIn<R>& P, R iW, Geo<R>& G) {
 }
 
 // Right-hand side of the 24 evolved variables (without dissipation).
-template <typename R>
-__device__ __forceinline__ void rhs_point(const PointIn<R>& P, const Gauge& gz, R iW, R rhs[NV]) {
+template <typename R, template <typename> class PT>
+__device__ __forceinline__ void rhs_point(const PT<R>& P, const Gauge& gz, R iW, R rhs[NV]) {
   Geo<R> G;
-  geometry<R>(P, iW, G);
+  geometry<R, PT>(P, iW, G);
   const R* u = P.u;
   const R W = u[V_W], K = u[V_TRK], al = u[V_ALPHA];
   const R* g = u + V_GT11;
@@ -217,8 +274,8 @@ __device__ __forceinline__ void rhs_point(const PointIn<R>& P, const Gauge& gz, 
   const R divb = P.db[0][0] + P.db[1][1] + P.db[2][2];
   const R divb23 = twothirds * divb;
 
-  rhs[V_W] = P.adv[V_W] + third * W * (al * K - divb);
-  rhs[V_TRK] = P.adv[V_TRK] - W2 * trDDa + al * (AA + third * K * K);
+  rhs[V_W] = advection<R>(P, V_W) + third * W * (al * K - divb);
+  rhs[V_TRK] = advection<R>(P, V_TRK) - W2 * trDDa + al * (AA + third * K * K);
   const R al2 = al + al;
 #pragma unroll
   for (int s = 0; s < 6; ++s) {
@@ -226,19 +283,19 @@ __device__ __forceinline__ void rhs_point(const PointIn<R>& P, const Gauge& gz, 
     R lg = g[sym(i, 0)] * P.db[j][0] + g[sym(j, 0)] * P.db[i][0];
     lg += g[sym(i, 1)] * P.db[j][1] + g[sym(j, 1)] * P.db[i][1];
     lg += g[sym(i, 2)] * P.db[j][2] + g[sym(j, 2)] * P.db[i][2];
-    rhs[V_GT11 + s] = P.adv[V_GT11 + s] - al2 * A[s] + lg - divb23 * g[s];
+    rhs[V_GT11 + s] = advection<R>(P, V_GT11 + s) - al2 * A[s] + lg - divb23 * g[s];
     R la = A[sym(i, 0)] * P.db[j][0] + A[sym(j, 0)] * P.db[i][0];
     la += A[sym(i, 1)] * P.db[j][1] + A[sym(j, 1)] * P.db[i][1];
     la += A[sym(i, 2)] * P.db[j][2] + A[sym(j, 2)] * P.db[i][2];
     const R AAm = A[sym(i, 0)] * Am[0][j] + A[sym(i, 1)] * Am[1][j] + A[sym(i, 2)] * Am[2][j];
     const R XTF = X[s] - trX3 * g[s];
-    rhs[V_AT11 + s] = P.adv[V_AT11 + s] + W2 * XTF + al * (K * A[s] - R(2) * AAm) + la - divb23 * A[s];
+    rhs[V_AT11 + s] = advection<R>(P, V_AT11 + s) + W2 * XTF + al * (K * A[s] - R(2) * AAm) + la - divb23 * A[s];
   }
 
   // Gamma-tilde: terms without advection
   R dddb[3];  // d_j d_k beta^k
 #pragma unroll
-  for (int j = 0; j < 3; ++j) dddb[j] = P.ddb[0][sym(j, 0)] + P.ddb[1][sym(j, 1)] + P.ddb[2][sym(j, 2)];
+  for (int j = 0; j < 3; ++j) dddb[j] = grad_div_shift<R>(P, j);
   R Au2[6];
 #pragma unroll
   for (int s = 0; s < 6; ++s) Au2[s] = (s == 1 || s == 2 || s == 4) ? Au[s] + Au[s] : Au[s];
@@ -246,9 +303,7 @@ __device__ __forceinline__ void rhs_point(const PointIn<R>& P, const Gauge& gz, 
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const R t1 = G.Gd[0] * P.db[0][i] + G.Gd[1] * P.db[1][i] + G.Gd[2] * P.db[2][i];
-    R t3 = G.gu2[0] * P.ddb[i][0];
-#pragma unroll
-    for (int s = 1; s < 6; ++s) t3 += G.gu2[s] * P.ddb[i][s];
+    const R t3 = shift_laplacian<R>(P, G.gu2, i);
     const R t4 = G.gu[sym(i, 0)] * dddb[0] + G.gu[sym(i, 1)] * dddb[1] + G.gu[sym(i, 2)] * dddb[2];
     const R t5 = Au[sym(i, 0)] * da[0] + Au[sym(i, 1)] * da[1] + Au[sym(i, 2)] * da[2];
     R t6 = Au2[0] * G.GU[i][0];
@@ -258,22 +313,22 @@ __device__ __forceinline__ void rhs_point(const PointIn<R>& P, const Gauge& gz, 
     const R t8 = G.gu[sym(i, 0)] * P.dK[0] + G.gu[sym(i, 1)] * P.dK[1] + G.gu[sym(i, 2)] * P.dK[2];
     gam_na[i] = (t3 - t1) + divb23 * G.Gd[i] + third * t4 - R(2) * t5 +
                 al2 * (t6 - R(3) * iW * t7 - twothirds * t8);
-    rhs[V_GAM1 + i] = P.adv[V_GAM1 + i] + gam_na[i];
+    rhs[V_GAM1 + i] = advection<R>(P, V_GAM1 + i) + gam_na[i];
   }
 
   // gauge
   const R ag = gz.advect_gauge ? R(1) : R(0);
   if (gz.lapse == 0)
-    rhs[V_ALPHA] = ag * P.adv[V_ALPHA] - al2 * K;
+    rhs[V_ALPHA] = ag * advection<R>(P, V_ALPHA) - al2 * K;
   else if (gz.lapse == 1)
-    rhs[V_ALPHA] = ag * P.adv[V_ALPHA] - al * al * K;
+    rhs[V_ALPHA] = ag * advection<R>(P, V_ALPHA) - al * al * K;
   else
     rhs[V_ALPHA] = R(0);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (gz.shift == 0) {
-      rhs[V_BETA1 + i] = ag * P.adv[V_BETA1 + i] + R(gz.shift_coeff) * u[V_B1 + i];
-      rhs[V_B1 + i] = ag * P.adv[V_B1 + i] + gam_na[i] - R(gz.eta) * u[V_B1 + i];
+      rhs[V_BETA1 + i] = ag * advection<R>(P, V_BETA1 + i) + R(gz.shift_coeff) * u[V_B1 + i];
+      rhs[V_B1 + i] = ag * advection<R>(P, V_B1 + i) + gam_na[i] - R(gz.eta) * u[V_B1 + i];
     } else {
       rhs[V_BETA1 + i] = R(0);
       rhs[V_B1 + i] = R(0);
@@ -285,7 +340,7 @@ __device__ __forceinline__ void rhs_point(const PointIn<R>& P, const Gauge& gz, 
 template <typename R>
 __device__ __forceinline__ void constraints_point(const PointIn<R>& P, const R dAt[3][6], R iW, R out[7]) {
   Geo<R> G;
-  geometry<R>(P, iW, G);
+  geometry<R, PointIn>(P, iW, G);
   const R* u = P.u;
   const R W = u[V_W], K = u[V_TRK];
   const R* A = u + V_AT11;
