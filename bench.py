@@ -68,9 +68,9 @@ N_SM = 152
 FP64_FMA_PER_CLK_SM = 2
 
 
-# DRAM traffic of one k_cfd_mass half-sweep at 256^3 (ncu dram__bytes_read.sum
-# + dram__bytes_write.sum: 271.2 MB + 214.4 MB), for the source it was taken on.
-CFD_TRAFFIC = {"src_sha": "d178fa7f0bde38d3", "bytes_per_launch": 271207168 + 214392320}
+# DRAM traffic of one k_cfd_mass_rb iteration at 256^3 (ncu dram__bytes_read.sum
+# + dram__bytes_write.sum), for the source it was taken on.
+CFD_TRAFFIC = {"src_sha": "56fd0bec3fd294aa", "bytes_per_launch": 288074496 + 228016640}
 
 # the sources that make up the fused FP64 stage kernel k_stage<8,0,double>
 STAGE_SOURCES = ("bssn_common.cuh", "bssn_point.cuh", "bssn_kernels.cuh", "bssn_order.cu")
@@ -574,21 +574,24 @@ def run_gpu(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = max_over_ranks(e0.elapsed_time(e1), world, dev) / args.steps
-        # the dominant kernel alone: mass-conservation half-sweeps, CUDA events
-        # on the launching stream
+        # the dominant kernel alone: one fused mass-conservation iteration
+        # (both colours), faces alternating between the two sets of arrays,
+        # CUDA events on the launching stream
+        src, dst = (u_, v_, w_), tuple(scratch[i * ((npts + 3) // 4 * 4):][:npts] for i in range(3))
         ev = []
-        for it in range(2 * args.steps):
+        for it in range(args.steps):
             ev.append(torch.cuda.Event(enable_timing=True))
             ev[-1].record(stream)
-            B.cfd_mass(d, it % 2, u_, v_, w_, p_)
+            B.cfd_mass_iteration(d, *src, *dst, p_)
             ev.append(torch.cuda.Event(enable_timing=True))
             ev[-1].record(stream)
+            src, dst = dst, src
         torch.cuda.synchronize()
         mass_ms = float(np.mean([ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(len(ev) // 2)]))
         cells = Nc ** 3
-        # algorithmic bytes per cell and half-sweep: u, v, w read and every face
-        # written once (12 + 12), p read and written for half the cells (2 + 2)
-        mass_bytes = 28.0 * cells
+        # algorithmic bytes per cell and iteration: u, v, w read and every face
+        # written once (12 + 12), p read and written (4 + 4)
+        mass_bytes = 32.0 * cells
         hbm = MEASURED.get("hbm_gbs")
         fin = bool(torch.isfinite(u_).all() and torch.isfinite(p_).all())
         umax = float(u_.view(Nc + 2, Nc + 2, Nc + 2)[1:-1, 1:-1, 1:-1].abs().max())  # interior (the lid ghost is 2U - u)
@@ -597,10 +600,10 @@ def run_gpu(args):
         return {"value": world * cells / (ms * 1e-3), "unit": "cell updates/s", "ms_per_step": ms,
                 "mass_iterations_per_step": iters, "gflops_algorithmic": world * 295 * cells / (ms * 1e-3) / 1e9,
                 "flops_per_cell_step": 295, "finite": fin, "max_abs_u_interior": umax,
-                "roofline": {"bound": "hbm", "kernel": "k_cfd_mass (one red-black half-sweep)",
+                "roofline": {"bound": "hbm", "kernel": "k_cfd_mass_rb (one red-black iteration in one pass)",
                              "achieved": mass_bytes / (mass_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                              "frac": (mass_bytes / (mass_ms * 1e-3) / 1e9 / hbm) if hbm else None,
-                             "launch_ms": mass_ms, "bytes_per_cell": 28,
+                             "launch_ms": mass_ms, "bytes_per_cell": 32,
                              "traffic": CFD_TRAFFIC["bytes_per_launch"] if CFD_TRAFFIC["src_sha"] == src_sha(
                                  ("bssn_cfd.cu",)) else None},
                 "paper_context": "90.5 GFlop/s (Chemora) and 43 GFlop/s (Physis) on one NVIDIA M2050, 256^3, "

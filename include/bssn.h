@@ -415,9 +415,23 @@ bssn_status_t bssn_cfd_velocity(const bssn_cfd_t* desc, const float* u, const fl
  * 1), in place on u, v, w, p. One iteration is colour 0 then colour 1. */
 bssn_status_t bssn_cfd_mass(const bssn_cfd_t* desc, int colour, float* u, float* v, float* w, float* p,
                             void* stream);
+/* One mass-conservation iteration (colour 0 then colour 1) in one pass: the
+ * faces from u, v, w (read only) into un, vn, wn, p in place. Equals
+ * bssn_cfd_mass with colour 0 then colour 1 on u, v, w bit for bit, the
+ * faces landing in un, vn, wn: their interior entries and the low wall faces
+ * (-1) are written, other ghost entries are not. Reads the interior entries
+ * and low wall faces of u, v, w, and the interior of p. The seven arrays
+ * must be distinct. */
+bssn_status_t bssn_cfd_mass_iteration(const bssn_cfd_t* desc, const float* u, const float* v, const float* w,
+                                      float* un, float* vn, float* wn, float* p, void* stream);
 /* One time step in place: boundary, velocity, boundary, then `iterations`
- * times (mass colour 0, mass colour 1, boundary). scratch: DEVICE, 16-byte
- * aligned, 3 * round_up(bssn_cfd_points(), 4) floats. */
+ * times (mass colour 0, mass colour 1, boundary); the result equals that
+ * sequence bit for bit. Each iteration runs as one fused pass between u, v,
+ * w and the scratch (bssn_cfd_mass_iteration), p in place; the boundary
+ * runs after the velocity kernel and once after the last iteration, since
+ * the iterations read no ghost entry but the low wall faces, which they
+ * carry over. scratch: DEVICE, 16-byte aligned, 3 * round_up(
+ * bssn_cfd_points(), 4) floats, contents ignored. */
 bssn_status_t bssn_cfd_step(const bssn_cfd_t* desc, int iterations, float* u, float* v, float* w, float* p,
                             float* scratch, void* stream);
 

@@ -585,7 +585,9 @@ def _cfd_lib():
         L.bssn_cfd_velocity.argtypes = [D, _p, _p, _p, _p, _p, _p, _p, _p]
         L.bssn_cfd_mass.argtypes = [D, ctypes.c_int, _p, _p, _p, _p, _p]
         L.bssn_cfd_step.argtypes = [D, ctypes.c_int, _p, _p, _p, _p, _p, _p]
-        for n in ("bssn_cfd_boundary", "bssn_cfd_velocity", "bssn_cfd_mass", "bssn_cfd_step"):
+        L.bssn_cfd_mass_iteration.argtypes = [D, _p, _p, _p, _p, _p, _p, _p, _p]
+        for n in ("bssn_cfd_boundary", "bssn_cfd_velocity", "bssn_cfd_mass", "bssn_cfd_mass_iteration",
+                  "bssn_cfd_step"):
             getattr(L, n).restype = ctypes.c_int
         L._cfd_typed = True
     return L
@@ -608,6 +610,11 @@ def cfd_velocity(desc, u, v, w, p, un, vn, wn, stream=None):
 def cfd_mass(desc, colour, u, v, w, p, stream=None):
     _check(_cfd_lib().bssn_cfd_mass(ctypes.byref(desc), colour, _ptr(u), _ptr(v), _ptr(w), _ptr(p),
                                     _stream(stream)), "cfd_mass")
+
+
+def cfd_mass_iteration(desc, u, v, w, un, vn, wn, p, stream=None):
+    _check(_cfd_lib().bssn_cfd_mass_iteration(ctypes.byref(desc), _ptr(u), _ptr(v), _ptr(w), _ptr(un), _ptr(vn),
+                                              _ptr(wn), _ptr(p), _stream(stream)), "cfd_mass_iteration")
 
 
 def cfd_step(desc, iterations, u, v, w, p, scratch, stream=None):

@@ -47,6 +47,7 @@ struct Cfd {
   float ih[3], i4h[3], dth[3];  // 1/h, 1/(4h), dt/h: no division in the kernels
   int per[3];
   float nu, dt, omega, alpha, lid, g[3];
+  float beta_in;  // beta of a cell whose six faces all move (the same float operations as the kernels)
 };
 
 __host__ __device__ __forceinline__ long long cidx(const Cfd& C, int i, int j, int k) {
@@ -108,8 +109,48 @@ __global__ void __launch_bounds__(CFD_THREADS) k_cfd_velocity(Cfd C, const float
   }
 }
 
-// --- kernel 2: mass conservation (one red-black half-sweep) ---------------------------------
+// --- kernel 2: mass conservation -------------------------------------------------------------
+// The arithmetic of one cell's update, shared by the half-sweep and the fused
+// iteration below so that the two give the same bits: every rounding is
+// spelled out (no contraction left to the compiler).
 
+// movable faces of cell c3 along each axis, beta and the low-face offsets
+struct CellFaces {
+  long long lo[3];
+  bool mlo[3], mhi[3];
+  float beta;
+};
+
+__device__ __forceinline__ CellFaces cell_faces(const Cfd& C, const int c3[3], long long o) {
+  const long long st[3] = {1, C.sy, C.sz};
+  CellFaces F;
+  float s = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    // low face: the neighbour's face, or face n-1 for cell 0 of a periodic axis
+    F.lo[a] = (C.per[a] && c3[a] == 0) ? o + (long long)(C.n[a] - 1) * st[a] : o - st[a];
+    F.mlo[a] = C.per[a] || c3[a] > 0;
+    F.mhi[a] = C.per[a] || c3[a] < C.n[a] - 1;
+    s = __fadd_rn(__fadd_rn(s, F.mlo[a] ? C.ih2[a] : 0.f), F.mhi[a] ? C.ih2[a] : 0.f);
+  }
+  const bool inner = F.mlo[0] && F.mhi[0] && F.mlo[1] && F.mhi[1] && F.mlo[2] && F.mhi[2];
+  F.beta = inner ? C.beta_in : __fdiv_rn(C.omega, __fmul_rn(C.dt, s));
+  return F;
+}
+
+// dp = -beta D from the cell's high and low face values
+__device__ __forceinline__ float cell_dp(const Cfd& C, float beta, const float fhi[3], const float flo[3]) {
+  float div = __fmul_rn(__fsub_rn(fhi[0], flo[0]), C.ih[0]);
+  div = __fmaf_rn(__fsub_rn(fhi[1], flo[1]), C.ih[1], div);
+  div = __fmaf_rn(__fsub_rn(fhi[2], flo[2]), C.ih[2], div);
+  return __fmul_rn(-beta, div);
+}
+
+// the faces moved by dp: the high face outward (+), the low face (-)
+__device__ __forceinline__ float move_hi(const Cfd& C, int a, float dp, float f) { return __fmaf_rn(C.dth[a], dp, f); }
+__device__ __forceinline__ float move_lo(const Cfd& C, int a, float dp, float f) { return __fmaf_rn(-C.dth[a], dp, f); }
+
+// one red-black half-sweep, in place
 __global__ void __launch_bounds__(CFD_THREADS) k_cfd_mass(Cfd C, int colour, float* __restrict__ u,
                                                           float* __restrict__ v, float* __restrict__ w,
                                                           float* __restrict__ p) {
@@ -124,30 +165,206 @@ __global__ void __launch_bounds__(CFD_THREADS) k_cfd_mass(Cfd C, int colour, flo
     if (i >= C.n[0]) continue;
     const int c3[3] = {i, j, k};
     const long long o = cidx(C, i, j, k);
-    const long long st[3] = {1, C.sy, C.sz};
     float* F[3] = {u, v, w};
-    long long lo[3];
-    bool mlo[3], mhi[3];
-    float s = 0.f;
+    const CellFaces cf = cell_faces(C, c3, o);
+    float fhi[3], flo[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      // low face: the neighbour's face, or face n-1 for cell 0 of a periodic axis
-      lo[a] = (C.per[a] && c3[a] == 0) ? o + (long long)(C.n[a] - 1) * st[a] : o - st[a];
-      mlo[a] = C.per[a] || c3[a] > 0;
-      mhi[a] = C.per[a] || c3[a] < C.n[a] - 1;
-      s = s + (mlo[a] ? C.ih2[a] : 0.f) + (mhi[a] ? C.ih2[a] : 0.f);
+      fhi[a] = F[a][o];
+      flo[a] = F[a][cf.lo[a]];
     }
-    const float beta = C.omega / (C.dt * s);
-    const float div = (F[0][o] - F[0][lo[0]]) * C.ih[0] + (F[1][o] - F[1][lo[1]]) * C.ih[1] +
-                      (F[2][o] - F[2][lo[2]]) * C.ih[2];
-    const float dp = -beta * div;
-    p[o] += dp;
+    const float dp = cell_dp(C, cf.beta, fhi, flo);
+    p[o] = __fadd_rn(p[o], dp);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const float cfa = C.dth[a] * dp;
-      if (mhi[a]) F[a][o] += cfa;
-      if (mlo[a]) F[a][lo[a]] -= cfa;
+      if (cf.mhi[a]) F[a][o] = move_hi(C, a, dp, fhi[a]);
+      if (cf.mlo[a]) F[a][cf.lo[a]] = move_lo(C, a, dp, flo[a]);
     }
+  }
+}
+
+// One whole mass-conservation iteration (colour 0, then colour 1) in one
+// pass: faces from (u, v, w) into (un, vn, wn), p in place. Every movable
+// face lies between a colour-0 and a colour-1 cell, so its value after the
+// iteration is the old value moved by the colour-0 cell's dp, then by the
+// colour-1 cell's dp (computed from the faces after the first move). The
+// colour-1 cell writes it; a wall face is copied by its one cell; p is read
+// and written by its own cell only. The colour-0 dp of a block's box and a
+// one-cell halo (periodic axes wrap) are recomputed per block, plane by
+// plane in z, through shared memory. The result equals the two half-sweeps
+// bit for bit (the same per-cell arithmetic).
+// Box of 32 x 4 cells x 16 planes per block: measured best on GB300 at 256^3
+// among 4-16 rows and 4-64 planes (fewer, taller boxes leave the SMs short
+// of independent work).
+constexpr int RB_TX = 32, RB_TY = 4, RB_KC = 16;
+
+__device__ __forceinline__ bool wrap_cell(const Cfd& C, int a, int& c) {
+  if (c >= 0 && c < C.n[a]) return true;
+  if (!C.per[a]) return false;
+  c = c < 0 ? c + C.n[a] : c - C.n[a];
+  return true;
+}
+
+__global__ void __launch_bounds__(RB_TX * RB_TY) k_cfd_mass_rb(Cfd C, const float* __restrict__ u,
+                                                               const float* __restrict__ v,
+                                                               const float* __restrict__ w, float* __restrict__ un,
+                                                               float* __restrict__ vn, float* __restrict__ wn,
+                                                               float* __restrict__ p) {
+  __shared__ float dps[3][RB_TY + 2][RB_TX + 2];
+  const float* S[3] = {u, v, w};
+  float* D[3] = {un, vn, wn};
+  const int i0 = (int)blockIdx.x * RB_TX, j0 = (int)blockIdx.y * RB_TY, k0 = (int)blockIdx.z * RB_KC;
+  const int k1 = min(k0 + RB_KC, C.n[2]);
+  // colour-0 pass: thread t < 17 (RB_TY + 2) takes colour-0 cell t % 17 of
+  // halo row t / 17 (a halo row is RB_TX + 2 = 34 cells, 17 of each colour);
+  // update pass: the first half of the threads take the 16 colour-1 cells of
+  // each of the RB_TY rows, the second half the colour-0 cells (warp-uniform
+  // branches)
+  constexpr int HALF = (RB_TX + 2) / 2;
+  const int t = (int)threadIdx.x;
+  const bool col1 = t < RB_TX * RB_TY / 2;
+  const int t2 = col1 ? t : t - RB_TX * RB_TY / 2;
+  const int ty = t2 / (RB_TX / 2), m2 = t2 % (RB_TX / 2);
+  // A box whose halo cells all lie inside the domain, away from its walls
+  // and its periodic seams, has every face of every cell movable: no masks,
+  // no wrap-around, beta_in everywhere, and 32-bit offsets within a plane.
+  // Most boxes are of this kind; they take the short path below.
+  const bool inner = i0 >= 2 && i0 + RB_TX <= C.n[0] - 2 && j0 >= 2 && j0 + RB_TY <= C.n[1] - 2 && k0 >= 2 &&
+                     k0 + RB_KC <= C.n[2] - 2;
+  if (inner) {
+    const int sy = (int)C.sy;
+    const long long st[3] = {1, C.sy, C.sz};
+    for (int k = k0 - 1; k <= k1; ++k) {
+      const int kc = k - 1;
+      const int tx = 2 * m2 + ((i0 + j0 + ty + kc + (col1 ? 1 : 0)) & 1);
+      const bool mine = kc >= k0;
+      const long long o = cidx(C, i0, j0, kc) + tx + ty * sy;
+      float fhi[3], flo[3], p0 = 0.f;
+      if (mine) {
+        p0 = p[o];
+        if (col1) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            fhi[a] = __ldg(S[a] + o);
+            flo[a] = __ldg(S[a] + o - st[a]);
+          }
+        }
+      }
+      const int slot = (k + 3) % 3;
+      if (t < HALF * (RB_TY + 2)) {
+        const int r = t / HALF;
+        const int x = 2 * (t % HALF) + ((i0 + j0 + r + k) & 1);  // i + j + k even, i = i0 - 1 + x, j = j0 - 1 + r
+        const long long oh = cidx(C, i0, j0, k) + (x - 1) + (r - 1) * sy;
+        float hhi[3], hlo[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          hhi[a] = __ldg(S[a] + oh);
+          hlo[a] = __ldg(S[a] + oh - st[a]);
+        }
+        dps[slot][r][x] = cell_dp(C, C.beta_in, hhi, hlo);
+      }
+      __syncthreads();
+      if (mine) {
+        const int s0 = (kc + 3) % 3;
+        if (!col1) {
+          p[o] = __fadd_rn(p0, dps[s0][ty + 1][tx + 1]);
+        } else {
+          const float nlo[3] = {dps[s0][ty + 1][tx], dps[s0][ty][tx + 1], dps[(kc + 2) % 3][ty + 1][tx + 1]};
+          const float nhi[3] = {dps[s0][ty + 1][tx + 2], dps[s0][ty + 2][tx + 1], dps[(kc + 4) % 3][ty + 1][tx + 1]};
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            flo[a] = move_hi(C, a, nlo[a], flo[a]);
+            fhi[a] = move_lo(C, a, nhi[a], fhi[a]);
+          }
+          const float dp = cell_dp(C, C.beta_in, fhi, flo);
+          p[o] = __fadd_rn(p0, dp);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            D[a][o] = move_hi(C, a, dp, fhi[a]);
+            D[a][o - st[a]] = move_lo(C, a, dp, flo[a]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    return;
+  }
+  for (int k = k0 - 1; k <= k1; ++k) {
+    // this thread's cell of plane k - 1: its pressure (and a colour-1 cell's
+    // faces) are loaded before the colour-0 pass below, so that both sets of
+    // loads are in flight together
+    const int kc = k - 1, j = j0 + ty;
+    const int tx = 2 * m2 + ((i0 + j + kc + (col1 ? 1 : 0)) & 1);
+    const int i = i0 + tx;
+    const bool mine = kc >= k0 && kc < k1 && i < C.n[0] && j < C.n[1];
+    long long o = 0;
+    CellFaces cf{};
+    float fhi[3] = {0.f, 0.f, 0.f}, flo[3] = {0.f, 0.f, 0.f}, p0 = 0.f;
+    if (mine) {
+      const int c3[3] = {i, j, kc};
+      o = cidx(C, i, j, kc);
+      cf = cell_faces(C, c3, o);
+      p0 = p[o];
+      if (col1) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          fhi[a] = __ldg(S[a] + o);
+          flo[a] = __ldg(S[a] + cf.lo[a]);
+        }
+      }
+    }
+    // colour-0 dp of plane k over the box and its halo
+    const int slot = (k + 3) % 3;
+    if (t < HALF * (RB_TY + 2)) {
+      const int r = t / HALF;
+      const int jh = j0 + r - 1;
+      const int x = 2 * (t % HALF) + ((i0 - 1 + jh + k) & 1);  // i + j + k even
+      int c3[3] = {i0 - 1 + x, jh, k};
+      if (wrap_cell(C, 0, c3[0]) && wrap_cell(C, 1, c3[1]) && wrap_cell(C, 2, c3[2])) {
+        const long long oh = cidx(C, c3[0], c3[1], c3[2]);
+        const CellFaces ch = cell_faces(C, c3, oh);
+        float hhi[3], hlo[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          hhi[a] = __ldg(S[a] + oh);
+          hlo[a] = __ldg(S[a] + ch.lo[a]);
+        }
+        dps[slot][r][x] = cell_dp(C, ch.beta, hhi, hlo);
+      }
+    }
+    __syncthreads();
+    // plane k - 1 of the box: colour 1 updates and writes its faces, colour 0
+    // its pressure and wall faces
+    if (mine) {
+      const int s0 = (kc + 3) % 3;
+      if (!col1) {
+        p[o] = __fadd_rn(p0, dps[s0][ty + 1][tx + 1]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (!cf.mhi[a]) D[a][o] = __ldg(S[a] + o);
+          if (!cf.mlo[a]) D[a][cf.lo[a]] = __ldg(S[a] + cf.lo[a]);
+        }
+      } else {
+        // the colour-0 neighbours' dp, low and high along each axis (read
+        // only where that neighbour exists)
+        const float nlo[3] = {dps[s0][ty + 1][tx], dps[s0][ty][tx + 1], dps[(kc + 2) % 3][ty + 1][tx + 1]};
+        const float nhi[3] = {dps[s0][ty + 1][tx + 2], dps[s0][ty + 2][tx + 1], dps[(kc + 4) % 3][ty + 1][tx + 1]};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          // the neighbour across the low face moved it as its high face, and conversely
+          if (cf.mlo[a]) flo[a] = move_hi(C, a, nlo[a], flo[a]);
+          if (cf.mhi[a]) fhi[a] = move_lo(C, a, nhi[a], fhi[a]);
+        }
+        const float dp = cell_dp(C, cf.beta, fhi, flo);
+        p[o] = __fadd_rn(p0, dp);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          D[a][o] = cf.mhi[a] ? move_hi(C, a, dp, fhi[a]) : fhi[a];
+          D[a][cf.lo[a]] = cf.mlo[a] ? move_lo(C, a, dp, flo[a]) : flo[a];
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -224,6 +441,9 @@ bool make_cfd(const bssn_cfd_t* d, Cfd* C) {
   C->omega = (float)d->omega;
   C->alpha = (float)d->alpha;
   C->lid = (float)d->lid;
+  float s = 0.f;
+  for (int a = 0; a < 3; ++a) s = (s + C->ih2[a]) + C->ih2[a];
+  C->beta_in = C->omega / (C->dt * s);
   return true;
 }
 
@@ -277,6 +497,20 @@ bssn_status_t bssn_cfd_mass(const bssn_cfd_t* desc, int colour, float* u, float*
   return cudaGetLastError() == cudaSuccess ? BSSN_OK : BSSN_ERR_CUDA;
 }
 
+bssn_status_t bssn_cfd_mass_iteration(const bssn_cfd_t* desc, const float* u, const float* v, const float* w,
+                                      float* un, float* vn, float* wn, float* p, void* stream) {
+  Cfd C;
+  if (!make_cfd(desc, &C) || !a16(u) || !a16(v) || !a16(w) || !a16(un) || !a16(vn) || !a16(wn) || !a16(p))
+    return BSSN_ERR_INVALID_ARG;
+  const void* q[7] = {u, v, w, un, vn, wn, p};
+  for (int x = 0; x < 7; ++x)
+    for (int y = x + 1; y < 7; ++y)
+      if (q[x] == q[y]) return BSSN_ERR_INVALID_ARG;
+  const dim3 rb((C.n[0] + RB_TX - 1) / RB_TX, (C.n[1] + RB_TY - 1) / RB_TY, (C.n[2] + RB_KC - 1) / RB_KC);
+  k_cfd_mass_rb<<<rb, RB_TX * RB_TY, 0, (cudaStream_t)stream>>>(C, u, v, w, un, vn, wn, p);
+  return cudaGetLastError() == cudaSuccess ? BSSN_OK : BSSN_ERR_CUDA;
+}
+
 bssn_status_t bssn_cfd_step(const bssn_cfd_t* desc, int iterations, float* u, float* v, float* w, float* p,
                             float* scratch, void* stream) {
   Cfd C;
@@ -290,23 +524,36 @@ bssn_status_t bssn_cfd_step(const bssn_cfd_t* desc, int iterations, float* u, fl
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = boundary_all(C, u, v, w, p, s);
   const long long n = (long long)C.n[0] * C.n[1] * C.n[2];
-  // the velocity kernel writes every interior entry of un, vn, wn; their
-  // ghosts are copied back unset and rewritten by the boundary kernel
+  // The velocity kernel writes every interior entry of un, vn, wn; the
+  // boundary kernel then sets their ghosts, among them the low wall faces
+  // (-1) that the mass iterations read. The iterations alternate between the
+  // two sets of arrays and write every entry they read, so the boundary runs
+  // again only after the last one: the ghosts depend on the interior alone,
+  // and the state equals boundary after every iteration bit for bit.
   if (e == cudaSuccess) {
     k_cfd_velocity<<<grid_for(n), CFD_THREADS, 0, s>>>(C, u, v, w, p, un, vn, wn);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(u, un, sizeof(float) * np, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(v, vn, sizeof(float) * np, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(w, wn, sizeof(float) * np, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = boundary_all(C, u, v, w, p, s);
-  const long long nh = (long long)((C.n[0] + 1) / 2) * C.n[1] * C.n[2];
+  if (e == cudaSuccess) e = boundary_all(C, un, vn, wn, p, s);
+  float* A[3] = {un, vn, wn};
+  float* Bv[3] = {u, v, w};
+  const dim3 rb((C.n[0] + RB_TX - 1) / RB_TX, (C.n[1] + RB_TY - 1) / RB_TY, (C.n[2] + RB_KC - 1) / RB_KC);
   for (int it = 0; it < iterations && e == cudaSuccess; ++it) {
-    k_cfd_mass<<<grid_for(nh), CFD_THREADS, 0, s>>>(C, 0, u, v, w, p);
-    k_cfd_mass<<<grid_for(nh), CFD_THREADS, 0, s>>>(C, 1, u, v, w, p);
+    k_cfd_mass_rb<<<rb, RB_TX * RB_TY, 0, s>>>(C, A[0], A[1], A[2], Bv[0], Bv[1], Bv[2], p);
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = boundary_all(C, u, v, w, p, s);
+    for (int a = 0; a < 3; ++a) {
+      float* t = A[a];
+      A[a] = Bv[a];
+      Bv[a] = t;
+    }
   }
+  // the current faces are in A: an even iteration count leaves them in the scratch
+  if (A[0] != u) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(u, un, sizeof(float) * np, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(v, vn, sizeof(float) * np, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w, wn, sizeof(float) * np, cudaMemcpyDeviceToDevice, s);
+  }
+  if (e == cudaSuccess) e = boundary_all(C, u, v, w, p, s);
   return e == cudaSuccess ? BSSN_OK : BSSN_ERR_CUDA;
 }
 

@@ -267,6 +267,15 @@ def test_cfd_rejects_invalid_arguments(L):
     with pytest.raises(B.BssnError) as e:
         B.cfd_step(ok, 4, FAKE, FAKE * 2, FAKE * 3, FAKE * 4, FAKE + 4, stream=0)  # misaligned scratch
     assert e.value.status == B.ERR_INVALID_ARG
+    for args in ((FAKE, FAKE * 2, FAKE * 3, FAKE, FAKE * 5, FAKE * 6, FAKE * 7),   # un is u
+                 (FAKE, FAKE * 2, FAKE * 3, FAKE * 4, FAKE * 5, FAKE * 6, FAKE * 6),  # p is wn
+                 (FAKE, FAKE * 2, FAKE * 3, FAKE * 4, FAKE * 5, FAKE * 6, FAKE + 8)):  # misaligned p
+        with pytest.raises(B.BssnError) as e:
+            B.cfd_mass_iteration(ok, *args, stream=0)
+        assert e.value.status == B.ERR_INVALID_ARG
+    with pytest.raises(B.BssnError) as e:
+        B.cfd_mass_iteration(bad[0], FAKE, FAKE * 2, FAKE * 3, FAKE * 4, FAKE * 5, FAKE * 6, FAKE * 7, stream=0)
+    assert e.value.status == B.ERR_INVALID_ARG
     assert B.last_error() == B.OK
 
 

@@ -149,3 +149,73 @@ def test_lid_cavity_full_size_sampled():
     kk, jj, ii = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
     red = (ii + jj + kk) % 2 == 0
     assert np.max(np.abs(D1[red] - (1 - 1.7) * D0[red])) < 1e-3 * np.max(np.abs(D0))
+
+
+STEP_CASES = CASES + [
+    ((2, 6, 4), (0.1, 0.1, 0.1), (True, False, True), dict(nu=0.02, dt=0.002, alpha=0.5)),   # two cells on a periodic axis
+    ((37, 13, 19), (0.05, 0.07, 0.06), (False, False, False), dict(nu=0.01, dt=0.002, lid=1.0)),  # ragged boxes
+    ((34, 18, 36), (0.05, 0.05, 0.05), (True, True, True), dict(nu=0.01, dt=0.002)),           # every axis periodic
+    # large enough for boxes away from every wall and seam (the kernel's short path)
+    ((70, 14, 38), (0.03, 0.04, 0.05), (False, False, False), dict(nu=0.01, dt=0.001, lid=1.0)),
+    ((68, 12, 36), (0.03, 0.04, 0.05), (True, False, True), dict(nu=0.01, dt=0.001, alpha=0.2)),
+]
+
+
+@pytest.mark.parametrize("case", range(len(STEP_CASES)))
+@pytest.mark.parametrize("iterations", [0, 1, 3, 4])
+def test_step_equals_its_kernels(case, iterations):
+    """bssn_cfd_step runs each mass iteration as one fused pass (colour-0
+    moves applied on the fly, faces into the other set of arrays) and the
+    boundary once at the end. It must equal, bit for bit, the kernels it
+    stands for: boundary, velocity, boundary, then per iteration the
+    colour-0 and colour-1 half-sweeps and the boundary."""
+    torch = need_gpu()
+    n, h, per, kw = STEP_CASES[case]
+    F = _flow(n, h, per, np.float32, **kw)
+    d = _desc(F)
+    init = _fields(n, 300 + 10 * case, amp=0.3)
+    a = _to_dev(torch, init)
+    b = _to_dev(torch, init)
+    npts = B.cfd_points(d)
+    scratch = torch.full((3 * ((npts + 3) // 4 * 4),), float("nan"), dtype=torch.float32, device="cuda")
+    B.cfd_step(d, iterations, *a, scratch)
+    u, v, w, p = b
+    B.cfd_boundary(d, u, v, w, p)
+    un, vn, wn = (torch.full_like(x, float("nan")) for x in (u, v, w))
+    B.cfd_velocity(d, u, v, w, p, un, vn, wn)
+    u.copy_(un)
+    v.copy_(vn)
+    w.copy_(wn)
+    B.cfd_boundary(d, u, v, w, p)
+    for _ in range(iterations):
+        B.cfd_mass(d, 0, u, v, w, p)
+        B.cfd_mass(d, 1, u, v, w, p)
+        B.cfd_boundary(d, u, v, w, p)
+    torch.cuda.synchronize()
+    for name, x, y in zip("uvwp", a, b):
+        assert torch.equal(x, y), (name, float(torch.max(torch.abs(x - y))))
+
+
+@pytest.mark.parametrize("case", range(len(STEP_CASES)))
+def test_mass_iteration_equals_two_half_sweeps(case):
+    """bssn_cfd_mass_iteration (one pass, faces into a second set of arrays)
+    against bssn_cfd_mass with colour 0 then colour 1 in place: the written
+    entries (interior and low wall faces) and p, bit for bit."""
+    torch = need_gpu()
+    n, h, per, kw = STEP_CASES[case]
+    d = _desc(_flow(n, h, per, np.float32, **kw))
+    a = _to_dev(torch, _fields(n, 400 + 10 * case, amp=0.3))
+    B.cfd_boundary(d, *a)
+    b = [x.clone() for x in a]
+    un, vn, wn = (torch.full_like(x, float("nan")) for x in a[:3])
+    B.cfd_mass_iteration(d, a[0], a[1], a[2], un, vn, wn, a[3])
+    B.cfd_mass(d, 0, *b)
+    B.cfd_mass(d, 1, *b)
+    torch.cuda.synchronize()
+    assert torch.equal(a[3], b[3])
+    for ax, (got, want) in enumerate(zip((un, vn, wn), b[:3])):
+        assert torch.equal(got[1:-1, 1:-1, 1:-1], want[1:-1, 1:-1, 1:-1]), "uvw"[ax]
+        if not per[ax]:  # the low wall face (-1) sits in the ghost layer of its own axis
+            lo = [slice(1, -1)] * 3
+            lo[2 - ax] = 0
+            assert torch.equal(got[tuple(lo)], want[tuple(lo)]), "uvw"[ax]

@@ -91,6 +91,59 @@ def test_fp32_steps_vs_oracle(order):
     assert np.max(err) < FP32_STEP_TOL, dict(zip(inputs.VARS, err))
 
 
+# alpha, beta^i, B^i
+_LAPSE = [17]
+_SHIFT = list(range(18, 24))
+
+
+@pytest.mark.parametrize("order", [4, 8])
+@pytest.mark.parametrize("gauge", [dict(lapse=0, shift=0, advect_gauge=1), dict(lapse=1, shift=0, advect_gauge=0),
+                                   dict(lapse=2, shift=1, advect_gauge=1), dict(lapse=0, shift=1, advect_gauge=0)])
+def test_fp32_gauge_switches(order, gauge):
+    """The FP32 form carries each variable's advection beside its dissipation
+    and weights it as the gauge's right-hand side takes it: advected lapse
+    and shift only with advect_gauge, nothing for a frozen lapse or shift.
+    Each gauge choice against the oracle: the right-hand side alone (frozen
+    variables exactly zero) and the fused stage with dissipation (frozen
+    variables: the dissipation alone, against the operator's norm bound)."""
+    torch = need_gpu()
+    g = order // 2 + 1
+    h = 0.12
+    u = smooth_bl(15, 12, 10, g, h, seed=80 + order + 5 * gauge["lapse"] + gauge["advect_gauge"])
+    eps = 0.07
+    p = B.make_params(fd_order=order, ko_eps=eps, eta=1.7, shift_coeff=0.7, **gauge)
+    frozen = (_LAPSE if gauge["lapse"] == 2 else []) + (_SHIFT if gauge["shift"] == 1 else [])
+    live = [v for v in range(24) if v not in frozen]
+    grid = grid_for(u, g, h)
+    d = B.upload(u, grid)
+    work = B.alloc_work(grid, p, B.FP32_RHS)
+    out = B.alloc_state(grid)
+    B.rhs(grid, p, B.FP32_RHS, d, out, work)
+    acc = B.alloc_state(grid)
+    ynext = B.alloc_state(grid)
+    dt = 0.25 * h
+    B.rk4_stage(grid, p, B.FP32_RHS, 0, dt, d, d, acc, ynext, work)
+    torch.cuda.synchronize()
+
+    got = B.download(out, grid)
+    want = oracle.rhs(u, g, h, oracle_params(p), ko=False)
+    err = rel_err_tensor(got, want, g)
+    assert np.max(err[live]) < FP32_RHS_TOL, dict(zip(inputs.VARS, err))
+    for v in frozen:
+        assert np.all(interior(got, g)[v] == 0.0), inputs.VARS[v]
+
+    k = B.download(acc, grid) / (dt / 6)
+    want_k = oracle.rhs(u, g, h, oracle_params(p), ko=True)
+    err = rel_err_tensor(k, want_k, g)
+    assert np.max(err[live]) < FP32_RHS_TOL, dict(zip(inputs.VARS, err))
+    if frozen:
+        scale = eps * 3 / h * np.max(np.abs(u[frozen].reshape(len(frozen), -1)), axis=1)
+        gi = interior(k, g)[frozen].reshape(len(frozen), -1)
+        wi = interior(want_k, g)[frozen].reshape(len(frozen), -1)
+        assert np.max(np.abs(wi), axis=1).min() > 0  # the dissipation is really there
+        assert np.max(np.max(np.abs(gi - wi), axis=1) / scale) < 1e-5
+
+
 def test_fp32_stage_split_matches_fused_call():
     """bssn_diff_tables + bssn_rk4_stage_fused == bssn_rk4_stage, both forms."""
     torch = need_gpu()
