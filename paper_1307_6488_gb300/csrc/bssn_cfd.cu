@@ -88,18 +88,22 @@ __device__ __forceinline__ float velocity_face(const Cfd& C, const float* const*
   return fc + C.dt * (grad + C.g[c] - flux + C.nu * vis);
 }
 
-__global__ void __launch_bounds__(CFD_THREADS) k_cfd_velocity(Cfd C, const float* __restrict__ u,
+// Each block takes a column of VEL_X x VEL_Y cells over VEL_Z planes, one
+// thread per (i, j) marching in z, so that the neighbouring planes a cell
+// reads are still in L1 from the plane before; no index division.
+constexpr int VEL_X = 32, VEL_Y = 8, VEL_Z = 8;
+
+__global__ void __launch_bounds__(VEL_X * VEL_Y) k_cfd_velocity(Cfd C, const float* __restrict__ u,
                                                               const float* __restrict__ v,
                                                               const float* __restrict__ w,
                                                               const float* __restrict__ p, float* __restrict__ un,
                                                               float* __restrict__ vn, float* __restrict__ wn) {
-  const long long total = (long long)C.n[0] * C.n[1] * C.n[2];
   const float* f[3] = {u, v, w};
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % C.n[0]);
-    const long long r = t / C.n[0];
-    const int j = (int)(r % C.n[1]), k = (int)(r / C.n[1]);
+  const int i = (int)blockIdx.x * VEL_X + (int)threadIdx.x % VEL_X;
+  const int j = (int)blockIdx.y * VEL_Y + (int)threadIdx.x / VEL_X;
+  if (i >= C.n[0] || j >= C.n[1]) return;
+  const int kb = (int)blockIdx.z * VEL_Z, ke = min(kb + VEL_Z, C.n[2]);
+  for (int k = kb; k < ke; ++k) {
     const long long o = cidx(C, i, j, k);
     // every interior entry is written: the wall faces n-1 of a wall axis keep
     // their value, all other faces are advanced
@@ -452,6 +456,10 @@ unsigned int grid_for(long long n) {
   return (unsigned int)(b < 1 ? 1 : (b > (1 << 20) ? (1 << 20) : b));
 }
 
+dim3 velocity_grid(const Cfd& C) {
+  return dim3((C.n[0] + VEL_X - 1) / VEL_X, (C.n[1] + VEL_Y - 1) / VEL_Y, (C.n[2] + VEL_Z - 1) / VEL_Z);
+}
+
 cudaError_t boundary_all(const Cfd& C, float* u, float* v, float* w, float* p, cudaStream_t s) {
   for (int a = 0; a < 3; ++a) {
     const long long n = 2LL * (C.n[(a + 1) % 3] + 2) * (C.n[(a + 2) % 3] + 2);
@@ -482,8 +490,7 @@ bssn_status_t bssn_cfd_velocity(const bssn_cfd_t* desc, const float* u, const fl
   if (!make_cfd(desc, &C) || !a16(u) || !a16(v) || !a16(w) || !a16(p) || !a16(un) || !a16(vn) || !a16(wn))
     return BSSN_ERR_INVALID_ARG;
   if (un == u || vn == v || wn == w || un == vn || un == wn || vn == wn) return BSSN_ERR_INVALID_ARG;
-  const long long n = (long long)C.n[0] * C.n[1] * C.n[2];
-  k_cfd_velocity<<<grid_for(n), CFD_THREADS, 0, (cudaStream_t)stream>>>(C, u, v, w, p, un, vn, wn);
+  k_cfd_velocity<<<velocity_grid(C), VEL_X * VEL_Y, 0, (cudaStream_t)stream>>>(C, u, v, w, p, un, vn, wn);
   return cudaGetLastError() == cudaSuccess ? BSSN_OK : BSSN_ERR_CUDA;
 }
 
@@ -523,7 +530,6 @@ bssn_status_t bssn_cfd_step(const bssn_cfd_t* desc, int iterations, float* u, fl
   float* wn = scratch + 2 * stride;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = boundary_all(C, u, v, w, p, s);
-  const long long n = (long long)C.n[0] * C.n[1] * C.n[2];
   // The velocity kernel writes every interior entry of un, vn, wn; the
   // boundary kernel then sets their ghosts, among them the low wall faces
   // (-1) that the mass iterations read. The iterations alternate between the
@@ -531,7 +537,7 @@ bssn_status_t bssn_cfd_step(const bssn_cfd_t* desc, int iterations, float* u, fl
   // again only after the last one: the ghosts depend on the interior alone,
   // and the state equals boundary after every iteration bit for bit.
   if (e == cudaSuccess) {
-    k_cfd_velocity<<<grid_for(n), CFD_THREADS, 0, s>>>(C, u, v, w, p, un, vn, wn);
+    k_cfd_velocity<<<velocity_grid(C), VEL_X * VEL_Y, 0, s>>>(C, u, v, w, p, un, vn, wn);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = boundary_all(C, un, vn, wn, p, s);
