@@ -1,0 +1,190 @@
+"""A second, independent transcription of the BSSN right-hand side, fed with
+exact derivatives, as a pin for the oracle's finite-difference one (not GPU).
+
+The paper cites the BSSN system (Sec. 1.1) without writing it out. The
+exact-solution pins elsewhere (flat space, Kasner, gauge wave, Kerr-Schild,
+Schwarzschild, York data) each leave some terms at zero: homogeneous data
+has no spatial derivatives, stationary data is tested with its own frozen
+gauge. Here every one of the 24 variables is a generic smooth analytic
+field (sums of sines with seeded wave vectors and phases, the conformal
+metric a perturbation of the identity), so every term of every equation is
+alive. Their first and second derivatives are taken exactly by sympy; the
+right-hand side is then assembled from those values by a plain numpy
+transcription written with full 3x3 tensors and einsum (inverse metric by
+numpy.linalg.inv), sharing nothing with the oracle's packed, point-by-point
+C++. The oracle's right-hand side at a grid point must converge to it at
+the stencil order (4 or 8) as the spacing halves; a wrong sign, index or
+dropped term in either transcription leaves an h-independent difference and
+stops the convergence.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+sp = pytest.importorskip("sympy")
+
+NV = 24
+W_, GT, K_, AT, GAM, AL, BE, BB = 0, 1, 7, 8, 14, 17, 18, 21
+PAIRS = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+X = sp.symbols("x y z", real=True)
+
+
+def fields(seed):
+    """24 smooth analytic fields: base value + two seeded sine waves each."""
+    rng = np.random.default_rng(seed)
+    base = np.zeros(NV)
+    base[W_] = 1.0
+    base[AL] = 1.0
+    base[K_] = 0.1
+    for s, (i, j) in enumerate(PAIRS):
+        base[GT + s] = 1.0 if i == j else 0.0
+    amp = np.full(NV, 0.08)
+    amp[GT:GT + 6] = 0.05
+    exprs = []
+    for v in range(NV):
+        e = sp.Float(base[v])
+        for _ in range(2):
+            k = rng.uniform(-1.6, 1.6, 3)
+            ph = rng.uniform(0, 2 * np.pi)
+            a = amp[v] * rng.uniform(0.5, 1.0)
+            e = e + sp.Float(a) * sp.sin(sum(sp.Float(k[d]) * X[d] for d in range(3)) + sp.Float(ph))
+        exprs.append(e)
+    return exprs
+
+
+def exact_derivatives(exprs, pt):
+    """Values, first and second derivatives of every field at pt."""
+    val = np.zeros(NV)
+    d1 = np.zeros((NV, 3))
+    d2 = np.zeros((NV, 3, 3))
+    sub = dict(zip(X, pt))
+    for v, e in enumerate(exprs):
+        val[v] = float(e.evalf(subs=sub))
+        for a in range(3):
+            da = sp.diff(e, X[a])
+            d1[v, a] = float(da.evalf(subs=sub))
+            for b in range(a, 3):
+                d2[v, a, b] = d2[v, b, a] = float(sp.diff(da, X[b]).evalf(subs=sub))
+    return val, d1, d2
+
+
+def sym33(vec6):
+    m = np.zeros(vec6.shape[1:] + (3, 3)) if vec6.ndim > 1 else np.zeros((3, 3))
+    for s, (i, j) in enumerate(PAIRS):
+        m[..., i, j] = m[..., j, i] = vec6[s]
+    return m
+
+
+def rhs_transcribed(val, d1, d2, lapse, shift, shift_coeff, eta, advect_gauge):
+    """The BSSN right-hand side (W form, vacuum) from exact point values.
+    Conventions: dX[k, ...] = d_k X; ddX[k, l, ...] = d_k d_l X."""
+    W, K, al = val[W_], val[K_], val[AL]
+    gt = sym33(val[GT:GT + 6])
+    At = sym33(val[AT:AT + 6])
+    beta, B = val[BE:BE + 3], val[BB:BB + 3]
+    dW, dK, dal = d1[W_], d1[K_], d1[AL]
+    dgt = np.stack([sym33(d1[GT:GT + 6, k]) for k in range(3)])            # [k, i, j]
+    ddgt = np.array([[sym33(d2[GT:GT + 6, k, l]) for l in range(3)] for k in range(3)])  # [k, l, i, j]
+    dGam = d1[GAM:GAM + 3].T                                                # [k, i] = d_k Gt^i
+    dbeta = d1[BE:BE + 3].T                                                 # [k, i] = d_k beta^i
+    ddbeta = np.moveaxis(d2[BE:BE + 3], 0, -1)                              # [k, l, i]
+    ddW, ddal = d2[W_], d2[AL]
+    adv = d1 @ beta                                                         # beta^k d_k u, every variable
+
+    gu = np.linalg.inv(gt)
+    Gl = 0.5 * (np.einsum("ikj->kij", dgt) + np.einsum("jki->kij", dgt) - dgt)  # Gt_{k ij}
+    Gu = np.einsum("kl,lij->kij", gu, Gl)                                   # Gt^k_ij
+    Gd = np.einsum("ij,kij->k", gu, Gu)
+    # conformal Ricci tensor
+    R = -0.5 * np.einsum("lm,lmij->ij", gu, ddgt)
+    R += 0.5 * (np.einsum("ki,jk->ij", gt, dGam) + np.einsum("kj,ik->ij", gt, dGam))
+    R += 0.5 * np.einsum("k,ijk->ij", Gd, Gl + np.einsum("jik->ijk", Gl))
+    R += np.einsum("lm,kli,jkm->ij", gu, Gu, Gl)
+    R += np.einsum("lm,klj,ikm->ij", gu, Gu, Gl)
+    R += np.einsum("lm,kim,klj->ij", gu, Gu, Gl)
+    # conformal-factor part
+    DDW = ddW - np.einsum("kij,k->ij", Gu, dW)
+    R += (DDW + gt * np.einsum("kl,kl", gu, DDW)) / W - 2 * gt * np.einsum("kl,k,l", gu, dW, dW) / W ** 2
+    # second covariant derivative of the lapse
+    DDa = ddal - np.einsum("kij,k->ij", Gu, dal)
+    DDa += (np.outer(dW, dal) + np.outer(dal, dW) - gt * np.einsum("kl,k,l", gu, dW, dal)) / W
+    D2a = W ** 2 * np.einsum("ij,ij", gu, DDa)
+    Am = gu @ At                                                            # At^i_j
+    Au = gu @ At @ gu                                                       # At^ij
+    divb = np.trace(dbeta)
+    out = np.zeros(NV)
+    out[W_] = adv[W_] + W * (al * K - divb) / 3
+    dgt_t = -2 * al * At + np.einsum("ik,jk->ij", gt, dbeta) + np.einsum("jk,ik->ij", gt, dbeta) - 2 / 3 * gt * divb
+    out[K_] = adv[K_] - D2a + al * (np.einsum("ij,ij", At, Au) + K ** 2 / 3)
+    X_ = -DDa + al * R
+    XTF = X_ - gt * np.einsum("kl,kl", gu, X_) / 3
+    dAt_t = (W ** 2 * XTF + al * (K * At - 2 * At @ Am) + np.einsum("ik,jk->ij", At, dbeta)
+             + np.einsum("jk,ik->ij", At, dbeta) - 2 / 3 * At * divb)
+    for s, (i, j) in enumerate(PAIRS):
+        out[GT + s] = adv[GT + s] + dgt_t[i, j]
+        out[AT + s] = adv[AT + s] + dAt_t[i, j]
+    gam_na = (-np.einsum("j,ji->i", Gd, dbeta) + 2 / 3 * Gd * divb + np.einsum("jk,jki->i", gu, ddbeta)
+              + gu @ np.einsum("jkk->j", ddbeta) / 3 - 2 * Au @ dal
+              + 2 * al * (np.einsum("ijk,jk->i", Gu, Au) - 3 / W * Au @ dW - 2 / 3 * gu @ dK))
+    out[GAM:GAM + 3] = adv[GAM:GAM + 3] + gam_na
+    ag = 1.0 if advect_gauge else 0.0
+    if lapse == 0:
+        out[AL] = ag * adv[AL] - 2 * al * K
+    elif lapse == 1:
+        out[AL] = ag * adv[AL] - al * al * K
+    if shift == 0:
+        out[BE:BE + 3] = ag * adv[BE:BE + 3] + shift_coeff * B
+        out[BB:BB + 3] = ag * adv[BB:BB + 3] + gam_na - eta * B
+    return out
+
+
+def oracle_at(exprs, pt, h, order, p):
+    """The oracle's right-hand side at pt: one interior point, its ghosts
+    filled with the exact fields."""
+    g = oracle.required_ghost(order)
+    off = (np.arange(2 * g + 1) - g) * h
+    zz, yy, xx = np.meshgrid(pt[2] + off, pt[1] + off, pt[0] + off, indexing="ij")
+    u = np.zeros((NV,) + xx.shape)
+    for v, e in enumerate(exprs):
+        f = sp.lambdify(X, e, "numpy")
+        u[v] = np.broadcast_to(f(xx, yy, zz), xx.shape)
+    return oracle.rhs(np.ascontiguousarray(u), g, h, p)[:, g, g, g]
+
+
+GAUGES = [dict(lapse=0, shift=0, advect_gauge=1), dict(lapse=1, shift=0, advect_gauge=0)]
+
+
+@pytest.mark.parametrize("order,hs", [(4, (0.08, 0.04, 0.02)), (8, (0.3, 0.15, 0.075))])
+@pytest.mark.parametrize("gauge", GAUGES)
+@pytest.mark.parametrize("seed", [11, 29])
+def test_rhs_converges_to_second_transcription(order, hs, gauge, seed):
+    exprs = fields(seed)
+    pt = np.random.default_rng(seed + 1).uniform(-1, 1, 3)
+    pars = dict(shift_coeff=0.75, eta=1.7, **gauge)
+    val, d1, d2 = exact_derivatives(exprs, pt)
+    want = rhs_transcribed(val, d1, d2, **pars)
+    p = oracle.Params(fd_order=order, ko_eps=0.0, **pars)
+    scale = np.max(np.abs(want))
+    errs = [np.max(np.abs(oracle_at(exprs, pt, h, order, p) - want)) / scale for h in hs]
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    # every variable is alive: a dropped term would show at O(1)
+    assert np.min(np.abs(want)) > 1e-4 * scale
+    assert errs[-1] < (1e-5 if order == 4 else 1e-7), errs
+    assert order - 0.6 < rates[-1] < order + 1.5, (errs, rates)
+
+
+def test_transcription_sees_each_term():
+    """The comparison is sensitive: perturbing the oracle's input by a
+    planted mistake of the size of one term (the sign of the shift's
+    B-coupling, eta) moves the right-hand side far outside the FD error."""
+    exprs = fields(11)
+    pt = np.array([0.3, -0.2, 0.5])
+    val, d1, d2 = exact_derivatives(exprs, pt)
+    good = rhs_transcribed(val, d1, d2, 0, 0, 0.75, 1.7, 1)
+    bad = rhs_transcribed(val, d1, d2, 0, 0, 0.75, -1.7, 1)
+    p = oracle.Params(fd_order=8, ko_eps=0.0, lapse=0, shift=0, shift_coeff=0.75, eta=1.7, advect_gauge=1)
+    got = oracle_at(exprs, pt, 0.05, 8, p)
+    scale = np.max(np.abs(good))
+    assert np.max(np.abs(got - good)) / scale < 1e-7
+    assert np.max(np.abs(got - bad)) / scale > 1e-3
