@@ -326,7 +326,8 @@ def run_gpu(args):
         ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
         stage_ms = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(len(ev) // 2)]
         l2, mx, st = B.constraints(grid, p, state, work)
-        return dict(state=state, ms=ms, stage_ms=float(np.mean(stage_ms)), launches=launches[0], l2=l2,
+        alg, _, _ = B.algebraic_constraints(grid, p, state, work)
+        return dict(state=state, ms=ms, stage_ms=float(np.mean(stage_ms)), launches=launches[0], l2=l2, alg=alg,
                     clocks=clk.summary() if clk else None)
 
     def run_batched(prec):
@@ -1017,6 +1018,7 @@ def run_gpu(args):
         "gpu_launches": f64["launches"],
         "clocks": f64["clocks"],
         "accuracy": {"fp64_ham_l2_after": float(f64["l2"][0]), "fp64_mom_l2_after": float(max(f64["l2"][1:4])),
+                     "fp64_det_gt_minus_1_l2_after": float(f64["alg"][0]), "fp64_trace_At_l2_after": float(f64["alg"][1]),
                      "parity": "FP64 RHS within 1e-12 per-variable relative of the CPU oracle (tests)"},
         "forms": {
             "fp32_rhs": {"value": world * pts * args.steps / (f32["ms"] * 1e-3), "unit": UNIT,
@@ -1033,7 +1035,8 @@ def run_gpu(args):
                                  if TRAFFIC_F32["src_sha"] == sha and n == N else None},
                          "err_vs_fp64_max_rel_per_tensor": float(np.max(err32)),
                          "err_vs_fp64_per_var": [float(x) for x in err32],
-                         "ham_l2_after": float(f32["l2"][0]), "gpu_launches": f32["launches"],
+                         "ham_l2_after": float(f32["l2"][0]), "det_gt_minus_1_l2_after": float(f32["alg"][0]),
+                         "trace_At_l2_after": float(f32["alg"][1]), "gpu_launches": f32["launches"],
                          "steps": args.steps + args.warmup},
             **batched,
         },

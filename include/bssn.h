@@ -511,6 +511,20 @@ bssn_status_t bssn_constraints(const bssn_grid_t* grid, const bssn_params_t* par
                                double* ham, double* mom, double* gcon, double* out_l2, double* out_max,
                                void* work, unsigned long long work_bytes, void* stream);
 
+/* Algebraic constraints of the conformal decomposition, FP64, at interior
+ * points of `state` (DEVICE; ghosts not needed): det(gt_ij) - 1 and the
+ * trace gt^ij At_ij. Exact data has both zero; the evolution does not
+ * enforce them (the paper cites BSSN without stating whether it does), so
+ * they are reported as diagnostics. out_l2, out_max: HOST double[2], the
+ * root-mean-square and maximum modulus over interior points, in the order
+ * det - 1, trace. work: as for bssn_constraints (>= bssn_work_bytes() for
+ * these params; only its reduction area is used). Synchronizes `stream`.
+ * Returns BSSN_ERR_NONFINITE (after filling the outputs) if any value is
+ * NaN/Inf. */
+bssn_status_t bssn_algebraic_constraints(const bssn_grid_t* grid, const bssn_params_t* params, const double* state,
+                                         double* out_l2, double* out_max, void* work, unsigned long long work_bytes,
+                                         void* stream);
+
 /* Gravitational-wave extraction beside the evolution (the WeylScal4 kernel
  * the paper runs on the GPU, Sec. 3.3), FP64, at interior points of `state`
  * (DEVICE, ghosts filled): from the BSSN variables

@@ -156,6 +156,28 @@ def rhs_points(u, g, h, p: Params, lin, ko=False):
     return out
 
 
+def algebraic_constraints(u, g):
+    """The algebraic constraints of the conformal decomposition at interior
+    points (the BSSN variables of Sec. 1.1 satisfy det(gt_ij) = 1 and
+    gt^ij At_ij = 0 for exact data): returns (det(gt) - 1, gt^ij At_ij),
+    each (nz, ny, nx). The determinant is the cofactor expansion along the
+    first row written out; the trace contracts At with numpy's inverse of
+    gt."""
+    _check_state(u, g)
+    ui = u[:, g:-g, g:-g, g:-g]
+    pairs = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    G = np.zeros(ui.shape[1:] + (3, 3))
+    A = np.zeros(ui.shape[1:] + (3, 3))
+    for s, (i, j) in enumerate(pairs):
+        G[..., i, j] = G[..., j, i] = ui[1 + s]
+        A[..., i, j] = A[..., j, i] = ui[8 + s]
+    det = (G[..., 0, 0] * (G[..., 1, 1] * G[..., 2, 2] - G[..., 1, 2] * G[..., 2, 1])
+           - G[..., 0, 1] * (G[..., 1, 0] * G[..., 2, 2] - G[..., 1, 2] * G[..., 2, 0])
+           + G[..., 0, 2] * (G[..., 1, 0] * G[..., 2, 1] - G[..., 1, 1] * G[..., 2, 0]))
+    tr = np.einsum("...ij,...ij->...", np.linalg.inv(G), A)
+    return det - 1.0, tr
+
+
 def ko(u, g, h, p: Params):
     nx, ny, nz, vs = _check_state(u, g)
     out = np.zeros_like(u)

@@ -89,10 +89,11 @@ def lib():
                                        _p]
     L.bssn_rk4_step.argtypes = [G, P, ctypes.c_int, ctypes.c_double, ctypes.c_int, _p, _p, _p, _p, ull, _p]
     L.bssn_constraints.argtypes = [G, P, _p, _p, _p, _p, _p, _p, _p, ull, _p]
+    L.bssn_algebraic_constraints.argtypes = [G, P, _p, _p, _p, _p, ull, _p]
     L.bssn_probe_fp_rates.argtypes = [_p]
     for name in ("bssn_fill_ghosts", "bssn_rhs", "bssn_ko_dissipation", "bssn_rk4_stage", "bssn_rk4_step",
                  "bssn_diff_tables", "bssn_rk4_stage_fused",
-                 "bssn_constraints", "bssn_probe_fp_rates"):
+                 "bssn_constraints", "bssn_algebraic_constraints", "bssn_probe_fp_rates"):
         getattr(L, name).restype = ctypes.c_int
     _L = L
     return L
@@ -434,6 +435,19 @@ def constraints(grid, params, state, work, ham=None, mom=None, gcon=None, stream
                                _stream(stream))
     if s not in (OK, ERR_NONFINITE):
         raise BssnError(s, "constraints")
+    return l2, mx, s
+
+
+def algebraic_constraints(grid, params, state, work, stream=None):
+    """det(gt) - 1 and gt^ij At_ij over interior points: returns (l2[2],
+    max[2], status); status is OK or ERR_NONFINITE."""
+    l2 = np.zeros(2)
+    mx = np.zeros(2)
+    s = lib().bssn_algebraic_constraints(ctypes.byref(grid), ctypes.byref(params), _ptr(state),
+                                         l2.ctypes.data_as(_p), mx.ctypes.data_as(_p), _ptr(work), _nbytes(work),
+                                         _stream(stream))
+    if s not in (OK, ERR_NONFINITE):
+        raise BssnError(s, "algebraic_constraints")
     return l2, mx, s
 
 

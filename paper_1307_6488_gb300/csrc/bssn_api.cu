@@ -198,6 +198,66 @@ __global__ void __launch_bounds__(256) k_reduce_partials(const double* __restric
   }
 }
 
+// ---------------------------------------------------------------- algebraic constraints
+// det gt - 1 and gt^ij At_ij at every interior point (both vanish for exact
+// data; the evolution does not enforce them), reduced per block like the
+// differential constraints: part[b * 14 + q], q = 0, 1 sums of squares,
+// q = 7, 8 maxima of the modulus, the other slots 0.
+__global__ void __launch_bounds__(CON_THREADS) k_algebraic(Layout L, const double* __restrict__ u,
+                                                           double* __restrict__ part, unsigned int* flag) {
+  const long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double c[2] = {0.0, 0.0};
+  bool bad = false;
+  if (lin < L.npts) {
+    const int i = (int)(lin % L.nx);
+    const long long r = lin / L.nx;
+    const int j = (int)(r % L.ny), k = (int)(r / L.ny);
+    const long long p = L.off0 + i + j * L.sy + k * L.sz;
+    double g[6], A[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      g[q] = __ldg(u + (V_GT11 + q) * L.vs + p);
+      A[q] = __ldg(u + (V_AT11 + q) * L.vs + p);
+    }
+    // cofactors of the symmetric matrix (xx, xy, xz, yy, yz, zz)
+    const double c0 = g[3] * g[5] - g[4] * g[4], c1 = g[2] * g[4] - g[1] * g[5], c2 = g[1] * g[4] - g[2] * g[3];
+    const double c3 = g[0] * g[5] - g[2] * g[2], c4 = g[1] * g[2] - g[0] * g[4], c5 = g[0] * g[3] - g[1] * g[1];
+    const double det = g[0] * c0 + g[1] * c1 + g[2] * c2;
+    c[0] = det - 1.0;
+    c[1] = (c0 * A[0] + c3 * A[3] + c5 * A[5] + 2.0 * (c1 * A[1] + c2 * A[2] + c4 * A[4])) / det;
+    bad = !isfinite(c[0]) || !isfinite(c[1]);
+  }
+  if (bad) atomicOr(flag, 1u);
+  __shared__ double red[CON_THREADS / 32][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    double sq = c[q] * c[q];
+    double m = fabs(c[q]);
+    if (!(m == m)) m = 0.0;  // NaN is reported by the flag
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sq += __shfl_down_sync(0xffffffffu, sq, o);
+      m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    }
+    if (lane == 0) {
+      red[warp][q] = sq;
+      red[warp][2 + q] = m;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 14) {
+    const int q = threadIdx.x;
+    double v = 0.0;
+    if (q == 0 || q == 1 || q == 7 || q == 8) {
+      const int slot = q < 7 ? q : 2 + (q - 7);
+      v = red[0][slot];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = q < 7 ? v + red[w][slot] : fmax(v, red[w][slot]);
+    }
+    part[(long long)blockIdx.x * 14 + q] = v;
+  }
+}
+
 // ---------------------------------------------------------------- FP rate probe
 constexpr int PROBE_CHAINS = 8;
 __global__ void k_probe_dfma(double* out, double b, double c, int iters) {
@@ -451,6 +511,38 @@ bssn_status_t bssn_constraints(const bssn_grid_t* grid, const bssn_params_t* par
   if (e != cudaSuccess) return latch(e);
   const double npts = (double)L.npts;
   for (int q = 0; q < 7; ++q) {
+    out_l2[q] = std::sqrt(host[q] / npts);
+    out_max[q] = host[7 + q];
+  }
+  unsigned int flag;
+  std::memcpy(&flag, &host[14], sizeof(flag));
+  return flag ? BSSN_ERR_NONFINITE : BSSN_OK;
+}
+
+bssn_status_t bssn_algebraic_constraints(const bssn_grid_t* grid, const bssn_params_t* params, const double* state,
+                                         double* out_l2, double* out_max, void* work, unsigned long long work_bytes,
+                                         void* stream) {
+  if (!grid_ok(grid) || !params_ok(grid, params)) return BSSN_ERR_INVALID_ARG;
+  if (!aligned16(state) || !aligned16(work) || !out_l2 || !out_max) return BSSN_ERR_INVALID_ARG;
+  if (work_bytes < work_layout(*grid, *params).total_bytes) return BSSN_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Layout L = make_layout(*grid);
+  const WorkPtrs w = work_ptrs(work, *grid, *params, BSSN_FP64);
+  cudaError_t e = cudaMemsetAsync(w.flag, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) {
+    k_algebraic<<<(unsigned int)con_blocks(L), CON_THREADS, 0, s>>>(L, state, w.part, w.flag);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    k_reduce_partials<<<1, 256, 0, s>>>(w.part, con_blocks(L), w.finals);
+    e = cudaGetLastError();
+  }
+  double host[16];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, w.finals, 16 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return latch(e);
+  const double npts = (double)L.npts;
+  for (int q = 0; q < 2; ++q) {
     out_l2[q] = std::sqrt(host[q] / npts);
     out_max[q] = host[7 + q];
   }

@@ -96,6 +96,11 @@ def test_invalid_arguments_rejected(L):
     assert L.bssn_rhs(G(g), G(B.make_params(shift=2)), 0, FAKE, FAKE * 4, FAKE * 2, nb, None) == E
     # constraints without host outputs
     assert L.bssn_constraints(G(g), G(p), FAKE, None, None, None, None, None, FAKE * 2, nb, None) == E
+    # algebraic constraints: no host outputs, misaligned state, scratch too small
+    h2 = ctypes.cast((ctypes.c_double * 2)(), ctypes.c_void_p)
+    assert L.bssn_algebraic_constraints(G(g), G(p), FAKE, None, None, FAKE * 2, nb, None) == E
+    assert L.bssn_algebraic_constraints(G(g), G(p), FAKE + 8, h2, h2, FAKE * 2, nb, None) == E
+    assert L.bssn_algebraic_constraints(G(g), G(p), FAKE, h2, h2, FAKE * 2, nb - 8, None) == E
     # step: bad boundary mode
     assert L.bssn_rk4_step(G(g), G(p), 0, 0.1, 3, None, FAKE, FAKE * 2, FAKE * 4, nb, None) == E
     assert B.last_error() == B.OK
