@@ -52,18 +52,18 @@ except (OSError, ValueError):
 
 # DRAM traffic of the fused stage kernel per launch, from one ncu capture of
 # the same source (profiles/); ignored when the kernel source has changed.
-# Captured at 96^3 (884,736 points: 3.264 GB read + 2.787 GB written per
+# Captured at 96^3 (884,736 points: 3.265 GB read + 2.789 GB written per
 # launch, 6.84 kB per point at 4 blocks/SM, rows traversed in bricks) and
 # scaled to 128^3 by
 # the point count, since the traffic is per point (state, tables and the
 # per-thread stack).
-TRAFFIC = {"src_sha": "4dc52511f4f9e9aa", "bytes_per_launch_128": (3.263100928e9 + 2.787525376e9) * 128 ** 3 / 96 ** 3}
+TRAFFIC = {"src_sha": "763e5da6656a7cae", "bytes_per_launch_128": (3.265242112e9 + 2.789099264e9) * 128 ** 3 / 96 ** 3}
 # FP64 pipe utilisation of the same launch (sm__pipe_fp64_cycles_active,
 # percent of peak over active cycles), for the same source.
-FP64_PIPE_BUSY = {"src_sha": "4dc52511f4f9e9aa", "pct_of_active_cycles": 85.14}
+FP64_PIPE_BUSY = {"src_sha": "763e5da6656a7cae", "pct_of_active_cycles": 85.15}
 # The same for the FP32-RHS stage kernel k_stage<8,0,float> (one launch at
-# 96^3: 0.581 GB read + 0.707 GB written, 1.46 kB per point), scaled to 128^3.
-TRAFFIC_F32 = {"src_sha": "4dc52511f4f9e9aa", "bytes_per_launch_128": (0.580835328e9 + 0.707021312e9) * 128 ** 3 / 96 ** 3}
+# 96^3: 0.582 GB read + 0.707 GB written, 1.46 kB per point), scaled to 128^3.
+TRAFFIC_F32 = {"src_sha": "763e5da6656a7cae", "bytes_per_launch_128": (0.581551104e9 + 0.706940160e9) * 128 ** 3 / 96 ** 3}
 N_SM = 152
 FP64_FMA_PER_CLK_SM = 2
 

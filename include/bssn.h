@@ -506,7 +506,9 @@ bssn_status_t bssn_corrector_apply(bssn_corrector_t* c, const bssn_grid_t* grid,
  * pointwise values when not NULL. out_l2[7] and out_max[7] are HOST arrays:
  * root-mean-square and maximum modulus over interior points, in the order
  * H, M1, M2, M3, G1, G2, G3. Synchronizes `stream`. Returns
- * BSSN_ERR_NONFINITE (after filling the outputs) if any value is NaN/Inf. */
+ * BSSN_ERR_NONFINITE (after filling the outputs) if any value is NaN/Inf
+ * or the conformal factor W is not positive at an interior point (the
+ * evolution has left the domain where the variables mean anything). */
 bssn_status_t bssn_constraints(const bssn_grid_t* grid, const bssn_params_t* params, const double* state,
                                double* ham, double* mom, double* gcon, double* out_l2, double* out_max,
                                void* work, unsigned long long work_bytes, void* stream);

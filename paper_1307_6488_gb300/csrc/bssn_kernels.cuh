@@ -654,6 +654,7 @@ __global__ void __launch_bounds__(128, STAGE_F64_MIN_BLOCKS) k_constraints(Layou
       for (int a = 0; a < 3; ++a) gcon[a * L.vs + p] = c[4 + a];
 #pragma unroll
     for (int q = 0; q < 7; ++q) bad |= !isfinite(c[q]);
+    bad |= !(Q.u[V_W] > 0.0);  // the conformal factor must stay positive
   }
   if (bad) atomicOr(flag, 1u);
   __shared__ double red[4][14];

@@ -243,6 +243,22 @@ def test_constraints_nonfinite_status():
     assert st == B.ERR_NONFINITE
 
 
+def test_constraints_flag_nonpositive_conformal_factor():
+    """A finite but non-positive W at one interior point is reported like a
+    non-finite value; the same state with W > 0 there is not."""
+    torch = need_gpu()
+    g = 3
+    u = perturbed_bl(8, 8, 8, g, 0.15, seed=4)
+    p = B.make_params(fd_order=4)
+    grid = grid_for(u, g, 0.15)
+    work = B.alloc_work(grid, p)
+    _, _, st = B.constraints(grid, p, B.upload(u, grid), work)
+    assert st == B.OK
+    u[IDX["W"], g + 1, g + 5, g + 2] = -0.25
+    _, _, st = B.constraints(grid, p, B.upload(u, grid), work)
+    assert st == B.ERR_NONFINITE
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_fill_ghosts_parity(mode):
     torch = need_gpu()
