@@ -52,18 +52,19 @@ except (OSError, ValueError):
 
 # DRAM traffic of the fused stage kernel per launch, from one ncu capture of
 # the same source (profiles/); ignored when the kernel source has changed.
-# Captured at 96^3 (884,736 points: 3.265 GB read + 2.789 GB written per
+# Captured at 96^3 (884,736 points: 3.249 GB read + 2.783 GB written per
 # launch, 6.84 kB per point at 4 blocks/SM, rows traversed in bricks) and
 # scaled to 128^3 by
 # the point count, since the traffic is per point (state, tables and the
 # per-thread stack).
-TRAFFIC = {"src_sha": "763e5da6656a7cae", "bytes_per_launch_128": (3.265242112e9 + 2.789099264e9) * 128 ** 3 / 96 ** 3}
+TRAFFIC = {"src_sha": "05abd4d45060a217", "bytes_per_launch_128": (3.248892416e9 + 2.782864640e9) * 128 ** 3 / 96 ** 3}
 # FP64 pipe utilisation of the same launch (sm__pipe_fp64_cycles_active,
 # percent of peak over active cycles), for the same source.
-FP64_PIPE_BUSY = {"src_sha": "763e5da6656a7cae", "pct_of_active_cycles": 85.15}
-# The same for the FP32-RHS stage kernel k_stage<8,0,float> (one launch at
-# 96^3: 0.582 GB read + 0.707 GB written, 1.46 kB per point), scaled to 128^3.
-TRAFFIC_F32 = {"src_sha": "763e5da6656a7cae", "bytes_per_launch_128": (0.581551104e9 + 0.706940160e9) * 128 ** 3 / 96 ** 3}
+FP64_PIPE_BUSY = {"src_sha": "05abd4d45060a217", "pct_of_active_cycles": 85.18}
+# The same for the FP32-RHS stage kernel k_stage<8,0,float> as bssn_rk4_step
+# runs it (writing the next stage's single-precision input too; one launch
+# at 96^3: 0.569 GB read + 0.757 GB written, 1.50 kB per point), scaled to 128^3.
+TRAFFIC_F32 = {"src_sha": "05abd4d45060a217", "bytes_per_launch_128": (0.568696832e9 + 0.756768256e9) * 128 ** 3 / 96 ** 3}
 N_SM = 152
 FP64_FMA_PER_CLK_SM = 2
 
@@ -282,26 +283,43 @@ def run_gpu(args):
     work = B.alloc_work(grid, p, device=dev)
     rates = None if (args.profile or args.corrector_only or args.amr_only or args.cfd_only) else B.probe_fp_rates()
 
-    def run_form(prec, sample_clocks):
+    def run_form(prec, sample_clocks, whole_step=False):
+        """Warm-up and timed RK4 steps of one form. Default: each stage through
+        its own calls (ghost fill, tables, fused stage) with CUDA events around
+        every fused-stage launch inside the timed region. whole_step: one
+        bssn_rk4_step call per step (the FP32 form then converts the state to
+        single precision once per step, each stage leaving the next its
+        single-precision input); the fused stage is then timed on two more
+        steps made of single calls (without those extra stores)."""
         state = state0.clone()
         launches = [0]
+        bufs3 = B.alloc_state(grid, device=dev, n=3) if whole_step else None
 
-        def step(ev=None):
-            ys = state
-            outs = [ya, yb, ya, state]
+        def staged(ev=None, y=None):
+            y = state if y is None else y
+            ys = y
+            outs = [ya, yb, ya, y]
             for s in range(4):
                 B.fill_ghosts(grid, 1, ghost_src, ys)
                 B.diff_tables(grid, p, prec, ys, work)
                 if ev is not None:
                     ev.append(torch.cuda.Event(enable_timing=True))
                     ev[-1].record(stream)
-                B.rk4_stage_fused(grid, p, prec, s, dt, state, ys, acc, outs[s], work)
+                B.rk4_stage_fused(grid, p, prec, s, dt, y, ys, acc, outs[s], work)
                 if ev is not None:
                     ev.append(torch.cuda.Event(enable_timing=True))
                     ev[-1].record(stream)
                 ys = outs[s]
-            B.fill_ghosts(grid, 1, ghost_src, state)
+            B.fill_ghosts(grid, 1, ghost_src, y)
             launches[0] += 13 if prec == B.FP64 else 17
+
+        def step(ev=None):
+            if not whole_step:
+                staged(ev)
+                return
+            B.rk4_step(grid, p, prec, dt, 1, ghost_src, state, bufs3, work)
+            # FP32: one conversion, 4 x (ghost fill, tables, fused stage), final ghost fill
+            launches[0] += 13 if prec == B.FP64 else 14
 
         for _ in range(args.warmup):
             step()
@@ -324,6 +342,14 @@ def run_gpu(args):
             clk.__exit__()
         barrier(world)
         ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
+        timed_launches = launches[0]
+        if whole_step:
+            spare = state.clone()  # the timed state stays at its step count
+            for _ in range(2):
+                staged(ev, spare)
+            torch.cuda.synchronize()
+            del spare
+        launches[0] = timed_launches
         stage_ms = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(len(ev) // 2)]
         l2, mx, st = B.constraints(grid, p, state, work)
         alg, _, _ = B.algebraic_constraints(grid, p, state, work)
@@ -864,7 +890,7 @@ def run_gpu(args):
         return
 
     f64 = run_form(B.FP64, not args.profile)
-    f32 = run_form(B.FP32_RHS, False)
+    f32 = run_form(B.FP32_RHS, False, whole_step=True)
     if args.profile:
         # profiling run (small case under ncu): only the two timed step loops
         if rank == 0:
@@ -1023,6 +1049,10 @@ def run_gpu(args):
         "forms": {
             "fp32_rhs": {"value": world * pts * args.steps / (f32["ms"] * 1e-3), "unit": UNIT,
                          "ms_per_step": f32["ms"] / args.steps, "stage_ms": f32["stage_ms"],
+                         "timed_through": "bssn_rk4_step: one single-precision conversion per step, each stage "
+                                          "writing the next stage's single-precision input",
+                         "stage_ms_from": "the fused stage kernel timed on two further steps of per-stage calls "
+                                          "(without the single-precision stores)",
                          "achieved_tflops": achieved32 / 1e12, "frac_of_fp32_peak": achieved32 / peak32,
                          # algorithmic bytes of the stage kernel per point and stage, averaged over
                          # the four stages: FP32 stencil input 96, FP32 tables 88, FP64 W 8, y0 192,

@@ -53,9 +53,9 @@ bool params_ok(const bssn_grid_t* G, const bssn_params_t* P) {
 // Scratch layout, one size for both precisions:
 //   [tables region][constraint partials][finals + flag]
 // The tables region holds, for BSSN_FP64, the double difference tables
-// (2 x 11 x p/2 arrays of var_stride doubles); for BSSN_FP32_RHS, the single
-// precision copy of the state (24 x var_stride floats) followed by the
-// single precision tables - which always fits in the double tables' space.
+// (2 x 11 x p/2 arrays of var_stride doubles); for BSSN_FP32_RHS, two single
+// precision copies of the state (24 x var_stride floats each: a whole step
+// alternates between them) followed by the single precision tables.
 struct WorkLayout {
   size_t tables;     // doubles
   size_t partials;   // doubles
@@ -67,7 +67,7 @@ WorkLayout work_layout(const bssn_grid_t& G, const bssn_params_t& P) {
   Layout L = make_layout(G);
   WorkLayout W;
   const size_t dbl = diff_doubles(L, P.fd_order / 2);
-  const size_t f32 = ((size_t)NV * L.vs + 2 * dbl / 2 + 1) / 2;  // floats -> doubles, rounded up
+  const size_t f32 = (2 * (size_t)NV * L.vs + 2 * dbl / 2 + 1) / 2;  // floats -> doubles, rounded up
   W.tables = dbl > f32 ? dbl : f32;
   W.partials = (size_t)con_blocks(L) * 14;
   W.finals = 16;
@@ -79,6 +79,7 @@ struct WorkPtrs {
   void* dX;       // difference tables (double or float)
   void* dY;
   float* f32;     // single-precision state copy (FP32 form)
+  float* f32b;    // a second one (the next stage's input, written by the stage before)
   double* dX64;   // double tables (constraints)
   double* dY64;
   double* part;
@@ -96,11 +97,13 @@ WorkPtrs work_ptrs(void* work, const bssn_grid_t& G, const bssn_params_t& P, bss
   w.dY64 = base + NM * H * L.vs;
   if (prec == BSSN_FP64) {
     w.f32 = nullptr;
+    w.f32b = nullptr;
     w.dX = w.dX64;
     w.dY = w.dY64;
   } else {
     w.f32 = (float*)base;
-    float* t = w.f32 + (size_t)NV * L.vs;
+    w.f32b = w.f32 + (size_t)NV * L.vs;
+    float* t = w.f32b + (size_t)NV * L.vs;
     w.dX = t;
     w.dY = t + NM * H * L.vs;
   }
@@ -142,10 +145,33 @@ cudaError_t run_stage(int order, bssn_precision_t prec, const bssn_grid_t& G, co
   return run_fused(order, prec, G, P, rk, ys, y0, acc, out, w, mode, s);
 }
 
+// A stage of the FP32 form inside a whole step: the single-precision input
+// ys32 is already complete (converted here only when `convert`), and the
+// stage also writes the single-precision copy of its output into out32
+// (nullable), whose ghosts the next ghost fill completes. The same values as
+// converting each stage's input afresh, without the conversion pass.
+cudaError_t run_stage32(int order, const bssn_grid_t& G, const bssn_params_t& P, const RK& rk, const double* ys,
+                        const double* y0, double* acc, double* out, const WorkPtrs& w, float* ys32, float* out32,
+                        bool convert, cudaStream_t s) {
+  const Layout L = make_layout(G);
+  cudaError_t e = convert ? launch_to_f32(L, ys, ys32, s) : cudaSuccess;
+  if (e == cudaSuccess)
+    e = order == 4 ? launch_diffs<4>(L, G, BSSN_FP32_RHS, ys32, w.dX, w.dY, s)
+                   : launch_diffs<8>(L, G, BSSN_FP32_RHS, ys32, w.dX, w.dY, s);
+  if (e != cudaSuccess) return e;
+  const Gauge gz = make_gauge(P);
+  StageArgs A{ys32, ys, y0, acc, out, w.dX, w.dY, out32};
+  return order == 4 ? launch_stage<4>(L, G, P.ko_eps, BSSN_FP32_RHS, gz, rk, A, 0, s)
+                    : launch_stage<8>(L, G, P.ko_eps, BSSN_FP32_RHS, gz, rk, A, 0, s);
+}
+
 bool prec_ok(bssn_precision_t prec) { return prec == BSSN_FP64 || prec == BSSN_FP32_RHS; }
 
 // ---------------------------------------------------------------- ghost fill
-__global__ void __launch_bounds__(256) k_fill_ghosts(Layout L, int mode, const double* __restrict__ src, double* u) {
+// Ghost fill; u32 (nullable): the single-precision copy of u, whose ghosts
+// get the same values rounded to float.
+__global__ void __launch_bounds__(256) k_fill_ghosts(Layout L, int mode, const double* __restrict__ src, double* u,
+                                                     float* u32) {
   const long long ex = L.nx + 2LL * L.g, ey = L.ny + 2LL * L.g, ez = L.nz + 2LL * L.g;
   const long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (lin >= ex * ey * ez) return;
@@ -157,7 +183,11 @@ __global__ void __launch_bounds__(256) k_fill_ghosts(Layout L, int mode, const d
   const long long p = L.off0 + i + j * L.sy + k * L.sz;
   if (mode == 1) {
 #pragma unroll 4
-    for (int v = 0; v < NV; ++v) u[v * L.vs + p] = __ldg(src + v * L.vs + p);
+    for (int v = 0; v < NV; ++v) {
+      const double x = __ldg(src + v * L.vs + p);
+      u[v * L.vs + p] = x;
+      if (u32) u32[v * L.vs + p] = __double2float_rn(x);
+    }
     return;
   }
   const int ii = ((i % L.nx) + L.nx) % L.nx;
@@ -165,13 +195,18 @@ __global__ void __launch_bounds__(256) k_fill_ghosts(Layout L, int mode, const d
   const int kk = ((k % L.nz) + L.nz) % L.nz;
   const long long q = L.off0 + ii + jj * L.sy + kk * L.sz;
 #pragma unroll 4
-  for (int v = 0; v < NV; ++v) u[v * L.vs + p] = u[v * L.vs + q];
+  for (int v = 0; v < NV; ++v) {
+    const double x = u[v * L.vs + q];
+    u[v * L.vs + p] = x;
+    if (u32) u32[v * L.vs + p] = __double2float_rn(x);
+  }
 }
 
-cudaError_t fill(const bssn_grid_t& G, int mode, const double* src, double* u, cudaStream_t s) {
+cudaError_t fill(const bssn_grid_t& G, int mode, const double* src, double* u, cudaStream_t s,
+                 float* u32 = nullptr) {
   const Layout L = make_layout(G);
   const long long n = (G.nx + 2LL * G.ghost) * (G.ny + 2LL * G.ghost) * (G.nz + 2LL * G.ghost);
-  k_fill_ghosts<<<(unsigned int)((n + 255) / 256), 256, 0, s>>>(L, mode, src, u);
+  k_fill_ghosts<<<(unsigned int)((n + 255) / 256), 256, 0, s>>>(L, mode, src, u, u32);
   return cudaGetLastError();
 }
 
@@ -404,11 +439,23 @@ bssn_status_t bssn_rk4_step(const bssn_grid_t* grid, const bssn_params_t* params
   cudaError_t e = cudaSuccess;
   const double* ys = state;
   double* outs[4] = {ya, yb, ya, state};
+  // FP32 form: the state is converted once; each later stage's input comes
+  // from the stage before, alternating between the two copies in work
+  const bool f32 = prec == BSSN_FP32_RHS;
+  float* cur32 = w.f32;
+  float* nxt32 = w.f32b;
   for (int st = 0; st < 4 && e == cudaSuccess; ++st) {
-    if (grid->ghost > 0) e = fill(*grid, bc, ghost_src, const_cast<double*>(ys), s);
+    if (grid->ghost > 0) e = fill(*grid, bc, ghost_src, const_cast<double*>(ys), s, (f32 && st > 0) ? cur32 : nullptr);
     if (e != cudaSuccess) break;
-    e = run_stage(order, prec, *grid, *params, make_rk(st, dt), ys, state, acc, outs[st], w, 0, s);
+    if (f32)
+      e = run_stage32(order, *grid, *params, make_rk(st, dt), ys, state, acc, outs[st], w, cur32,
+                      st < 3 ? nxt32 : nullptr, st == 0, s);
+    else
+      e = run_stage(order, prec, *grid, *params, make_rk(st, dt), ys, state, acc, outs[st], w, 0, s);
     ys = outs[st];
+    float* t = cur32;
+    cur32 = nxt32;
+    nxt32 = t;
   }
   if (e == cudaSuccess && grid->ghost > 0) e = fill(*grid, bc, ghost_src, state, s);
   return latch(e);
@@ -443,11 +490,21 @@ bssn_status_t bssn_rk3_step(const bssn_grid_t* grid, const bssn_params_t* params
   // y1 -> bufs, y2 -> bufs + n, y3 -> state (y0 is read only at the point written)
   const double* ys = state;
   double* outs[3] = {bufs, bufs + n, state};
+  const bool f32 = prec == BSSN_FP32_RHS;  // as in bssn_rk4_step
+  float* cur32 = w.f32;
+  float* nxt32 = w.f32b;
   for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
-    if (grid->ghost > 0) e = fill(*grid, bc, ghost_src, const_cast<double*>(ys), s);
+    if (grid->ghost > 0) e = fill(*grid, bc, ghost_src, const_cast<double*>(ys), s, (f32 && st > 0) ? cur32 : nullptr);
     if (e != cudaSuccess) break;
-    e = run_stage(order, prec, *grid, *params, make_rk3(st, dt), ys, state, nullptr, outs[st], w, 0, s);
+    if (f32)
+      e = run_stage32(order, *grid, *params, make_rk3(st, dt), ys, state, nullptr, outs[st], w, cur32,
+                      st < 2 ? nxt32 : nullptr, st == 0, s);
+    else
+      e = run_stage(order, prec, *grid, *params, make_rk3(st, dt), ys, state, nullptr, outs[st], w, 0, s);
     ys = outs[st];
+    float* t = cur32;
+    cur32 = nxt32;
+    nxt32 = t;
   }
   if (e == cudaSuccess && grid->ghost > 0) e = fill(*grid, bc, ghost_src, state, s);
   return latch(e);

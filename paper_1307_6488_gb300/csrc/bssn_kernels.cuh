@@ -54,6 +54,7 @@ struct StagePtrs {
   double* out;         // ynext (stage) or rhs (right-hand side only)
   const R* dX;         // x-difference tables
   const R* dY;         // y-difference tables
+  float* out32;        // FP32 form, stages: also the single-precision copy of ynext (nullable)
 };
 
 __device__ __forceinline__ void point_coords(const Layout& L, long long lin, int& i, int& j, int& k) {
@@ -566,12 +567,17 @@ __device__ __forceinline__ void stage_point(const Layout& L, const Coef<R>& C, c
     for (int v = 0; v < NV; ++v) S.out[v * vs + p] = (double)rhs[v];
     return;
   }
+  // the FP32 form can leave the next stage its single-precision input
+  bool copy32 = false;
+  if constexpr (std::is_same<R, float>::value) copy32 = S.out32 != nullptr;
   if (rk.method == 3) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const long long o = v * vs + p;
       const double kv = (double)(rhs[v] + ko[v]);
-      S.out[o] = fma(rk.cdt, kv, fma(rk.a1, __ldg(S.ys64 + o), rk.a0 * __ldg(S.y0 + o)));
+      const double yn = fma(rk.cdt, kv, fma(rk.a1, __ldg(S.ys64 + o), rk.a0 * __ldg(S.y0 + o)));
+      S.out[o] = yn;
+      if (copy32) S.out32[o] = __double2float_rn(yn);
     }
     return;
   }
@@ -580,15 +586,18 @@ __device__ __forceinline__ void stage_point(const Layout& L, const Coef<R>& C, c
     const long long o = v * vs + p;
     const double kv = (double)(rhs[v] + ko[v]);
     const double y0 = __ldg(S.y0 + o);
+    double yn;
     if (rk.stage == 0) {
       S.acc[o] = rk.bdt * kv;
-      S.out[o] = fma(rk.cdt, kv, y0);
+      yn = fma(rk.cdt, kv, y0);
     } else if (rk.stage < 3) {
       S.acc[o] = fma(rk.bdt, kv, S.acc[o]);
-      S.out[o] = fma(rk.cdt, kv, y0);
+      yn = fma(rk.cdt, kv, y0);
     } else {
-      S.out[o] = y0 + fma(rk.bdt, kv, S.acc[o]);
+      yn = y0 + fma(rk.bdt, kv, S.acc[o]);
     }
+    S.out[o] = yn;
+    if (copy32) S.out32[o] = __double2float_rn(yn);
   }
 }
 

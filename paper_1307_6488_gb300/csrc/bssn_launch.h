@@ -16,6 +16,7 @@ struct StageArgs {
   double* out;
   const void* dX;
   const void* dY;
+  float* out32 = nullptr;  // FP32 form: single-precision copy of out (nullable)
 };
 
 // FP64: first-difference tables (H per mixed variable); FP32_RHS: first-

@@ -63,10 +63,11 @@ extern "C" bssn_status_t bssn_rk4_stage_noalloc(const bssn_grid_t* grid, const b
   const bssn_status_t st = scratch_on_current_device(&scratch);
   if (st != BSSN_OK) return st;
 
-  // Difference tables inside the scratch, laid out as bssn_work_bytes sizes
-  // them: FP64 - x tables then y tables (11 x p/2 arrays of var_stride
-  // doubles each); FP32-RHS - the single-precision state copy (24 arrays of
-  // var_stride floats) followed by the single-precision x and y tables.
+  // Difference tables inside the scratch: FP64 - x tables then y tables
+  // (11 x p/2 arrays of var_stride doubles each); FP32-RHS - one
+  // single-precision state copy (24 arrays of var_stride floats) followed by
+  // the single-precision x and y tables (bssn_work_bytes also counts a
+  // second copy, which only whole steps use, so this fits within it).
   const Layout L = make_layout(*grid);
   const size_t H = (size_t)params->fd_order / 2;
   const size_t tab = (size_t)NM * H * (size_t)L.vs;

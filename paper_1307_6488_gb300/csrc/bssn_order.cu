@@ -28,7 +28,7 @@ cudaError_t launch_diffs<BSSN_ORDER>(const Layout& L, const bssn_grid_t& G, bssn
 template <typename R>
 static cudaError_t stage_typed(const Layout& L, const bssn_grid_t& G, double eps, const Gauge& gz, const RK& rk,
                                const StageArgs& A, int mode, cudaStream_t s) {
-  StagePtrs<R> S{(const R*)A.ys, A.ys64, A.y0, A.acc, A.out, (const R*)A.dX, (const R*)A.dY};
+  StagePtrs<R> S{(const R*)A.ys, A.ys64, A.y0, A.acc, A.out, (const R*)A.dX, (const R*)A.dY, A.out32};
   const Coef<R> C = make_coef<BSSN_ORDER, R>(G, eps);
   // FP32: 2D tiles of STAGE_F32_TILE_X x (128 / STAGE_F32_TILE_X) points
   const int tx = std::is_same<R, float>::value ? STAGE_F32_TILE_X : 0;

@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(TILE_THREADS, stage_min_blocks<R>()) kb_stage(
     S.out = D.buf[out];
     S.dX = (const R*)D.dX;
     S.dY = (const R*)D.dY;
+    S.out32 = nullptr;
     stage_point<PO, 0, R>(L, coef_of<R>(D), gz, rk, S, p);
   }
 }

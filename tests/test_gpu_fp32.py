@@ -144,6 +144,51 @@ def test_fp32_gauge_switches(order, gauge):
         assert np.max(np.max(np.abs(gi - wi), axis=1) / scale) < 1e-5
 
 
+@pytest.mark.parametrize("order,bc", [(8, 1), (4, 0)])
+@pytest.mark.parametrize("method", [4, 3])
+def test_fp32_whole_step_equals_its_stages(order, bc, method):
+    """bssn_rk4_step and bssn_rk3_step convert the state to single precision
+    once per step: each stage writes the single-precision copy of its output
+    beside it and the ghost fill completes it. Two steps must equal, bit for
+    bit, the stages called one at a time (ghost fill, then the stage with its
+    own fresh conversion), static and periodic ghosts."""
+    torch = need_gpu()
+    g = order // 2 + 1
+    h = 0.12
+    u = smooth_bl(14, 11, 9, g, h, seed=70 + order + method)
+    p = B.make_params(fd_order=order)
+    grid = grid_for(u, g, h)
+    src = B.upload(u, grid)
+    a = src.clone()
+    b = src.clone()
+    work = B.alloc_work(grid, p, B.FP32_RHS)
+    bufs = B.alloc_state(grid, n=3)
+    mine = B.alloc_state(grid, n=3)
+    n = 24 * grid.var_stride
+    ya, yb, acc = mine[:n], mine[n:2 * n], mine[2 * n:]
+    dt = 0.25 * h
+    gsrc = src if bc == 1 else None
+    for _ in range(2):
+        if method == 4:
+            B.rk4_step(grid, p, B.FP32_RHS, dt, bc, gsrc, a, bufs, work)
+            ys, outs = b, [ya, yb, ya, b]
+            for st in range(4):
+                B.fill_ghosts(grid, bc, gsrc, ys)
+                B.rk4_stage(grid, p, B.FP32_RHS, st, dt, b, ys, acc, outs[st], work)
+                ys = outs[st]
+        else:
+            B.rk3_step(grid, p, B.FP32_RHS, dt, bc, gsrc, a, bufs, work)
+            ys, outs = b, [ya, yb, b]
+            for st in range(3):
+                B.fill_ghosts(grid, bc, gsrc, ys)
+                B.rk3_stage(grid, p, B.FP32_RHS, st, dt, b, ys, outs[st], work)
+                ys = outs[st]
+        B.fill_ghosts(grid, bc, gsrc, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b), float(torch.max(torch.abs(a - b)))
+    assert not torch.equal(a, src)
+
+
 def test_fp32_stage_split_matches_fused_call():
     """bssn_diff_tables + bssn_rk4_stage_fused == bssn_rk4_stage, both forms."""
     torch = need_gpu()
