@@ -39,10 +39,10 @@ WORKLOAD = ("Brill-Lindquist two punctures (m=0.5 at x=+-1.5), 128^3 on [-8,8]^3
 # with mixed derivatives counted as one first-derivative stencil applied to
 # shared first derivatives (33 x 12), the algebra as the oracle writes it,
 # Kreiss-Oliger for 24 variables and the RK4 stage combination (4 per
-# variable). See DESIGN.md "Algorithmic work".
+# variable).
 FLOPS_PER_POINT_STAGE = None  # filled from the oracle's counter at start-up
 
-# Driver-measured copy bandwidth and dense BF16 GEMM rate of this GPU type
+# Measured copy bandwidth and dense BF16 GEMM rate of this GPU type
 # (absent on machines where they were not measured).
 try:
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as _f:
