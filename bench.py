@@ -214,6 +214,39 @@ def cpu_oracle_rate_single_thread(budget_s=4.0, n=16):
         return None
 
 
+def cpu_oracle_gauge_wave_24(want_state=True):
+    """The 24^3 gauge-wave configuration in full on the oracle: 10 RK4 steps
+    (4th order, 3 ghosts, periodic, 1+log + Gamma-driver, KO 0.1, dt = dx/4,
+    A = 0.01 plus 1e-10 seeded noise). Returns (final state or None,
+    updates/s, seconds, threads)."""
+    import oracle
+    from paper_1307_6488_gb300 import inputs
+    u, h = inputs.gauge_wave(24, 3, amplitude=0.01, noise=1e-10, seed=1307)
+    p = oracle.Params(fd_order=4, ko_eps=0.1, lapse=0, shift=0, eta=2.0)
+    dt = 0.25 * h
+    oracle.rk4_step(u, 3, h, dt, p, bc=0)  # warm the library
+    t0 = time.perf_counter()
+    y = u
+    for _ in range(10):
+        y = oracle.rk4_step(y, 3, h, dt, p, bc=0)
+    el = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return (y if want_state else None), 10 * 24 ** 3 / el, el, threads
+
+
+def cpu_oracle_gauge_wave_24_single_thread():
+    """The same on one OpenMP thread, in a child process; (updates/s, seconds)
+    or None."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "r = bench.cpu_oracle_gauge_wave_24(False); print(json.dumps(r[1:3]))" % (ROOT,))
+    env = dict(os.environ, OMP_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+        return tuple(json.loads(out.stdout.strip().splitlines()[-1]))
+    except Exception:  # noqa: BLE001 - a baseline that could not be taken is reported as missing
+        return None
+
+
 def run_reference(args):
     # under torchrun only rank 0 times the oracle; the other ranks leave at
     # once (no process group: nothing is exchanged)
@@ -523,9 +556,20 @@ def run_gpu(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms_graph = e0.elapsed_time(e1) / reps
+        # the same 10 steps on the oracle (all host cores and one), and the
+        # GPU's 10-step state against the oracle's
+        st.copy_(s0)
+        ten()
+        torch.cuda.synchronize()
+        got = B.download(st, gq)
+        want, cpu_rate, cpu_s, cpu_threads = cpu_oracle_gauge_wave_24()
+        one = cpu_oracle_gauge_wave_24_single_thread()
         del bufs, wk
         return {"value": world * 10 * 24 ** 3 / (ms_graph * 1e-3), "unit": UNIT, "ms_per_10_steps_graph": ms_graph,
                 "ms_per_10_steps_eager": ms_eager, "launches_per_10_steps": 130,
+                "cpu_oracle": {"value": cpu_rate, "unit": UNIT, "seconds": cpu_s, "cores": cpu_threads,
+                               "single_thread": None if one is None else {"value": one[0], "seconds": one[1]}},
+                "gpu_vs_oracle_after_10_steps_max_rel_per_tensor": float(np.max(tensor_rel_err(got, want, 3))),
                 "workload": "24^3 gauge wave + 1e-10 noise, periodic, 4th order, 3 ghosts, 10 RK4 steps"}
 
     def run_paper_shape(nn, lo, hi, prec, method, steps):
