@@ -16,7 +16,9 @@ independently of how the oracle transcribes the equations:
     constraint -> its closed form at the stencil order;
   * Brill-Lindquist: momentum constraint and several right-hand sides are
     exactly zero;
-  * relabelling the axes permutes the right-hand side accordingly.
+  * relabelling the axes permutes the right-hand side accordingly;
+  * reflecting one axis reflects the right-hand side, each component
+    signed by its parity under the reflection.
 """
 import numpy as np
 import pytest
@@ -227,3 +229,41 @@ def test_axis_relabelling(order):
     scale = np.max(np.abs(interior(want, g)).reshape(NVAR, -1), axis=1) + 1e-300
     err = np.max(np.abs(interior(r2 - want, g)).reshape(NVAR, -1), axis=1) / scale
     assert np.max(err) < 1e-13, err
+
+
+@pytest.mark.parametrize("order", [4, 8])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_reflection(order, axis):
+    """Reflecting one coordinate, x_a -> -x_a, maps the right-hand side of the
+    reflected state to the reflected right-hand side: each component picks up
+    (-1)^(number of indices equal to a). With a generic shift of both signs
+    this pins the mirroring of the one-sided advection stencil and every
+    sign in the algebra that a relabelling cannot reach."""
+    g = order // 2 + 1
+    n = 7
+    u, h = inputs.brill_lindquist(n, g, lo=-2.0, hi=2.0, centers=((-0.43, 0.31, 0.2), (0.52, -0.15, -0.33)),
+                                  masses=(0.3, 0.4))
+    inputs.smooth_perturbation(u, g, 3e-2, 17 + axis, h)
+    p = oracle.Params(fd_order=order, eta=1.5)
+    r = oracle.rhs(u, g, h, p, ko=True)
+    sign = np.ones(NVAR)
+    for i in range(3):
+        for j in range(i, 3):
+            s = (-1.0) ** ((i == axis) + (j == axis))
+            sign[IDX["gt11"] + inputs.SYM[i][j]] = s
+            sign[IDX["At11"] + inputs.SYM[i][j]] = s
+    for base in ("Gt1", "beta1", "B1"):
+        sign[IDX[base] + axis] = -1.0
+
+    def reflect(s):
+        # array axes are (var, z, y, x): coordinate a is array axis 3 - a
+        return np.ascontiguousarray(np.flip(s, axis=3 - axis) * sign[:, None, None, None])
+
+    r2 = oracle.rhs(reflect(u), g, h, p, ko=True)
+    want = reflect(r)
+    scale = np.max(np.abs(interior(want, g)).reshape(NVAR, -1), axis=1) + 1e-300
+    err = np.max(np.abs(interior(r2 - want, g)).reshape(NVAR, -1), axis=1) / scale
+    assert np.max(err) < 1e-13, dict(zip(inputs.VARS, err))
+    # the shift really has both signs along the reflected axis
+    b = interior(u, g)[IDX["beta1"] + axis]
+    assert b.min() < 0 < b.max()
