@@ -15,7 +15,8 @@ numpy.linalg.inv), sharing nothing with the oracle's packed, point-by-point
 C++. The oracle's right-hand side at a grid point must converge to it at
 the stencil order (4 or 8) as the spacing halves; a wrong sign, index or
 dropped term in either transcription leaves an h-independent difference and
-stops the convergence.
+stops the convergence. The Hamiltonian, momentum and Gamma constraints are
+checked the same way.
 """
 import numpy as np
 import pytest
@@ -139,6 +140,41 @@ def rhs_transcribed(val, d1, d2, lapse, shift, shift_coeff, eta, advect_gauge):
     return out
 
 
+def constraints_transcribed(val, d1, d2):
+    """Hamiltonian, momentum and Gamma constraints from exact point values:
+    H = R + 2/3 K^2 - At_ij At^ij with R = W^2 gt^ij R_ij,
+    M_i = gt^jk (d_k At_ij - Gt^l_ki At_lj - Gt^l_kj At_il) - 3/W At^j_i d_j W - 2/3 d_i K,
+    G^i = Gt^i - gt^jk Gt^i_jk."""
+    W, K = val[W_], val[K_]
+    gt = sym33(val[GT:GT + 6])
+    At = sym33(val[AT:AT + 6])
+    dW, dK = d1[W_], d1[K_]
+    dgt = np.stack([sym33(d1[GT:GT + 6, k]) for k in range(3)])
+    ddgt = np.array([[sym33(d2[GT:GT + 6, k, l]) for l in range(3)] for k in range(3)])
+    dAt = np.stack([sym33(d1[AT:AT + 6, k]) for k in range(3)])             # [k, i, j] = d_k At_ij
+    dGam = d1[GAM:GAM + 3].T
+    ddW = d2[W_]
+    gu = np.linalg.inv(gt)
+    Gl = 0.5 * (np.einsum("ikj->kij", dgt) + np.einsum("jki->kij", dgt) - dgt)
+    Gu = np.einsum("kl,lij->kij", gu, Gl)
+    Gd = np.einsum("ij,kij->k", gu, Gu)
+    R = -0.5 * np.einsum("lm,lmij->ij", gu, ddgt)
+    R += 0.5 * (np.einsum("ki,jk->ij", gt, dGam) + np.einsum("kj,ik->ij", gt, dGam))
+    R += 0.5 * np.einsum("k,ijk->ij", Gd, Gl + np.einsum("jik->ijk", Gl))
+    R += np.einsum("lm,kli,jkm->ij", gu, Gu, Gl)
+    R += np.einsum("lm,klj,ikm->ij", gu, Gu, Gl)
+    R += np.einsum("lm,kim,klj->ij", gu, Gu, Gl)
+    DDW = ddW - np.einsum("kij,k->ij", Gu, dW)
+    R += (DDW + gt * np.einsum("kl,kl", gu, DDW)) / W - 2 * gt * np.einsum("kl,k,l", gu, dW, dW) / W ** 2
+    Au = gu @ At @ gu
+    H = W ** 2 * np.einsum("ij,ij", gu, R) + 2 / 3 * K ** 2 - np.einsum("ij,ij", At, Au)
+    DAt = np.einsum("kij->ijk", dAt) - np.einsum("lki,lj->ijk", Gu, At) - np.einsum("lkj,il->ijk", Gu, At)  # [i,j,k]
+    Amix = np.einsum("jk,ik->ij", gu, At)                                   # [i, j] = At^j_i
+    M = np.einsum("jk,ijk->i", gu, DAt) - 3 / W * Amix @ dW - 2 / 3 * dK
+    G = val[GAM:GAM + 3] - Gd
+    return np.concatenate([[H], M, G])
+
+
 def oracle_at(exprs, pt, h, order, p):
     """The oracle's right-hand side at pt: one interior point, its ghosts
     filled with the exact fields."""
@@ -149,7 +185,11 @@ def oracle_at(exprs, pt, h, order, p):
     for v, e in enumerate(exprs):
         f = sp.lambdify(X, e, "numpy")
         u[v] = np.broadcast_to(f(xx, yy, zz), xx.shape)
-    return oracle.rhs(np.ascontiguousarray(u), g, h, p)[:, g, g, g]
+    u = np.ascontiguousarray(u)
+    if p is None:
+        _, _, _, (ham, mom, gcon) = oracle.constraints(u, g, h, order, fields=True)
+        return np.concatenate([[ham[g, g, g]], mom[:, g, g, g], gcon[:, g, g, g]])
+    return oracle.rhs(u, g, h, p)[:, g, g, g]
 
 
 GAUGES = [dict(lapse=0, shift=0, advect_gauge=1), dict(lapse=1, shift=0, advect_gauge=0)]
@@ -169,6 +209,22 @@ def test_rhs_converges_to_second_transcription(order, hs, gauge, seed):
     errs = [np.max(np.abs(oracle_at(exprs, pt, h, order, p) - want)) / scale for h in hs]
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     # every variable is alive: a dropped term would show at O(1)
+    assert np.min(np.abs(want)) > 1e-4 * scale
+    assert errs[-1] < (1e-5 if order == 4 else 1e-7), errs
+    assert order - 0.6 < rates[-1] < order + 1.5, (errs, rates)
+
+
+@pytest.mark.parametrize("order,hs", [(4, (0.08, 0.04, 0.02)), (8, (0.3, 0.15, 0.075))])
+@pytest.mark.parametrize("seed", [11, 29])
+def test_constraints_converge_to_second_transcription(order, hs, seed):
+    """The same for the Hamiltonian, momentum and Gamma constraints."""
+    exprs = fields(seed)
+    pt = np.random.default_rng(seed + 2).uniform(-1, 1, 3)
+    val, d1, d2 = exact_derivatives(exprs, pt)
+    want = constraints_transcribed(val, d1, d2)
+    scale = np.max(np.abs(want))
+    errs = [np.max(np.abs(oracle_at(exprs, pt, h, order, None) - want)) / scale for h in hs]
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.min(np.abs(want)) > 1e-4 * scale
     assert errs[-1] < (1e-5 if order == 4 else 1e-7), errs
     assert order - 0.6 < rates[-1] < order + 1.5, (errs, rates)
