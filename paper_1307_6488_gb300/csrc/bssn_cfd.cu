@@ -48,6 +48,7 @@ struct Cfd {
   int per[3];
   float nu, dt, omega, alpha, lid, g[3];
   float beta_in;  // beta of a cell whose six faces all move (the same float operations as the kernels)
+  float beta_xw;  // beta of a cell with one x face on a wall and the other five movable
 };
 
 __host__ __device__ __forceinline__ long long cidx(const Cfd& C, int i, int j, int k) {
@@ -209,6 +210,87 @@ __device__ __forceinline__ bool wrap_cell(const Cfd& C, int a, int& c) {
   return true;
 }
 
+// The short path of k_cfd_mass_rb for a box whose halo lies away from the
+// y and z walls and seams. XW: the box touches a walled x end (cells past
+// the last do not exist; a cell with an x wall face has beta_xw and keeps
+// that face); otherwise it is inner along x too and has no masks at all.
+template <bool XW>
+__device__ __forceinline__ void mass_rb_short(const Cfd& C, const float* const* S, float* const* D,
+                                              float* __restrict__ p, float (&dps)[3][RB_TY + 2][RB_TX + 2], int i0,
+                                              int j0, int k0, int k1, int t, bool col1, int ty, int m2) {
+  constexpr int HALF = (RB_TX + 2) / 2;
+  const int nx = C.n[0];
+  const int sy = (int)C.sy;
+  const long long st[3] = {1, C.sy, C.sz};
+  for (int k = k0 - 1; k <= k1; ++k) {
+    const int kc = k - 1;
+    const int tx = 2 * m2 + ((i0 + j0 + ty + kc + (col1 ? 1 : 0)) & 1);
+    const int i = i0 + tx;
+    const bool mine = kc >= k0 && (!XW || i < nx);
+    const bool xlo = !XW || i > 0, xhi = !XW || i < nx - 1;  // x faces movable
+    const long long o = cidx(C, i0, j0, kc) + tx + ty * sy;
+    float fhi[3], flo[3], p0 = 0.f;
+    if (mine) {
+      p0 = p[o];
+      if (col1) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          fhi[a] = __ldg(S[a] + o);
+          flo[a] = __ldg(S[a] + o - st[a]);
+        }
+      }
+    }
+    const int slot = (k + 3) % 3;
+    if (t < HALF * (RB_TY + 2)) {
+      const int r = t / HALF;
+      const int x = 2 * (t % HALF) + ((i0 + j0 + r + k) & 1);  // i + j + k even, i = i0 - 1 + x, j = j0 - 1 + r
+      const int ih = i0 - 1 + x;
+      if (!XW || (ih >= 0 && ih < nx)) {
+        const long long oh = cidx(C, i0, j0, k) + (x - 1) + (r - 1) * sy;
+        float hhi[3], hlo[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          hhi[a] = __ldg(S[a] + oh);
+          hlo[a] = __ldg(S[a] + oh - st[a]);
+        }
+        const bool full = !XW || (ih > 0 && ih < nx - 1);
+        dps[slot][r][x] = cell_dp(C, full ? C.beta_in : C.beta_xw, hhi, hlo);
+      }
+    }
+    __syncthreads();
+    if (mine) {
+      const int s0 = (kc + 3) % 3;
+      if (!col1) {
+        p[o] = __fadd_rn(p0, dps[s0][ty + 1][tx + 1]);
+        if (XW) {
+          if (!xhi) D[0][o] = __ldg(S[0] + o);
+          if (!xlo) D[0][o - 1] = __ldg(S[0] + o - 1);
+        }
+      } else {
+        const float nlo[3] = {dps[s0][ty + 1][tx], dps[s0][ty][tx + 1], dps[(kc + 2) % 3][ty + 1][tx + 1]};
+        const float nhi[3] = {dps[s0][ty + 1][tx + 2], dps[s0][ty + 2][tx + 1], dps[(kc + 4) % 3][ty + 1][tx + 1]};
+        if (xlo) flo[0] = move_hi(C, 0, nlo[0], flo[0]);
+        if (xhi) fhi[0] = move_lo(C, 0, nhi[0], fhi[0]);
+#pragma unroll
+        for (int a = 1; a < 3; ++a) {
+          flo[a] = move_hi(C, a, nlo[a], flo[a]);
+          fhi[a] = move_lo(C, a, nhi[a], fhi[a]);
+        }
+        const float dp = cell_dp(C, (xlo && xhi) ? C.beta_in : C.beta_xw, fhi, flo);
+        p[o] = __fadd_rn(p0, dp);
+        D[0][o] = xhi ? move_hi(C, 0, dp, fhi[0]) : fhi[0];
+        D[0][o - 1] = xlo ? move_lo(C, 0, dp, flo[0]) : flo[0];
+#pragma unroll
+        for (int a = 1; a < 3; ++a) {
+          D[a][o] = move_hi(C, a, dp, fhi[a]);
+          D[a][o - st[a]] = move_lo(C, a, dp, flo[a]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(RB_TX * RB_TY) k_cfd_mass_rb(Cfd C, const float* __restrict__ u,
                                                                const float* __restrict__ v,
                                                                const float* __restrict__ w, float* __restrict__ un,
@@ -229,68 +311,18 @@ __global__ void __launch_bounds__(RB_TX * RB_TY) k_cfd_mass_rb(Cfd C, const floa
   const bool col1 = t < RB_TX * RB_TY / 2;
   const int t2 = col1 ? t : t - RB_TX * RB_TY / 2;
   const int ty = t2 / (RB_TX / 2), m2 = t2 % (RB_TX / 2);
-  // A box whose halo cells all lie inside the domain, away from its walls
-  // and its periodic seams, has every face of every cell movable: no masks,
-  // no wrap-around, beta_in everywhere, and 32-bit offsets within a plane.
-  // Most boxes are of this kind; they take the short path below.
-  const bool inner = i0 >= 2 && i0 + RB_TX <= C.n[0] - 2 && j0 >= 2 && j0 + RB_TY <= C.n[1] - 2 && k0 >= 2 &&
-                     k0 + RB_KC <= C.n[2] - 2;
-  if (inner) {
-    const int sy = (int)C.sy;
-    const long long st[3] = {1, C.sy, C.sz};
-    for (int k = k0 - 1; k <= k1; ++k) {
-      const int kc = k - 1;
-      const int tx = 2 * m2 + ((i0 + j0 + ty + kc + (col1 ? 1 : 0)) & 1);
-      const bool mine = kc >= k0;
-      const long long o = cidx(C, i0, j0, kc) + tx + ty * sy;
-      float fhi[3], flo[3], p0 = 0.f;
-      if (mine) {
-        p0 = p[o];
-        if (col1) {
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            fhi[a] = __ldg(S[a] + o);
-            flo[a] = __ldg(S[a] + o - st[a]);
-          }
-        }
-      }
-      const int slot = (k + 3) % 3;
-      if (t < HALF * (RB_TY + 2)) {
-        const int r = t / HALF;
-        const int x = 2 * (t % HALF) + ((i0 + j0 + r + k) & 1);  // i + j + k even, i = i0 - 1 + x, j = j0 - 1 + r
-        const long long oh = cidx(C, i0, j0, k) + (x - 1) + (r - 1) * sy;
-        float hhi[3], hlo[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          hhi[a] = __ldg(S[a] + oh);
-          hlo[a] = __ldg(S[a] + oh - st[a]);
-        }
-        dps[slot][r][x] = cell_dp(C, C.beta_in, hhi, hlo);
-      }
-      __syncthreads();
-      if (mine) {
-        const int s0 = (kc + 3) % 3;
-        if (!col1) {
-          p[o] = __fadd_rn(p0, dps[s0][ty + 1][tx + 1]);
-        } else {
-          const float nlo[3] = {dps[s0][ty + 1][tx], dps[s0][ty][tx + 1], dps[(kc + 2) % 3][ty + 1][tx + 1]};
-          const float nhi[3] = {dps[s0][ty + 1][tx + 2], dps[s0][ty + 2][tx + 1], dps[(kc + 4) % 3][ty + 1][tx + 1]};
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            flo[a] = move_hi(C, a, nlo[a], flo[a]);
-            fhi[a] = move_lo(C, a, nhi[a], fhi[a]);
-          }
-          const float dp = cell_dp(C, C.beta_in, fhi, flo);
-          p[o] = __fadd_rn(p0, dp);
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            D[a][o] = move_hi(C, a, dp, fhi[a]);
-            D[a][o - st[a]] = move_lo(C, a, dp, flo[a]);
-          }
-        }
-      }
-      __syncthreads();
-    }
+  // A box whose halo cells lie away from the walls and periodic seams of y
+  // and z takes a short path (no masks, no wrap-around, 32-bit offsets
+  // within a plane): fully inner boxes without any mask, boxes at the ends
+  // of a row along a walled x with the two x masks only. Most boxes are of
+  // the first kind.
+  const bool yz_inner = j0 >= 2 && j0 + RB_TY <= C.n[1] - 2 && k0 >= 2 && k0 + RB_KC <= C.n[2] - 2;
+  if (yz_inner && i0 >= 2 && i0 + RB_TX <= C.n[0] - 2) {
+    mass_rb_short<false>(C, S, D, p, dps, i0, j0, k0, k1, t, col1, ty, m2);
+    return;
+  }
+  if (yz_inner && !C.per[0]) {
+    mass_rb_short<true>(C, S, D, p, dps, i0, j0, k0, k1, t, col1, ty, m2);
     return;
   }
   for (int k = k0 - 1; k <= k1; ++k) {
@@ -448,6 +480,9 @@ bool make_cfd(const bssn_cfd_t* d, Cfd* C) {
   float s = 0.f;
   for (int a = 0; a < 3; ++a) s = (s + C->ih2[a]) + C->ih2[a];
   C->beta_in = C->omega / (C->dt * s);
+  s = C->ih2[0];
+  for (int a = 1; a < 3; ++a) s = (s + C->ih2[a]) + C->ih2[a];
+  C->beta_xw = C->omega / (C->dt * s);
   return true;
 }
 
