@@ -71,7 +71,7 @@ FP64_FMA_PER_CLK_SM = 2
 
 # DRAM traffic of one k_cfd_mass_rb iteration at 256^3 (ncu dram__bytes_read.sum
 # + dram__bytes_write.sum), for the source it was taken on.
-CFD_TRAFFIC = {"src_sha": "4f9fbb9e49791ae9", "bytes_per_launch": 287919872 + 227734528}
+CFD_TRAFFIC = {"src_sha": "1559830c488ce0a5", "bytes_per_launch": 286361600 + 225778176}
 
 # the sources that make up the fused FP64 stage kernel k_stage<8,0,double>
 STAGE_SOURCES = ("bssn_common.cuh", "bssn_point.cuh", "bssn_kernels.cuh", "bssn_order.cu")
