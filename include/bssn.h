@@ -183,7 +183,11 @@ bssn_status_t bssn_rk4_stage_noalloc(const bssn_grid_t* grid, const bssn_params_
  * filled before each (bc 0 periodic, bc 1 static from ghost_src). Needs three
  * state-sized buffers in `bufs` (bufs, bufs + var_stride*24, ...: 3*24*
  * var_stride doubles) besides work. On return the interior of state holds the
- * new values and its ghosts are refilled. */
+ * new values and its ghosts are refilled. In the FP32-RHS form the state is
+ * converted to single precision once per step: each stage also stores the
+ * single-precision copy of its output (in work) and the ghost fill completes
+ * it, so the result equals the four stages called one at a time bit for
+ * bit, without their per-stage conversions. bssn_rk3_step does the same. */
 bssn_status_t bssn_rk4_step(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec,
                             double dt, int bc, const double* ghost_src, double* state, double* bufs,
                             void* work, unsigned long long work_bytes, void* stream);
