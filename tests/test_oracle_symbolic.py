@@ -15,8 +15,8 @@ numpy.linalg.inv), sharing nothing with the oracle's packed, point-by-point
 C++. The oracle's right-hand side at a grid point must converge to it at
 the stencil order (4 or 8) as the spacing halves; a wrong sign, index or
 dropped term in either transcription leaves an h-independent difference and
-stops the convergence. The Hamiltonian, momentum and Gamma constraints are
-checked the same way.
+stops the convergence. The Hamiltonian, momentum and Gamma constraints and
+the electric and magnetic parts of the Weyl tensor are checked the same way.
 """
 import numpy as np
 import pytest
@@ -175,6 +175,79 @@ def constraints_transcribed(val, d1, d2):
     return np.concatenate([[H], M, G])
 
 
+def weyl_transcribed(val, d1, d2):
+    """Electric and magnetic parts of the Weyl tensor from exact point values,
+    with the physical metric's own Christoffel symbols (not the conformal
+    split): gamma = gt / W^2, K_ij = (At_ij + gt_ij K / 3) / W^2,
+    E_ij = R_ij + K K_ij - K_ik K^k_j (K the evolved trace variable),
+    B_ij = 1/2 (eps_i^kl D_k K_lj + eps_j^kl D_k K_li), eps^mkl = [mkl] / sqrt(det gamma).
+    Returns E and B packed (11 12 13 22 23 33)."""
+    W, K = val[W_], val[K_]
+    gt = sym33(val[GT:GT + 6])
+    At = sym33(val[AT:AT + 6])
+    dW, dK = d1[W_], d1[K_]
+    dgt = np.stack([sym33(d1[GT:GT + 6, k]) for k in range(3)])
+    dAt = np.stack([sym33(d1[AT:AT + 6, k]) for k in range(3)])
+    R = _physical_ricci(val, d1, d2)  # through the conformal decomposition
+    gam = gt / W ** 2
+    Kd = (At + gt * K / 3) / W ** 2
+    dgam = dgt / W ** 2 - 2 * gt[None] * dW[:, None, None] / W ** 3
+    dKd = ((dAt + dgt * K / 3 + gt[None] * dK[:, None, None] / 3) / W ** 2
+           - 2 * (At + gt * K / 3)[None] * dW[:, None, None] / W ** 3)
+    gamu = np.linalg.inv(gam)
+    chr_ = 0.5 * np.einsum("pq,kql->pkl", gamu, dgam) + 0.5 * np.einsum("pq,lqk->pkl", gamu, dgam) \
+        - 0.5 * np.einsum("pq,qkl->pkl", gamu, dgam)                         # Gamma^p_kl
+    DK = dKd - np.einsum("pkl,pj->klj", chr_, Kd) - np.einsum("pkj,lp->klj", chr_, Kd)  # [k, l, j]
+    E = R + K * Kd - Kd @ gamu @ Kd
+    lc = np.zeros((3, 3, 3))
+    for a, b, c in ((0, 1, 2), (1, 2, 0), (2, 0, 1)):
+        lc[a, b, c] = 1.0
+        lc[a, c, b] = -1.0
+    eps_u = lc / np.sqrt(np.linalg.det(gam))                                  # eps^mkl
+    eps_m = np.einsum("im,mkl->ikl", gam, eps_u)                              # eps_i^kl
+    X = np.einsum("ikl,klj->ij", eps_m, DK)
+    Bm = 0.5 * (X + X.T)
+    pack = lambda M: np.array([M[i, j] for (i, j) in PAIRS])
+    return pack(E), pack(Bm)
+
+
+def _physical_ricci(val, d1, d2):
+    """R_ij of gamma = gt / W^2 through the conformal decomposition
+    (conformal Ricci with the evolved Gt^i in its derivative term, plus the
+    conformal-factor part), as the right-hand side uses it."""
+    W = val[W_]
+    gt = sym33(val[GT:GT + 6])
+    dW = d1[W_]
+    dgt = np.stack([sym33(d1[GT:GT + 6, k]) for k in range(3)])
+    ddgt = np.array([[sym33(d2[GT:GT + 6, k, l]) for l in range(3)] for k in range(3)])
+    dGam = d1[GAM:GAM + 3].T
+    ddW = d2[W_]
+    gu = np.linalg.inv(gt)
+    Gl = 0.5 * (np.einsum("ikj->kij", dgt) + np.einsum("jki->kij", dgt) - dgt)
+    Gu = np.einsum("kl,lij->kij", gu, Gl)
+    Gd = np.einsum("ij,kij->k", gu, Gu)
+    R = -0.5 * np.einsum("lm,lmij->ij", gu, ddgt)
+    R += 0.5 * (np.einsum("ki,jk->ij", gt, dGam) + np.einsum("kj,ik->ij", gt, dGam))
+    R += 0.5 * np.einsum("k,ijk->ij", Gd, Gl + np.einsum("jik->ijk", Gl))
+    R += np.einsum("lm,kli,jkm->ij", gu, Gu, Gl)
+    R += np.einsum("lm,klj,ikm->ij", gu, Gu, Gl)
+    R += np.einsum("lm,kim,klj->ij", gu, Gu, Gl)
+    DDW = ddW - np.einsum("kij,k->ij", Gu, dW)
+    R += (DDW + gt * np.einsum("kl,kl", gu, DDW)) / W - 2 * gt * np.einsum("kl,k,l", gu, dW, dW) / W ** 2
+    return R
+
+
+def oracle_weyl_at(exprs, pt, h, order):
+    g = oracle.required_ghost(order)
+    off = (np.arange(2 * g + 1) - g) * h
+    zz, yy, xx = np.meshgrid(pt[2] + off, pt[1] + off, pt[0] + off, indexing="ij")
+    u = np.zeros((NV,) + xx.shape)
+    for v, e in enumerate(exprs):
+        u[v] = np.broadcast_to(sp.lambdify(X, e, "numpy")(xx, yy, zz), xx.shape)
+    out = oracle.psi4(np.ascontiguousarray(u), g, h, order, pt)  # the one interior point is pt
+    return out["E"][:, g, g, g], out["B"][:, g, g, g]
+
+
 def oracle_at(exprs, pt, h, order, p):
     """The oracle's right-hand side at pt: one interior point, its ghosts
     filled with the exact fields."""
@@ -228,6 +301,22 @@ def test_constraints_converge_to_second_transcription(order, hs, seed):
     assert np.min(np.abs(want)) > 1e-4 * scale
     assert errs[-1] < (1e-5 if order == 4 else 1e-7), errs
     assert order - 0.6 < rates[-1] < order + 1.5, (errs, rates)
+
+
+@pytest.mark.parametrize("order,hs", [(4, (0.08, 0.04, 0.02)), (8, (0.3, 0.15, 0.075))])
+def test_weyl_parts_converge_to_second_transcription(order, hs):
+    """E_ij and B_ij of the Weyl diagnostics (the inputs of Psi_4), against a
+    transcription that takes the physical metric's Christoffels directly."""
+    exprs = fields(11)
+    pt = np.array([0.37, -0.21, 0.44])
+    val, d1, d2 = exact_derivatives(exprs, pt)
+    wE, wB = weyl_transcribed(val, d1, d2)
+    for name, want, k in (("E", wE, 0), ("B", wB, 1)):
+        scale = np.max(np.abs(want))
+        errs = [np.max(np.abs(oracle_weyl_at(exprs, pt, h, order)[k] - want)) / scale for h in hs]
+        rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+        assert errs[-1] < (1e-5 if order == 4 else 1e-7), (name, errs)
+        assert order - 0.6 < rates[-1] < order + 1.5, (name, errs, rates)
 
 
 def test_transcription_sees_each_term():
