@@ -319,6 +319,46 @@ def test_weyl_parts_converge_to_second_transcription(order, hs):
         assert order - 0.6 < rates[-1] < order + 1.5, (name, errs, rates)
 
 
+def test_psi4_from_transcribed_weyl_parts():
+    """Psi_4 and the invariant I assembled from the transcribed E and B at
+    the point: the gamma-orthonormal triad by Gram-Schmidt of the radial,
+    theta and phi coordinate directions about the coordinate origin,
+    m = (e_theta + i e_phi) / sqrt(2), Psi_4 = (E - i B)_ij mbar^i mbar^j,
+    I = (E - i B)_ij (E - i B)^ij / 2. The oracle's values converge to them
+    at the stencil order."""
+    exprs = fields(29)
+    pt = np.array([0.61, -0.48, 0.33])
+    val, d1, d2 = exact_derivatives(exprs, pt)
+    wE, wB = weyl_transcribed(val, d1, d2)
+    Q = sym33(wE) - 1j * sym33(wB)
+    gam = sym33(val[GT:GT + 6]) / val[W_] ** 2
+    dot = lambda a, b: a @ gam @ b
+    x, y, z = pt
+    basis = [np.array([x, y, z]), np.array([x * z, y * z, -(x * x + y * y)]), np.array([-y, x, 0.0])]
+    tri = []
+    for v in basis:
+        for e in tri:
+            v = v - dot(v, e) * e
+        tri.append(v / np.sqrt(dot(v, v)))
+    m = (tri[1] + 1j * tri[2]) / np.sqrt(2)
+    want_psi4 = np.einsum("ij,i,j", Q, np.conj(m), np.conj(m))
+    gamu = np.linalg.inv(gam)
+    want_inv = 0.5 * np.einsum("ij,ik,jl,kl", Q, gamu, gamu, Q)
+    errs = []
+    for h in (0.3, 0.15, 0.075):
+        g = oracle.required_ghost(8)
+        off = (np.arange(2 * g + 1) - g) * h
+        zz, yy, xx = np.meshgrid(pt[2] + off, pt[1] + off, pt[0] + off, indexing="ij")
+        u = np.zeros((NV,) + xx.shape)
+        for v, e in enumerate(exprs):
+            u[v] = np.broadcast_to(sp.lambdify(X, e, "numpy")(xx, yy, zz), xx.shape)
+        out = oracle.psi4(np.ascontiguousarray(u), g, h, 8, pt)
+        errs.append(max(abs(out["psi4"][g, g, g] - want_psi4) / abs(want_psi4),
+                        abs(out["inv"][g, g, g] - want_inv) / abs(want_inv)))
+    rate = np.log2(errs[1] / errs[2])
+    assert errs[-1] < 1e-7 and 7.4 < rate < 9.5, (errs, rate)
+
+
 def test_transcription_sees_each_term():
     """The comparison is sensitive: perturbing the oracle's input by a
     planted mistake of the size of one term (the sign of the shift's
