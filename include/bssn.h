@@ -531,6 +531,21 @@ bssn_status_t bssn_algebraic_constraints(const bssn_grid_t* grid, const bssn_par
                                          double* out_l2, double* out_max, void* work, unsigned long long work_bytes,
                                          void* stream);
 
+/* Checkpoint and resume. bssn_checkpoint_write stores `state` (HOST, the
+ * full 24 * grid->var_stride doubles of the padded layout, ghosts included)
+ * with the grid, the parameters, the time t and the step count in one file
+ * at `path` (overwritten), followed by a 64-bit FNV-1a hash of the data.
+ * bssn_checkpoint_read restores grid, params, t and step, and - if `state`
+ * (HOST, `capacity` doubles) is not NULL - the data. A resumed evolution
+ * continues from exactly the same bits. Both return BSSN_ERR_INVALID_ARG
+ * for NULL or invalid arguments, a file that cannot be opened, written or
+ * read in full, a foreign format (magic, byte order, version), an invalid
+ * grid, too small a capacity or a hash mismatch. Host only; no GPU work. */
+bssn_status_t bssn_checkpoint_write(const char* path, const bssn_grid_t* grid, const bssn_params_t* params, double t,
+                                    long long step, const double* state);
+bssn_status_t bssn_checkpoint_read(const char* path, bssn_grid_t* grid, bssn_params_t* params, double* t,
+                                   long long* step, double* state, unsigned long long capacity);
+
 /* Gravitational-wave extraction beside the evolution (the WeylScal4 kernel
  * the paper runs on the GPU, Sec. 3.3), FP64, at interior points of `state`
  * (DEVICE, ghosts filled): from the BSSN variables

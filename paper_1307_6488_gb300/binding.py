@@ -451,6 +451,45 @@ def algebraic_constraints(grid, params, state, work, stream=None):
     return l2, mx, s
 
 
+def checkpoint_write(path, grid, params, t, step, state):
+    """Write a checkpoint: state is the HOST copy of the full padded state
+    (24 * var_stride doubles, e.g. state_tensor.cpu().numpy())."""
+    a = np.ascontiguousarray(np.asarray(state, dtype=np.float64).reshape(-1))
+    if a.size < NVAR * grid.var_stride:
+        raise BssnError(ERR_INVALID_ARG, "checkpoint_write: state smaller than 24 * var_stride")
+    _check(_ckp_lib().bssn_checkpoint_write(os.fsencode(path), ctypes.byref(grid), ctypes.byref(params), float(t),
+                                           int(step), a.ctypes.data_as(_p)), "checkpoint_write")
+
+
+def checkpoint_read(path, with_state=True):
+    """Read a checkpoint: returns (grid, params, t, step, state) with state a
+    HOST numpy array of 24 * var_stride doubles (None without with_state)."""
+    L = _ckp_lib()
+    grid, params = Grid(), Params()
+    t, step = ctypes.c_double(), ctypes.c_longlong()
+    _check(L.bssn_checkpoint_read(os.fsencode(path), ctypes.byref(grid), ctypes.byref(params), ctypes.byref(t),
+                                  ctypes.byref(step), None, 0), "checkpoint_read")
+    state = None
+    if with_state:
+        state = np.empty(NVAR * grid.var_stride)
+        _check(L.bssn_checkpoint_read(os.fsencode(path), ctypes.byref(grid), ctypes.byref(params), ctypes.byref(t),
+                                      ctypes.byref(step), state.ctypes.data_as(_p), state.size), "checkpoint_read")
+    return grid, params, t.value, step.value, state
+
+
+def _ckp_lib():
+    L = lib()
+    if not getattr(L, "_ckp_typed", False):
+        Gp, Pp = ctypes.POINTER(Grid), ctypes.POINTER(Params)
+        L.bssn_checkpoint_write.argtypes = [ctypes.c_char_p, Gp, Pp, ctypes.c_double, ctypes.c_longlong, _p]
+        L.bssn_checkpoint_read.argtypes = [ctypes.c_char_p, Gp, Pp, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_longlong), _p, ctypes.c_ulonglong]
+        L.bssn_checkpoint_write.restype = ctypes.c_int
+        L.bssn_checkpoint_read.restype = ctypes.c_int
+        L._ckp_typed = True
+    return L
+
+
 def probe_fp_rates():
     out = np.zeros(3)
     _check(lib().bssn_probe_fp_rates(out.ctypes.data_as(_p)), "probe_fp_rates")

@@ -25,6 +25,7 @@ UNITS = [
     ("bssn_transfer.cu", "bssn_transfer.o", []),
     ("bssn_amr.cu", "bssn_amr.o", []),
     ("bssn_cfd.cu", "bssn_cfd.o", []),
+    ("bssn_checkpoint.cu", "bssn_checkpoint.o", []),
 ]
 
 
