@@ -34,14 +34,6 @@ N, G, ORDER, LO, HI = 128, 5, 8, -8.0, 8.0
 WORKLOAD = ("Brill-Lindquist two punctures (m=0.5 at x=+-1.5), 128^3 on [-8,8]^3, 8th-order FD, 5 ghosts, static "
             "boundary, 1+log + Gamma-driver (eta=2), KO eps=0.1, dt=0.25h, FP64, RK4")
 
-# Algorithmic FP64 flops per interior point per RK4 stage, 8th order: the
-# oracle's instrumented count (add/sub/mul/div = 1) of the right-hand side
-# with mixed derivatives counted as one first-derivative stencil applied to
-# shared first derivatives (33 x 12), the algebra as the oracle writes it,
-# Kreiss-Oliger for 24 variables and the RK4 stage combination (4 per
-# variable).
-FLOPS_PER_POINT_STAGE = None  # filled from the oracle's counter at start-up
-
 # Measured copy bandwidth and dense BF16 GEMM rate of this GPU type
 # (absent on machines where they were not measured).
 try:
@@ -89,18 +81,31 @@ def kernel_src_sha():
     return src_sha(STAGE_SOURCES)
 
 
+# Stencil applications per interior point and right-hand side (counts of the
+# method, not of any implementation): first derivatives of W, gt_ij (6), K,
+# Gt^i (3), alpha, beta^i (3) along 3 axes; diagonal and mixed second
+# derivatives of W, gt_ij, alpha, beta^i; upwinded advection of all 24
+# variables along 3 axes, summed over the axes (2 adds per variable).
+N_FIRST, N_SECOND, N_MIXED, N_ADV, N_ADV_SUM = 45, 33, 33, 72, 48
+
+
 def algorithmic_flops(order=ORDER):
+    """Flops per interior point and RK4 stage, from the oracle's per-stencil
+    counts (pinned against hand counts in tests/test_flop_counts.py): each
+    mixed derivative counted as one first-derivative stencil applied to shared
+    first derivatives, the oracle's pointwise algebra, Kreiss-Oliger for the
+    24 variables plus one add each to put it into the right-hand side, and
+    the stage update (acc += b dt k, ynext = y0 + c dt k: 4 per variable)."""
     import oracle
     c = oracle.flop_counts(order)
-    n_first = 45          # 15 variables x 3 directions
-    n_second = 33         # 11 variables x 3 diagonal
-    n_mixed = 33          # 11 variables x 3 pairs
-    n_adv = 72            # 24 variables x 3 directions
-    gather_sep = c["gather_rhs"] - n_mixed * c["mixed_tensor"] + n_mixed * c["first"]
-    per_rhs = gather_sep + c["rhs_algebra"]
-    return dict(rhs=per_rhs, ko=24 * c["ko_var"], rk=24 * 4, total=per_rhs + 24 * c["ko_var"] + 24 * 4,
-                first=c["first"], second=c["second"], adv_dir=c["upwind_dir"], algebra=c["rhs_algebra"],
-                mixed_tensor=c["mixed_tensor"], n=(n_first, n_second, n_mixed, n_adv))
+    gather = (N_FIRST * c["first"] + N_SECOND * c["second"] + N_MIXED * c["first"] + N_ADV * c["upwind_dir"]
+              + N_ADV_SUM)
+    per_rhs = gather + c["rhs_algebra"]
+    ko = 24 * (c["ko_var"] + 1)
+    rk = 24 * 4
+    return dict(rhs=per_rhs, ko=ko, rk=rk, total=per_rhs + ko + rk, gather=gather, first=c["first"],
+                second=c["second"], adv_dir=c["upwind_dir"], algebra=c["rhs_algebra"],
+                mixed_tensor=c["mixed_tensor"], n=(N_FIRST, N_SECOND, N_MIXED, N_ADV))
 
 
 class ClockSampler:
@@ -175,17 +180,25 @@ def max_over_ranks(x, world, device):
 
 
 # ------------------------------------------------------------------ reference arm (CPU oracle)
-def cpu_oracle_rate(budget_s=15.0, n=32, max_steps=None):
-    """Oracle RK4 steps of the same workload (8th order BL, static boundary)
-    on an n^3 block of the [-8,8]^3 domain spacing; returns updates/s,
-    steps, seconds, threads."""
+def oracle_block(n=32):
+    """The workload's central n^3 block (same spacing, order, gauge and
+    dissipation as the 128^3 grid, static boundary from its own t = 0 ghosts)
+    for the CPU oracle: (state, h, dt, params)."""
     import oracle
     from paper_1307_6488_gb300 import inputs
     h = (HI - LO) / N
     lo = -n * h / 2
     u, _ = inputs.brill_lindquist(n, G, lo=lo, hi=-lo)
     p = oracle.Params(fd_order=ORDER, ko_eps=0.1, lapse=0, shift=0, eta=2.0)
-    dt = 0.25 * h
+    return u, h, 0.25 * h, p
+
+
+def cpu_oracle_rate(budget_s=15.0, n=32, max_steps=None):
+    """Oracle RK4 steps of the same workload (8th order BL, static boundary)
+    on an n^3 block of the [-8,8]^3 domain spacing; returns updates/s,
+    steps, seconds, threads."""
+    import oracle
+    u, h, dt, p = oracle_block(n)
     oracle.rk4_step(u, G, h, dt, p, bc=1, ghost_src=u)  # warm the library
     t0 = time.perf_counter()
     steps = 0
@@ -252,21 +265,30 @@ def run_reference(args):
     # once (no process group: nothing is exchanged)
     if int(os.environ.get("RANK", "0")) != 0:
         return
+    import oracle
     n = 32
-    rates = []
+    # input built and the library loaded before the clock starts; the timed
+    # region is exactly K oracle RK4 steps, each on the previous one's result
+    u, h, dt, p = oracle_block(n)
+    y = u
     for _ in range(args.warmup):
-        cpu_oracle_rate(budget_s=0.0, n=n, max_steps=1)
+        y = oracle.rk4_step(y, G, h, dt, p, bc=1, ghost_src=u)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        r, _, _, threads = cpu_oracle_rate(budget_s=0.0, n=n, max_steps=1)
-        rates.append(r)
+        y = oracle.rk4_step(y, G, h, dt, p, bc=1, ghost_src=u)
     el = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     value = n ** 3 * args.steps / el
-    sample = f"one oracle RK4 step per step on a {n}^3 block of the workload (same spacing, order, gauge, KO)"
+    sample = (f"one oracle RK4 step per step on the central {n}^3 block of the 128^3 workload (same spacing, "
+              f"order, gauge, KO; static boundary from the block's own t = 0 ghosts); updates/s of that block")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_grid": n},
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_grid": n,
+                       "sampling": f"a {n}^3 block of the 128^3 grid: updates/s is per interior point, so the "
+                                   f"rate carries over; the oracle's cost per point does not depend on the grid "
+                                   f"size"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -603,7 +625,7 @@ def run_gpu(args):
     def run_paper_shapes():
         """The paper's two GPU configurations with Brill-Lindquist data in
         place of its QC-0 data: its single-GPU benchmark, 100^3 evolved
-        points + 5 ghosts at 8th order (Sec. 4), and its binary-black-hole
+        points + 5 ghosts at 8th order (Sec. 3.4), and its binary-black-hole
         grid, 270^3 points on [-6.75, 6.75]^3, 8th order, RK3 (Sec. 3.3), which
         the paper spread over 27 GPUs and which fits one GB300."""
         out = {}
@@ -620,7 +642,7 @@ def run_gpu(args):
         return out
 
     def run_cfd():
-        """The paper's CFD benchmark shape (Sec. 4): incompressible Navier-Stokes
+        """The paper's CFD benchmark shape (Sec. 3.2): incompressible Navier-Stokes
         by SOLA in single precision on 256^3 cells, three kernels (velocity,
         4 red-black mass-conservation iterations, boundary after each). Here a
         lid-driven cavity (no-slip walls, lid speed 1, nu = 1e-3, i.e. Re =
@@ -1041,12 +1063,14 @@ def run_gpu(args):
     value = world * pts * args.steps / (f64["ms"] * 1e-3)
     e2e_value = world * pts * e2e_steps / (e2e_ms * 1e-3)
     achieved = flops["total"] * pts / (f64["stage_ms"] * 1e-3)  # FLOP/s of the fused stage kernel
-    # FP64 peak from the unit counts and the clock: 2 FP64 FMA per clock per
-    # SM (the nominal 1.25 TFLOP/s of 152 SMs at 2070 MHz), at the median SM
-    # clock sampled during the timed region; the live probe of back-to-back
-    # DFMAs is reported beside it
+    # FP64 peak: the FP64 FMA rate per SM clock measured by the probe (SM
+    # cycle counter; the unit count gives 2), times the SMs, 2 flop and the
+    # median SM clock sampled during the timed region. The probe's own rate
+    # per second, at whatever clock it ran, is reported beside it.
     sm_mhz = (f64["clocks"] or {}).get("sm_mhz") or MEASURED.get("sm_max_mhz") or 2070.0
-    peak = N_SM * FP64_FMA_PER_CLK_SM * 2.0 * sm_mhz * 1e6
+    per_clk = rates["fp64_fma_per_clk_sm"]
+    peak = N_SM * per_clk * 2.0 * sm_mhz * 1e6
+    peak_nominal = N_SM * FP64_FMA_PER_CLK_SM * 2.0 * sm_mhz * 1e6
     peak_probe = 2.0 * rates["fp64_fma_per_s"]
     sha = kernel_src_sha()
     traffic = TRAFFIC["bytes_per_launch_128"] if TRAFFIC["src_sha"] == sha and n == N else None
@@ -1064,9 +1088,11 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_stage<8,0,double> (fused RHS+KO+RK stage)",
                      "flops_per_point": flops["total"], "stage_ms": f64["stage_ms"],
-                     "peak_source": f"2 FP64 FMA/clock/SM x {N_SM} SMs x 2 flop at the sampled median SM clock "
-                                    f"{sm_mhz:.0f} MHz (nominal 1.25 TFLOP/s at 2070 MHz)",
+                     "peak_source": f"measured {per_clk:.3f} FP64 FMA/clock/SM (probe, SM cycle counter) x "
+                                    f"{N_SM} SMs x 2 flop at the sampled median SM clock {sm_mhz:.0f} MHz",
+                     "peak_nominal": peak_nominal / 1e12,
                      "peak_probe": peak_probe / 1e12,
+                     "peak_probe_sm_mhz": rates["sm_mhz_fp64_fma"],
                      "frac_of_probe": achieved / peak_probe,
                      # the HBM side of the same kernel: algorithmic bytes per point and stage,
                      # averaged over the four stages: ys 192, difference tables 704, y0 192,

@@ -10,7 +10,10 @@
  * Framework for Cross-Architecture Code Generation" (arXiv:1307.6488).
  *   Sec. 1.1  the BSSN system, its variables and its cost per grid point;
  *   Sec. 2.3  customized finite-differencing operators;
- *   Sec. 2.6  kernel frames, tiles, fat kernels (prior art for the kernels);
+ *   Sec. 2.4.1 the code generator's optimizations (constant folding, common
+ *             subexpressions, loop fission into derivative and RHS passes);
+ *   Secs. 2.5, 2.7  kernel frames (data staging and iteration), tiles, fat
+ *             kernels (prior art for the kernels);
  *   Sec. 3.3  the production configuration: 8th-order differencing,
  *             5 ghost zones for the partially upwinded stencils, double
  *             precision, a Runge-Kutta method of lines, a boundary kernel;
@@ -59,7 +62,8 @@ typedef enum {
   BSSN_ERR_NONFINITE = 3,   /* a NaN/Inf was found (constraints / plan checks)  */
   BSSN_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up                */
   BSSN_ERR_UNSUPPORTED = 5, /* valid request this build does not implement       */
-  BSSN_ERR_NOMEM = 6        /* a plan could not allocate its own storage         */
+  BSSN_ERR_NOMEM = 6,       /* a plan could not allocate its own storage         */
+  BSSN_ERR_BOUNDS = 7       /* bounds-check build: an index left its array       */
 } bssn_status_t;
 
 typedef enum {
@@ -94,6 +98,38 @@ const char* bssn_status_string(bssn_status_t s);
  * (BSSN_OK if none). Host-only, does not synchronize. */
 bssn_status_t bssn_last_error(void);
 void bssn_clear_error(void);
+
+/* Compile-time bounds-check mode. The library built with -DBSSN_BOUNDS_CHECK
+ * (libbssn_check.so; the same entry points) checks, in every kernel that
+ * indexes global memory through computed offsets (single-grid and patch
+ * stencils, ghost fills, difference tables, constraints, Psi_4, the refined
+ * hierarchy's entry lists, the CFD kernels), each point's or entry's whole
+ * access range against the extent of its array. A range outside is counted
+ * in a device word and that access is skipped; nothing traps.
+ * bssn_bounds_check_enabled() is 1 in that build, 0 otherwise.
+ * bssn_bounds_violations() waits for `stream`, returns the count of
+ * violations since the last call in *count (HOST) and clears it:
+ * BSSN_ERR_BOUNDS if it is not 0, BSSN_OK otherwise (always OK and 0 in the
+ * ordinary build). Synchronizes. */
+int bssn_bounds_check_enabled(void);
+bssn_status_t bssn_bounds_violations(unsigned long long* count, void* stream);
+
+/* Waits for `stream` to finish and reports device-side failures of the
+ * kernels that run on it: BSSN_ERR_TIMEOUT if a bounded wait inside a
+ * single-grid FP32-RHS stage kernel gave up since the last check (the
+ * record, one per device, is cleared by this call), BSSN_ERR_CUDA if the
+ * stream reported an error (also latched). Synchronizes. */
+bssn_status_t bssn_check_device(void* stream);
+
+/* Self-test of the conversions between single and double precision that
+ * the FP32-RHS kernels do on the integer pipes (IEEE 754 field moves, round
+ * to nearest even, hardware fallback for subnormal results, infinities and
+ * NaNs): for i < n, f_bits[i] and f_hw[i] receive din[i] rounded to single
+ * precision by that code and by the hardware instruction, d_bits[i] and
+ * d_hw[i] receive fin[i] widened to double both ways. The two members of
+ * each pair must agree bit for bit. Device arrays of n elements. */
+bssn_status_t bssn_test_conversions(long long n, const double* din, const float* fin, float* f_bits, float* f_hw,
+                                    double* d_bits, double* d_hw, void* stream);
 
 /* Bytes of scratch ("work") that bssn_rhs, bssn_rk4_stage and
  * bssn_constraints need for this grid, order and precision. Returns 0 and
@@ -139,7 +175,7 @@ bssn_status_t bssn_rk4_stage(const bssn_grid_t* grid, const bssn_params_t* param
                              double* ynext, void* work, unsigned long long work_bytes, void* stream);
 
 /* The two halves of bssn_rk4_stage, for callers that schedule or time them
- * separately (the paper's split of "RHS derivatives" from the rest, Sec. 2.3):
+ * separately (the paper's split of "RHS derivatives" from the rest, Sec. 2.4.1):
  * bssn_diff_tables fills the first-difference tables in `work` from `state`;
  * bssn_rk4_stage_fused then runs the fused right-hand side + dissipation +
  * stage update reading those tables, which must have been made from the same
@@ -173,8 +209,8 @@ bssn_status_t bssn_rk4_stage_fused(const bssn_grid_t* grid, const bssn_params_t*
  * Sharing: every call uses the same array and overwrites what the previous
  * call left there; nothing in it has to start at zero. Calls that overlap on
  * the GPU (on different streams without ordering between them) race on the
- * array; serialise them. CUDA failures are reported by the returned status
- * only (bssn_last_error does not see them). */
+ * array; serialise them. A CUDA failure is returned and also latched for
+ * bssn_last_error(), as for every other call. */
 bssn_status_t bssn_rk4_stage_noalloc(const bssn_grid_t* grid, const bssn_params_t* params,
                                      bssn_precision_t prec, int stage, double dt, const double* y0,
                                      const double* ys, double* acc, double* ynext, void* stream);
@@ -217,7 +253,7 @@ bssn_status_t bssn_rk3_step(const bssn_grid_t* grid, const bssn_params_t* params
 /* ---------------------------------------------------------------- batched patches
  * Many independent uneven grid patches advanced by one RK4 step per call,
  * the single-GPU analogue of the block-structured (AMR / multi-block) grids
- * the paper plans for (Sec. 4; tile selection prior art, Sec. 2.6). Each
+ * the paper plans for (Sec. 4; tile selection prior art, Sec. 2.7.1). Each
  * patch has static ghosts: before every stage they are copied from the
  * patch's t = 0 values. There is no exchange between patches. */
 typedef struct bssn_plan bssn_plan_t;
@@ -375,7 +411,7 @@ bssn_status_t bssn_sommerfeld_rhs(const bssn_grid_t* grid, const bssn_params_t* 
                                   const double* state, double* rhs, void* stream);
 
 /* ---------------------------------------------------------------- CFD benchmark (SOLA Navier-Stokes)
- * The paper's second workload (Sec. 4, "CFD with Chemora and Physis"): the
+ * The paper's second workload (Sec. 3.2, "CFD with Chemora and Physis"): the
  * incompressible Navier-Stokes equations by the SOLA scheme in single
  * precision, as three stencil kernels - explicit velocity update, iterative
  * mass conservation, boundary condition. Arrays u, v, w, p are DEVICE
@@ -535,12 +571,22 @@ bssn_status_t bssn_algebraic_constraints(const bssn_grid_t* grid, const bssn_par
  * full 24 * grid->var_stride doubles of the padded layout, ghosts included)
  * with the grid, the parameters, the time t and the step count in one file
  * at `path` (overwritten), followed by a 64-bit FNV-1a hash of the data.
+ * The file is written under a temporary name next to `path` (suffix
+ * ".tmp<pid>"), flushed to disk and renamed over `path` only when every write
+ * succeeded: a failed write returns an error, removes the temporary file and
+ * leaves any previous checkpoint at `path` as it was.
  * bssn_checkpoint_read restores grid, params, t and step, and - if `state`
  * (HOST, `capacity` doubles) is not NULL - the data. A resumed evolution
  * continues from exactly the same bits. Both return BSSN_ERR_INVALID_ARG
  * for NULL or invalid arguments, a file that cannot be opened, written or
  * read in full, a foreign format (magic, byte order, version), an invalid
- * grid, too small a capacity or a hash mismatch. Host only; no GPU work. */
+ * grid, parameters that the stepping entry points would reject (order,
+ * ghost width for that order, gauge switches, non-finite or negative
+ * constants), a non-finite t, too small a capacity or a hash mismatch.
+ * Resuming a static-boundary evolution (fill mode 1, bc = 1): its ghost
+ * cells hold their t = 0 values at every step, and they are part of the
+ * saved state, so a copy of the loaded state serves as ghost_src (mode 1
+ * reads only ghost cells of its source). Host only; no GPU work. */
 bssn_status_t bssn_checkpoint_write(const char* path, const bssn_grid_t* grid, const bssn_params_t* params, double t,
                                     long long step, const double* state);
 bssn_status_t bssn_checkpoint_read(const char* path, bssn_grid_t* grid, bssn_params_t* params, double* t,
@@ -567,9 +613,24 @@ bssn_status_t bssn_psi4(const bssn_grid_t* grid, const bssn_params_t* params, co
                         const double* origin, double* psi_re, double* psi_im, double* inv_re, double* inv_im,
                         double* E, double* B, void* work, unsigned long long work_bytes, void* stream);
 
-/* Measured issue rates of this device's floating-point pipes (a short
- * microbenchmark, ~20 ms). out[0] = FP64 FMA/s, out[1] = FP32 FMA/s,
- * out[2] = FP64 add/s. HOST array. Synchronizes the device. */
+/* Failure-path probe of the tensor-core (tcgen05) kernels: one CTA runs
+ * their bounded-wait and abort code with a barrier that nothing arrives at.
+ * One role waits with the given limit (1 us .. 1 s), gives up and raises
+ * the CTA's abort flag; a second role, waiting with the kernels' default
+ * 2 s limit, is released by that flag; the MMA in flight is waited for and
+ * TMEM is freed. Returns BSSN_ERR_TIMEOUT (the expected outcome) and sets
+ * *flags (HOST): bit 0 = TMEM freed, bit 1 = the second role left on the
+ * abort flag. Nothing traps or faults; the device stays usable.
+ * Synchronizes the device. */
+bssn_status_t bssn_probe_wait_timeout(unsigned long long limit_ns, unsigned int* flags);
+
+/* Measured rates of this device's floating-point pipes (a microbenchmark of
+ * independent multiply-add or add chains at full occupancy, ~0.3 s).
+ * out[0] = FP64 FMA/s, out[1] = FP32 FMA/s, out[2] = FP64 add/s (whole
+ * device, best of three launches); out[3..5] = the same operations per SM
+ * clock cycle and SM (median over SMs, from the SM cycle counter); out[6..8]
+ * = the SM clock in MHz during each of the three measurements (cycle counter
+ * against the global timer). HOST array of 9 doubles. Synchronizes. */
 bssn_status_t bssn_probe_fp_rates(double* out);
 
 /* Measures the rate of back-to-back dense BF16 tcgen05 MMAs (M = 128, K = 16,

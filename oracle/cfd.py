@@ -1,5 +1,5 @@
 """Incompressible Navier-Stokes on a staggered grid by the SOLA scheme: the
-three-kernel CFD benchmark of the paper's Sec. 4 ("CFD with Chemora and
+three-kernel CFD benchmark of the paper's Sec. 3.2 ("CFD with Chemora and
 Physis": an explicit velocity update, an iterative mass-conservation kernel
 that updates velocity and pressure, and a boundary kernel applied after each
 iteration; single precision; 256^3 per GPU).

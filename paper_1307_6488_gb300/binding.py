@@ -11,9 +11,10 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libbssn.so")
+# BSSN_BOUNDS_CHECK=1 selects the bounds-check build of the same library
+LIB_PATH = os.path.join(HERE, "libbssn_check.so" if os.environ.get("BSSN_BOUNDS_CHECK") == "1" else "libbssn.so")
 
-OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_NOMEM = range(7)
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_NOMEM, ERR_BOUNDS = range(8)
 FP64, FP32_RHS = 0, 1
 NVAR = 24
 
@@ -131,6 +132,43 @@ def last_error():
 
 def clear_error():
     lib().bssn_clear_error()
+
+
+def bounds_check_enabled():
+    L = lib()
+    L.bssn_bounds_check_enabled.restype = ctypes.c_int
+    return bool(L.bssn_bounds_check_enabled())
+
+
+def bounds_violations(stream=None):
+    """bssn_bounds_violations: (status, count) since the last call, cleared."""
+    L = lib()
+    L.bssn_bounds_violations.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), _p]
+    L.bssn_bounds_violations.restype = ctypes.c_int
+    c = ctypes.c_ulonglong(0)
+    st = L.bssn_bounds_violations(ctypes.byref(c), _stream(stream))
+    return st, c.value
+
+
+def check_device(stream=None):
+    """bssn_check_device: synchronizes the stream; raises BssnError with
+    ERR_TIMEOUT if a bounded wait of a tiled FP32-RHS stage kernel gave up
+    since the last check."""
+    L = lib()
+    L.bssn_check_device.argtypes = [_p]
+    L.bssn_check_device.restype = ctypes.c_int
+    _check(L.bssn_check_device(_stream(stream)), "bssn_check_device")
+
+
+def test_conversions(din, fin, f_bits, f_hw, d_bits, d_hw, stream=None):
+    """bssn_test_conversions: single/double conversions by the library's
+    integer-pipe code and by the hardware instruction, side by side."""
+    L = lib()
+    L.bssn_test_conversions.argtypes = [ctypes.c_longlong, _p, _p, _p, _p, _p, _p, _p]
+    L.bssn_test_conversions.restype = ctypes.c_int
+    n = din.numel()
+    _check(L.bssn_test_conversions(n, _ptr(din), _ptr(fin), _ptr(f_bits), _ptr(f_hw), _ptr(d_bits), _ptr(d_hw),
+                                   _stream(stream)), "bssn_test_conversions")
 
 
 def work_bytes(grid, params, prec=FP64):
@@ -490,10 +528,22 @@ def _ckp_lib():
     return L
 
 
+def probe_wait_timeout(limit_ns):
+    """bssn_probe_wait_timeout: returns (status, flags) without raising."""
+    L = lib()
+    L.bssn_probe_wait_timeout.argtypes = [ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_uint)]
+    L.bssn_probe_wait_timeout.restype = ctypes.c_int
+    flags = ctypes.c_uint(0)
+    st = L.bssn_probe_wait_timeout(limit_ns, ctypes.byref(flags))
+    return st, flags.value
+
+
 def probe_fp_rates():
-    out = np.zeros(3)
+    out = np.zeros(9)
     _check(lib().bssn_probe_fp_rates(out.ctypes.data_as(_p)), "probe_fp_rates")
-    return dict(fp64_fma_per_s=out[0], fp32_fma_per_s=out[1], fp64_add_per_s=out[2])
+    return dict(fp64_fma_per_s=out[0], fp32_fma_per_s=out[1], fp64_add_per_s=out[2],
+                fp64_fma_per_clk_sm=out[3], fp32_fma_per_clk_sm=out[4], fp64_add_per_clk_sm=out[5],
+                sm_mhz_fp64_fma=out[6], sm_mhz_fp32_fma=out[7], sm_mhz_fp64_add=out[8])
 
 
 def _nbytes(x):

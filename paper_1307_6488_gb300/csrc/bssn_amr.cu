@@ -63,6 +63,7 @@
 #include <vector>
 
 #include "../../include/bssn.h"
+#include "bssn_launch.h"
 #include "bssn_patch.cuh"
 
 using namespace bssn;
@@ -121,6 +122,9 @@ __global__ void __launch_bounds__(ENTRY_THREADS) ka_copy(const CopyEntry* __rest
                                                          const PatchDev* __restrict__ P, int which) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const CopyEntry e = E[t];
+    if (!in_range(e.dst_off, e.dst_off, padded_points(P[e.dst].L)) ||
+        !in_range(e.src_off, e.src_off, padded_points(P[e.src].L)))
+      continue;
     double* u = P[e.dst].buf[which] + e.dst_off;
     const double* s = P[e.src].buf[which] + e.src_off;
     const long long vd = P[e.dst].L.vs, vsrc = P[e.src].L.vs;
@@ -134,6 +138,7 @@ __global__ void __launch_bounds__(ENTRY_THREADS) ka_static(const StaticEntry* __
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const StaticEntry e = E[t];
     const PatchDev& D = P[e.patch];
+    if (!in_range(e.off, e.off, padded_points(D.L))) continue;
     double* u = D.buf[which] + e.off;
     const double* s = D.ghost + e.off;
 #pragma unroll 4
@@ -192,6 +197,7 @@ __global__ void __launch_bounds__(ENTRY_THREADS) ka_prolong_x(const ProlongBox* 
     for (int c = 0; c < 4; ++c) {
       src[c] = map[B.map0 + ((long long)cz * B.nc[1] + cy) * B.nc[0] + cx + c];
       ok = ok && src[c].patch >= 0;
+      if (src[c].patch >= 0) ok = ok && in_range(src[c].off, src[c].off, padded_points(P[src[c].patch].L));
     }
 #pragma unroll 1
     for (int v = 0; v < NV; ++v) {
@@ -235,6 +241,7 @@ __global__ void __launch_bounds__(ENTRY_THREADS) ka_prolong_y(const ProlongBox* 
     double w[4];
     prolong_w(odd, w);
     const long long p1 = B.x1_0 + ((long long)cz * B.nc[1] + cy) * B.fx[0] + i;
+    if (!in_range(p1, p1 + 3 * B.fx[0], n1)) continue;
 #pragma unroll 4
     for (int f = 0; f < nf * NV; ++f) {
       const double* x = X1 + (long long)f * n1 + p1;
@@ -257,6 +264,7 @@ __global__ void __launch_bounds__(ENTRY_THREADS) ka_prolong_z(const ProlongEntry
     prolong_w(odd, w);
     const long long plane = (long long)B.fx[1] * B.fx[0];
     const long long p2 = B.x2_0 + (cz * (long long)B.fx[1] + e.j) * B.fx[0] + e.i;
+    if (!in_range(p2, p2 + 3 * plane, n2)) continue;
 #pragma unroll 4
     for (int f = 0; f < 5 * NV; ++f) {
       const double* x = X2 + (long long)f * n2 + p2;
@@ -282,6 +290,7 @@ __global__ void __launch_bounds__(ENTRY_THREADS) ka_regrid_z(const ProlongEntry*
     const long long plane = (long long)B.fx[1] * B.fx[0];
     const long long p2 = B.x2_0 + (cz * (long long)B.fx[1] + e.j) * B.fx[0] + e.i;
     const PatchDev& D = P[e.dst];
+    if (!in_range(p2, p2 + 3 * plane, n2) || !in_range(e.dst_off, e.dst_off, padded_points(D.L))) continue;
 #pragma unroll 4
     for (int v = 0; v < NV; ++v) {
       const double* x = X2 + (long long)v * n2 + p2;
@@ -304,6 +313,7 @@ __global__ void __launch_bounds__(ENTRY_THREADS) ka_regrid_copy(const RegridCopy
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const RegridCopy e = E[t];
     const PatchDev& D = P[e.dst];
+    if (!in_range(e.dst_off, e.dst_off, padded_points(D.L))) continue;
 #pragma unroll 4
     for (int v = 0; v < NV; ++v) D.buf[0][v * D.L.vs + e.dst_off] = __ldg(e.src + v * e.src_vs);
   }
@@ -317,6 +327,7 @@ __global__ void __launch_bounds__(ENTRY_THREADS) ka_prolong_fill(const ProlongEn
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const ProlongEntry e = E[t];
     const PatchDev& D = P[e.dst];
+    if (!in_range(e.dst_off, e.dst_off, padded_points(D.L))) continue;
     double* u = D.buf[which] + e.dst_off;
 #pragma unroll 2
     for (int v = 0; v < NV; ++v) {
@@ -339,6 +350,9 @@ __global__ void __launch_bounds__(ENTRY_THREADS) ka_restrict(const RestrictEntry
     const RestrictEntry e = E[t];
     const PatchDev& F = P[e.fine];
     const PatchDev& C = P[e.coarse];
+    if (!in_range(e.fine_off, e.fine_off + 3 * (F.L.sz + F.L.sy + 1), padded_points(F.L)) ||
+        !in_range(e.coarse_off, e.coarse_off, padded_points(C.L)))
+      continue;
 #pragma unroll 1
     for (int v = 0; v < NV; ++v) {
       const double* u = F.buf[0] + v * F.L.vs + e.fine_off;
@@ -396,6 +410,7 @@ __global__ void __launch_bounds__(ENTRY_THREADS) ka_radiative(const RadEntry* __
     const PatchDev& D = P[e.patch];
     const Layout& L = D.L;
     const long long p = e.i + e.j * L.sy + e.k * L.sz;
+    if (!in_range(p, p, padded_points(L))) continue;
     const double inv_r = 1.0 / sqrt(e.x * e.x + e.y * e.y + e.z * e.z);
 #pragma unroll 1
     for (int v = 0; v < NV; ++v) {
@@ -830,6 +845,10 @@ cudaError_t enqueue_level(bssn_amr* A, int l, int m, cudaStream_t s) {
 bool a16(const void* p) { return p && ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace
+
+namespace bssn {
+cudaError_t bounds_take_amr(unsigned long long* out) { return bounds_take_local(out); }
+}  // namespace bssn
 
 extern "C" {
 

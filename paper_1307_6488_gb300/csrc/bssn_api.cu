@@ -2,13 +2,19 @@
 // reductions, the RK4 step driver and the floating-point rate probe.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <type_traits>
+#include <vector>
 
 #include "../../include/bssn.h"
+#include "bssn_bounds.cuh"
 #include "bssn_common.cuh"
+#include "bssn_cvt.cuh"
 #include "bssn_launch.h"
 
 using namespace bssn;
@@ -25,6 +31,12 @@ bssn_status_t latch(cudaError_t e) {
 }
 
 bool aligned16(const void* p) { return p && ((uintptr_t)p & 15u) == 0; }
+
+__device__ __forceinline__ uint64_t tc_global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 int required_ghost(int order) { return order / 2 + 1; }
 
@@ -65,9 +77,11 @@ struct WorkLayout {
 
 WorkLayout work_layout(const bssn_grid_t& G, const bssn_params_t& P) {
   Layout L = make_layout(G);
+  const Layout32 L32 = make_layout32(G);
   WorkLayout W;
   const size_t dbl = diff_doubles(L, P.fd_order / 2);
-  const size_t f32 = (2 * (size_t)NV * L.vs + 2 * dbl / 2 + 1) / 2;  // floats -> doubles, rounded up
+  // two single-precision copies and the 22 D_x / D_y tables, Layout32
+  const size_t f32 = ((2 * (size_t)NV + 2 * NM) * (size_t)L32.vs + 1) / 2;  // floats -> doubles, rounded up
   W.tables = dbl > f32 ? dbl : f32;
   W.partials = (size_t)con_blocks(L) * 14;
   W.finals = 16;
@@ -76,10 +90,11 @@ WorkLayout work_layout(const bssn_grid_t& G, const bssn_params_t& P) {
 }
 
 struct WorkPtrs {
-  void* dX;       // difference tables (double or float)
+  void* dX;       // difference tables (FP64 form)
   void* dY;
-  float* f32;     // single-precision state copy (FP32 form)
+  float* f32;     // single-precision state copy (FP32 form, Layout32)
   float* f32b;    // a second one (the next stage's input, written by the stage before)
+  float* tab32;   // D_x then D_y tables of the 11 mixed variables (FP32 form, Layout32)
   double* dX64;   // double tables (constraints)
   double* dY64;
   double* part;
@@ -98,14 +113,15 @@ WorkPtrs work_ptrs(void* work, const bssn_grid_t& G, const bssn_params_t& P, bss
   if (prec == BSSN_FP64) {
     w.f32 = nullptr;
     w.f32b = nullptr;
+    w.tab32 = nullptr;
     w.dX = w.dX64;
     w.dY = w.dY64;
   } else {
+    const Layout32 L32 = make_layout32(G);
     w.f32 = (float*)base;
-    w.f32b = w.f32 + (size_t)NV * L.vs;
-    float* t = w.f32b + (size_t)NV * L.vs;
-    w.dX = t;
-    w.dY = t + NM * H * L.vs;
+    w.f32b = w.f32 + (size_t)NV * L32.vs;
+    w.tab32 = w.f32b + (size_t)NV * L32.vs;
+    w.dX = w.dY = nullptr;
   }
   w.part = base + W.tables;
   w.finals = w.part + W.partials;
@@ -113,26 +129,41 @@ WorkPtrs work_ptrs(void* work, const bssn_grid_t& G, const bssn_params_t& P, bss
   return w;
 }
 
-// Difference tables of ys (for the FP32 form: first the single-precision copy).
+// Difference tables of ys (for the FP32 form: first the single-precision
+// copy, then its D_x / D_y tables).
 cudaError_t run_diffs(int order, bssn_precision_t prec, const bssn_grid_t& G, const double* ys, const WorkPtrs& w,
                       cudaStream_t s) {
   const Layout L = make_layout(G);
-  const void* src = ys;
   if (prec == BSSN_FP32_RHS) {
-    cudaError_t e = launch_to_f32(L, ys, w.f32, s);
+    const Layout32 L32 = make_layout32(G);
+    cudaError_t e = launch_to_f32t(L, L32, ys, w.f32, s);
     if (e != cudaSuccess) return e;
-    src = w.f32;
+    return order == 4 ? launch_d1tab32<4>(L32, G, w.f32, w.tab32, s) : launch_d1tab32<8>(L32, G, w.f32, w.tab32, s);
   }
-  return order == 4 ? launch_diffs<4>(L, G, prec, src, w.dX, w.dY, s)
-                    : launch_diffs<8>(L, G, prec, src, w.dX, w.dY, s);
+  return order == 4 ? launch_diffs<4>(L, G, prec, ys, w.dX, w.dY, s)
+                    : launch_diffs<8>(L, G, prec, ys, w.dX, w.dY, s);
+}
+
+// The tiled FP32-RHS stage on the single-precision copy ys32 and the tables
+// in work (out32: nullable single-precision copy of the output).
+cudaError_t fused32(int order, const bssn_grid_t& G, const bssn_params_t& P, const RK& rk, const double* ys,
+                    const float* ys32, const double* y0, double* acc, double* out, float* out32, const float* tab32,
+                    int mode, cudaStream_t s) {
+  const Layout L = make_layout(G);
+  const Layout32 L32 = make_layout32(G);
+  const Gauge gz = make_gauge(P);
+  const Stage32Ptrs S{ys, ys32, y0, acc, out, out32};
+  return order == 4 ? launch_stage32<4>(L, L32, G, P.ko_eps, gz, rk, S, tab32, mode, s)
+                    : launch_stage32<8>(L, L32, G, P.ko_eps, gz, rk, S, tab32, mode, s);
 }
 
 cudaError_t run_fused(int order, bssn_precision_t prec, const bssn_grid_t& G, const bssn_params_t& P, const RK& rk,
                       const double* ys, const double* y0, double* acc, double* out, const WorkPtrs& w, int mode,
                       cudaStream_t s) {
+  if (prec == BSSN_FP32_RHS) return fused32(order, G, P, rk, ys, w.f32, y0, acc, out, nullptr, w.tab32, mode, s);
   const Layout L = make_layout(G);
   const Gauge gz = make_gauge(P);
-  StageArgs A{prec == BSSN_FP64 ? (const void*)ys : (const void*)w.f32, ys, y0, acc, out, w.dX, w.dY};
+  StageArgs A{(const void*)ys, ys, y0, acc, out, w.dX, w.dY};
   if (order == 4) return launch_stage<4>(L, G, P.ko_eps, prec, gz, rk, A, mode, s);
   return launch_stage<8>(L, G, P.ko_eps, prec, gz, rk, A, mode, s);
 }
@@ -154,15 +185,12 @@ cudaError_t run_stage32(int order, const bssn_grid_t& G, const bssn_params_t& P,
                         const double* y0, double* acc, double* out, const WorkPtrs& w, float* ys32, float* out32,
                         bool convert, cudaStream_t s) {
   const Layout L = make_layout(G);
-  cudaError_t e = convert ? launch_to_f32(L, ys, ys32, s) : cudaSuccess;
+  const Layout32 L32 = make_layout32(G);
+  cudaError_t e = convert ? launch_to_f32t(L, L32, ys, ys32, s) : cudaSuccess;
   if (e == cudaSuccess)
-    e = order == 4 ? launch_diffs<4>(L, G, BSSN_FP32_RHS, ys32, w.dX, w.dY, s)
-                   : launch_diffs<8>(L, G, BSSN_FP32_RHS, ys32, w.dX, w.dY, s);
+    e = order == 4 ? launch_d1tab32<4>(L32, G, ys32, w.tab32, s) : launch_d1tab32<8>(L32, G, ys32, w.tab32, s);
   if (e != cudaSuccess) return e;
-  const Gauge gz = make_gauge(P);
-  StageArgs A{ys32, ys, y0, acc, out, w.dX, w.dY, out32};
-  return order == 4 ? launch_stage<4>(L, G, P.ko_eps, BSSN_FP32_RHS, gz, rk, A, 0, s)
-                    : launch_stage<8>(L, G, P.ko_eps, BSSN_FP32_RHS, gz, rk, A, 0, s);
+  return fused32(order, G, P, rk, ys, ys32, y0, acc, out, out32, w.tab32, 0, s);
 }
 
 bool prec_ok(bssn_precision_t prec) { return prec == BSSN_FP64 || prec == BSSN_FP32_RHS; }
@@ -170,8 +198,8 @@ bool prec_ok(bssn_precision_t prec) { return prec == BSSN_FP64 || prec == BSSN_F
 // ---------------------------------------------------------------- ghost fill
 // Ghost fill; u32 (nullable): the single-precision copy of u, whose ghosts
 // get the same values rounded to float.
-__global__ void __launch_bounds__(256) k_fill_ghosts(Layout L, int mode, const double* __restrict__ src, double* u,
-                                                     float* u32) {
+__global__ void __launch_bounds__(256) k_fill_ghosts(Layout L, Layout32 L32, int mode, const double* __restrict__ src,
+                                                     double* u, float* u32) {
   const long long ex = L.nx + 2LL * L.g, ey = L.ny + 2LL * L.g, ez = L.nz + 2LL * L.g;
   const long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (lin >= ex * ey * ez) return;
@@ -181,12 +209,14 @@ __global__ void __launch_bounds__(256) k_fill_ghosts(Layout L, int mode, const d
   const int k = (int)(t / ey) - L.g;
   if (i >= 0 && i < L.nx && j >= 0 && j < L.ny && k >= 0 && k < L.nz) return;
   const long long p = L.off0 + i + j * L.sy + k * L.sz;
+  const long long p32 = idx32(L32, i, j, k);
+  if (!in_range(p, p, padded_points(L)) || (u32 && !in_range(p32, p32, padded_points32(L32)))) return;
   if (mode == 1) {
 #pragma unroll 4
     for (int v = 0; v < NV; ++v) {
       const double x = __ldg(src + v * L.vs + p);
       u[v * L.vs + p] = x;
-      if (u32) u32[v * L.vs + p] = __double2float_rn(x);
+      if (u32) u32[v * L32.vs + p32] = f64_to_f32_rn(x);
     }
     return;
   }
@@ -194,11 +224,12 @@ __global__ void __launch_bounds__(256) k_fill_ghosts(Layout L, int mode, const d
   const int jj = ((j % L.ny) + L.ny) % L.ny;
   const int kk = ((k % L.nz) + L.nz) % L.nz;
   const long long q = L.off0 + ii + jj * L.sy + kk * L.sz;
+  if (!in_range(q, q, padded_points(L))) return;
 #pragma unroll 4
   for (int v = 0; v < NV; ++v) {
     const double x = u[v * L.vs + q];
     u[v * L.vs + p] = x;
-    if (u32) u32[v * L.vs + p] = __double2float_rn(x);
+    if (u32) u32[v * L32.vs + p32] = f64_to_f32_rn(x);
   }
 }
 
@@ -206,7 +237,7 @@ cudaError_t fill(const bssn_grid_t& G, int mode, const double* src, double* u, c
                  float* u32 = nullptr) {
   const Layout L = make_layout(G);
   const long long n = (G.nx + 2LL * G.ghost) * (G.ny + 2LL * G.ghost) * (G.nz + 2LL * G.ghost);
-  k_fill_ghosts<<<(unsigned int)((n + 255) / 256), 256, 0, s>>>(L, mode, src, u, u32);
+  k_fill_ghosts<<<(unsigned int)((n + 255) / 256), 256, 0, s>>>(L, make_layout32(G), mode, src, u, u32);
   return cudaGetLastError();
 }
 
@@ -294,39 +325,81 @@ __global__ void __launch_bounds__(CON_THREADS) k_algebraic(Layout L, const doubl
 }
 
 // ---------------------------------------------------------------- FP rate probe
-constexpr int PROBE_CHAINS = 8;
-__global__ void k_probe_dfma(double* out, double b, double c, int iters) {
-  double a[PROBE_CHAINS];
-  for (int j = 0; j < PROBE_CHAINS; ++j) a[j] = threadIdx.x * 1e-3 + j;
-  for (int i = 0; i < iters; ++i)
+// Independent multiply-add (or add) chains per thread, full occupancy. Each
+// block records its SM, the SM clock counter and the global timer before and
+// after its loop, so that the host gets operations per SM clock (independent
+// of the clock the GPU happened to run at) and the clock itself.
+constexpr int PROBE_CHAINS = 16;
+constexpr int PROBE_THREADS = 256;
+
+template <int KIND>  // 0: FP64 FMA, 1: FP32 FMA, 2: FP64 add
+__global__ void __launch_bounds__(PROBE_THREADS) k_probe(double* out, unsigned long long* tm, double b, double c,
+                                                         int iters) {
+  using T = typename std::conditional<KIND == 1, float, double>::type;
+  T a[PROBE_CHAINS];
+  const T bb = (T)b, cc = (T)c;
 #pragma unroll
-    for (int j = 0; j < PROBE_CHAINS; ++j) a[j] = fma(a[j], b, c);
-  double s = 0;
+  for (int j = 0; j < PROBE_CHAINS; ++j) a[j] = (T)(threadIdx.x * 1e-3 + j);
+  __syncthreads();
+  const unsigned long long c0 = clock64();
+  const uint64_t t0 = tc_global_ns();
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < PROBE_CHAINS; ++j) {
+      if (KIND == 2)
+        a[j] = a[j] + bb;
+      else
+        a[j] = fma(a[j], bb, cc);
+    }
+  }
+  __syncthreads();
+  const unsigned long long c1 = clock64();
+  const uint64_t t1 = tc_global_ns();
+  T s = 0;
+#pragma unroll
   for (int j = 0; j < PROBE_CHAINS; ++j) s += a[j];
-  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+  out[blockIdx.x * blockDim.x + threadIdx.x] = (double)s;
+  if (threadIdx.x == 0) {
+    unsigned int sm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    unsigned long long* r = tm + 5ull * blockIdx.x;
+    r[0] = sm;
+    r[1] = c0;
+    r[2] = c1;
+    r[3] = t0;
+    r[4] = t1;
+  }
 }
-__global__ void k_probe_dadd(double* out, double b, double c, int iters) {
-  double a[PROBE_CHAINS];
-  for (int j = 0; j < PROBE_CHAINS; ++j) a[j] = threadIdx.x * 1e-3 + j;
-  for (int i = 0; i < iters; ++i)
-#pragma unroll
-    for (int j = 0; j < PROBE_CHAINS; ++j) a[j] = a[j] + b;
-  double s = 0;
-  for (int j = 0; j < PROBE_CHAINS; ++j) s += a[j];
-  out[blockIdx.x * blockDim.x + threadIdx.x] = s + c;
-}
-__global__ void k_probe_ffma(double* out, float b, float c, int iters) {
-  float a[PROBE_CHAINS];
-  for (int j = 0; j < PROBE_CHAINS; ++j) a[j] = threadIdx.x * 1e-3f + j;
-  for (int i = 0; i < iters; ++i)
-#pragma unroll
-    for (int j = 0; j < PROBE_CHAINS; ++j) a[j] = fmaf(a[j], b, c);
-  float s = 0;
-  for (int j = 0; j < PROBE_CHAINS; ++j) s += a[j];
-  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+
+// Both conversion paths on the same inputs (self-test of bssn_cvt.cuh).
+__global__ void k_test_conversions(long long n, const double* __restrict__ din, const float* __restrict__ fin,
+                                   float* f_bits, float* f_hw, double* d_bits, double* d_hw) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  f_bits[i] = f64_to_f32_rn(din[i]);
+  f_hw[i] = __double2float_rn(din[i]);
+  double d;
+  f32_to_f64_vec<1>(fin + i, &d);
+  d_bits[i] = d;
+  d_hw[i] = (double)fin[i];
 }
 
 }  // namespace
+
+namespace bssn {
+bssn_status_t latch_cuda(cudaError_t e) { return latch(e); }
+
+bool grid_params_valid(const bssn_grid_t* grid, const bssn_params_t* params) {
+  return grid_ok(grid) && params_ok(grid, params);
+}
+
+cudaError_t rk4_stage_on_work(void* work, const bssn_grid_t& G, const bssn_params_t& P, bssn_precision_t prec,
+                              int stage, double dt, const double* y0, const double* ys, double* acc, double* ynext,
+                              cudaStream_t s) {
+  const WorkPtrs w = work_ptrs(work, G, P, prec);
+  return run_stage(P.fd_order, prec, G, P, make_rk(stage, dt), ys, y0, acc, ynext, w, 0, s);
+}
+}  // namespace bssn
 
 // =================================================================== C ABI
 extern "C" {
@@ -340,11 +413,54 @@ const char* bssn_status_string(bssn_status_t s) {
     case BSSN_ERR_TIMEOUT: return "device wait timed out";
     case BSSN_ERR_UNSUPPORTED: return "unsupported";
     case BSSN_ERR_NOMEM: return "out of memory";
+    case BSSN_ERR_BOUNDS: return "index out of bounds (bounds-check build)";
   }
   return "unknown status";
 }
 
 bssn_status_t bssn_last_error(void) { return (bssn_status_t)g_last_error.load(); }
+
+bssn_status_t bssn_test_conversions(long long n, const double* din, const float* fin, float* f_bits, float* f_hw,
+                                    double* d_bits, double* d_hw, void* stream) {
+  if (n < 0 || n > (1LL << 40)) return BSSN_ERR_INVALID_ARG;
+  if (n == 0) return BSSN_OK;
+  if (!aligned16(din) || !aligned16(fin) || !aligned16(f_bits) || !aligned16(f_hw) || !aligned16(d_bits) ||
+      !aligned16(d_hw))
+    return BSSN_ERR_INVALID_ARG;
+  k_test_conversions<<<(unsigned int)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, din, fin, f_bits, f_hw,
+                                                                                     d_bits, d_hw);
+  return latch(cudaGetLastError());
+}
+
+int bssn_bounds_check_enabled(void) { return kBoundsCheck ? 1 : 0; }
+
+bssn_status_t bssn_bounds_violations(unsigned long long* count, void* stream) {
+  if (!count) return BSSN_ERR_INVALID_ARG;
+  *count = 0;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  unsigned long long total = 0, c = 0;
+  cudaError_t (*takes[])(unsigned long long*) = {bounds_take_local,       bounds_take_order<4>, bounds_take_order<8>,
+                                                 bounds_take_stage32<4>, bounds_take_stage32<8>, bounds_take_batch,
+                                                 bounds_take_amr,        bounds_take_cfd};
+  for (auto take : takes) {
+    if (e != cudaSuccess) break;
+    e = take(&c);
+    total += c;
+  }
+  if (e != cudaSuccess) return latch(e);
+  *count = total;
+  return total ? BSSN_ERR_BOUNDS : BSSN_OK;
+}
+
+bssn_status_t bssn_check_device(void* stream) {
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return latch(e);
+  unsigned int w4 = 0, w8 = 0;
+  e = stage32_take_error<4>(&w4);
+  if (e == cudaSuccess) e = stage32_take_error<8>(&w8);
+  if (e != cudaSuccess) return latch(e);
+  return (w4 | w8) ? BSSN_ERR_TIMEOUT : BSSN_OK;
+}
 void bssn_clear_error(void) { g_last_error.store(BSSN_OK); }
 
 unsigned long long bssn_work_bytes(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec) {
@@ -393,9 +509,7 @@ bssn_status_t bssn_rk4_stage(const bssn_grid_t* grid, const bssn_params_t* param
     return BSSN_ERR_INVALID_ARG;
   if (ynext == ys || ynext == acc || acc == ys || acc == y0) return BSSN_ERR_INVALID_ARG;
   if (work_bytes < work_layout(*grid, *params).total_bytes) return BSSN_ERR_INVALID_ARG;
-  const WorkPtrs w = work_ptrs(work, *grid, *params, prec);
-  return latch(run_stage(params->fd_order, prec, *grid, *params, make_rk(stage, dt), ys, y0, acc, ynext, w, 0,
-                         (cudaStream_t)stream));
+  return latch(rk4_stage_on_work(work, *grid, *params, prec, stage, dt, y0, ys, acc, ynext, (cudaStream_t)stream));
 }
 
 bssn_status_t bssn_diff_tables(const bssn_grid_t* grid, const bssn_params_t* params, bssn_precision_t prec,
@@ -614,32 +728,86 @@ bssn_status_t bssn_probe_fp_rates(double* out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return latch(e);
-  const int threads = 256, blocks = sms * 8;
-  double* buf = nullptr;
-  e = cudaMalloc(&buf, sizeof(double) * blocks * threads);
+  void (*kerns[3])(double*, unsigned long long*, double, double, int) = {k_probe<0>, k_probe<1>, k_probe<2>};
+  int per_sm = 1;
+  for (int kind = 0; kind < 3 && e == cudaSuccess; ++kind) {
+    int b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kerns[kind], PROBE_THREADS, 0);
+    per_sm = kind == 0 ? b : std::min(per_sm, b);
+  }
   if (e != cudaSuccess) return latch(e);
+  per_sm = std::max(per_sm, 1);
+  const int blocks = sms * per_sm;
+  double* buf = nullptr;
+  unsigned long long* tm = nullptr;
+  e = cudaMalloc(&buf, sizeof(double) * blocks * PROBE_THREADS);
+  if (e == cudaSuccess) e = cudaMalloc(&tm, sizeof(unsigned long long) * 5 * blocks);
+  if (e != cudaSuccess) {
+    cudaFree(buf);
+    return latch(e);
+  }
+  std::vector<unsigned long long> h(5ull * blocks);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int iters[3] = {2048, 32768, 2048};
+  // about 40 ms per launch for the FP64 kinds at the nominal rate
+  const int iters[3] = {4096, 131072, 4096};
   for (int kind = 0; kind < 3 && e == cudaSuccess; ++kind) {
     float best = 1e30f;
+    double best_clk = 0.0, best_mhz = 0.0;
     for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
       cudaEventRecord(e0);
-      if (kind == 0) k_probe_dfma<<<blocks, threads>>>(buf, 1.0000001, 1e-9, iters[kind]);
-      if (kind == 1) k_probe_ffma<<<blocks, threads>>>(buf, 1.0000001f, 1e-9f, iters[kind]);
-      if (kind == 2) k_probe_dadd<<<blocks, threads>>>(buf, 1e-9, 0.0, iters[kind]);
+      kerns[kind]<<<blocks, PROBE_THREADS>>>(buf, tm, kind == 2 ? 1e-9 : 1.0000001, kind == 2 ? 0.0 : 1e-9,
+                                              iters[kind]);
       cudaEventRecord(e1);
       e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaMemcpy(h.data(), tm, h.size() * sizeof(unsigned long long),
+                                           cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) break;
       float ms = 0;
       cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) best = ms;
+      // per SM: operations of its blocks over the cycles and time between the
+      // first start and the last end it recorded
+      std::map<unsigned long long, std::vector<unsigned long long>> per;  // sm -> c0, c1, t0, t1, blocks
+      for (int bk = 0; bk < blocks; ++bk) {
+        const unsigned long long* r = &h[5ull * bk];
+        auto it = per.find(r[0]);
+        if (it == per.end()) {
+          per[r[0]] = {r[1], r[2], r[3], r[4], 1};
+        } else {
+          auto& v = it->second;
+          v[0] = std::min(v[0], r[1]);
+          v[1] = std::max(v[1], r[2]);
+          v[2] = std::min(v[2], r[3]);
+          v[3] = std::max(v[3], r[4]);
+          v[4] += 1;
+        }
+      }
+      std::vector<double> clk, mhz;
+      for (auto& kv : per) {
+        const auto& v = kv.second;
+        const double cyc = (double)(v[1] - v[0]), ns = (double)(v[3] - v[2]);
+        if (cyc <= 0 || ns <= 0) continue;
+        clk.push_back((double)v[4] * PROBE_THREADS * (double)iters[kind] * PROBE_CHAINS / cyc);
+        mhz.push_back(cyc / ns * 1e3);
+      }
+      if (clk.empty()) continue;
+      std::sort(clk.begin(), clk.end());
+      std::sort(mhz.begin(), mhz.end());
+      if (ms < best) {
+        best = ms;
+        best_clk = clk[clk.size() / 2];
+        best_mhz = mhz[mhz.size() / 2];
+      }
     }
-    out[kind] = (double)blocks * threads * iters[kind] * PROBE_CHAINS / (best * 1e-3);
+    out[kind] = (double)blocks * PROBE_THREADS * iters[kind] * PROBE_CHAINS / (best * 1e-3);
+    out[3 + kind] = best_clk;
+    out[6 + kind] = best_mhz;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(buf);
+  cudaFree(tm);
   return latch(e == cudaSuccess ? cudaGetLastError() : e);
 }
 

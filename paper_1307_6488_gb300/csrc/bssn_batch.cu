@@ -209,6 +209,10 @@ float time_shape(bssn_plan* pl, int b, int shape, cudaStream_t s, cudaError_t* e
 
 }  // namespace
 
+namespace bssn {
+cudaError_t bounds_take_batch(unsigned long long* out) { return bounds_take_local(out); }
+}  // namespace bssn
+
 extern "C" {
 
 bssn_status_t bssn_plan_create(bssn_plan_t** out, const bssn_block_t* blocks, int nblocks,

@@ -1,4 +1,4 @@
-// The paper's CFD benchmark (Sec. 4, "CFD with Chemora and Physis"): the
+// The paper's CFD benchmark (Sec. 3.2, "CFD with Chemora and Physis"): the
 // incompressible Navier-Stokes equations by the SOLA scheme on a staggered
 // grid in single precision, as three stencil kernels - the explicit velocity
 // update, the iterative mass conservation (velocity and pressure), and the
@@ -35,6 +35,9 @@
 #include <cstdint>
 
 #include "../../include/bssn.h"
+#include "bssn_bounds.cuh"
+
+using bssn::in_range;
 
 namespace {
 
@@ -54,6 +57,9 @@ struct Cfd {
 __host__ __device__ __forceinline__ long long cidx(const Cfd& C, int i, int j, int k) {
   return (long long)(i + 1) + (long long)(j + 1) * C.sy + (long long)(k + 1) * C.sz;
 }
+
+// entries of one padded array (the extent of every index into it)
+__host__ __device__ __forceinline__ long long cfd_extent(const Cfd& C) { return C.sz * (C.n[2] + 2LL); }
 
 // --- kernel 1: velocity ----------------------------------------------------------------------
 
@@ -106,6 +112,7 @@ __global__ void __launch_bounds__(VEL_X * VEL_Y) k_cfd_velocity(Cfd C, const flo
   const int kb = (int)blockIdx.z * VEL_Z, ke = min(kb + VEL_Z, C.n[2]);
   for (int k = kb; k < ke; ++k) {
     const long long o = cidx(C, i, j, k);
+    if (!in_range(o - C.sz, o + C.sz, cfd_extent(C))) continue;
     // every interior entry is written: the wall faces n-1 of a wall axis keep
     // their value, all other faces are advanced
     un[o] = (C.per[0] || i < C.n[0] - 1) ? velocity_face<0>(C, f, p, o) : u[o];
@@ -173,6 +180,10 @@ __global__ void __launch_bounds__(CFD_THREADS) k_cfd_mass(Cfd C, int colour, flo
     float* F[3] = {u, v, w};
     const CellFaces cf = cell_faces(C, c3, o);
     float fhi[3], flo[3];
+    const long long ext = cfd_extent(C);
+    if (!in_range(o, o, ext) || !in_range(cf.lo[0], cf.lo[0], ext) || !in_range(cf.lo[1], cf.lo[1], ext) ||
+        !in_range(cf.lo[2], cf.lo[2], ext))
+      continue;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       fhi[a] = F[a][o];
@@ -301,6 +312,11 @@ __global__ void __launch_bounds__(RB_TX * RB_TY) k_cfd_mass_rb(Cfd C, const floa
   float* D[3] = {un, vn, wn};
   const int i0 = (int)blockIdx.x * RB_TX, j0 = (int)blockIdx.y * RB_TY, k0 = (int)blockIdx.z * RB_KC;
   const int k1 = min(k0 + RB_KC, C.n[2]);
+  // the box with its one-cell halo inside the padded arrays (the same for
+  // every thread of the block, so the block leaves as a whole)
+  if (!in_range(cidx(C, i0 - 1, j0 - 1, k0 - 1),
+                cidx(C, min(i0 + RB_TX, C.n[0]), min(j0 + RB_TY, C.n[1]), k1), cfd_extent(C)))
+    return;
   // colour-0 pass: thread t < 17 (RB_TY + 2) takes colour-0 cell t % 17 of
   // halo row t / 17 (a halo row is RB_TX + 2 = 34 cells, 17 of each colour);
   // update pass: the first half of the threads take the 16 colour-1 cells of
@@ -424,6 +440,7 @@ __global__ void __launch_bounds__(CFD_THREADS) k_cfd_boundary(Cfd C, int a, floa
     const long long ib = q % eb, ic = q / eb;
     const long long base = ib * st[b] + ic * st[c];          // padded index 0 along a
     const long long g = base + (side ? (na + 1) : 0) * st[a];  // the ghost point
+    if (!in_range(base, base + (na + 1) * st[a], cfd_extent(C))) continue;
     if (C.per[a]) {
       const long long src = base + (side ? 1 : na) * st[a];
 #pragma unroll
@@ -504,6 +521,10 @@ cudaError_t boundary_all(const Cfd& C, float* u, float* v, float* w, float* p, c
 }
 
 }  // namespace
+
+namespace bssn {
+cudaError_t bounds_take_cfd(unsigned long long* out) { return bounds_take_local(out); }
+}  // namespace bssn
 
 extern "C" {
 

@@ -3,6 +3,9 @@
 // parameters, the time and the step count, in one file. Host memory only:
 // the caller copies the state off the device before writing and back after
 // reading, so a resumed evolution continues from exactly the same bits.
+// The file is written under a temporary name, flushed to disk and renamed
+// over `path` only once every write succeeded, so a failed or interrupted
+// write leaves the previous checkpoint at `path` intact.
 //
 // File layout (native little-endian, as on both host architectures):
 //   "BSSNCKP1", uint32 byte-order mark 0x01020304, uint32 format version 1,
@@ -10,13 +13,17 @@
 //   int32 fd_order; double ko_eps; int32 lapse, shift; double shift_coeff,
 //   eta; int32 advect_gauge; double t; int64 step; int64 data doubles;
 //   uint64 FNV-1a hash of the data bytes; then the data.
+#include <unistd.h>
+
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "../../include/bssn.h"
+#include "bssn_launch.h"
 
 namespace {
 
@@ -74,6 +81,7 @@ extern "C" {
 bssn_status_t bssn_checkpoint_write(const char* path, const bssn_grid_t* grid, const bssn_params_t* params, double t,
                                     long long step, const double* state) {
   if (!path || !grid || !params || !state || !grid_valid(*grid) || !std::isfinite(t)) return BSSN_ERR_INVALID_ARG;
+  if (!bssn::grid_params_valid(grid, params)) return BSSN_ERR_INVALID_ARG;
   const long long ndata = NVARS * grid->var_stride;
   Out h;
   h.b.insert(h.b.end(), MAGIC, MAGIC + 8);
@@ -98,11 +106,15 @@ bssn_status_t bssn_checkpoint_write(const char* path, const bssn_grid_t* grid, c
   h.put((int64_t)step);
   h.put((int64_t)ndata);
   h.put(fnv1a(reinterpret_cast<const unsigned char*>(state), (size_t)ndata * sizeof(double)));
-  FILE* f = std::fopen(path, "wb");
+  const std::string tmp = std::string(path) + ".tmp" + std::to_string((long long)getpid());
+  FILE* f = std::fopen(tmp.c_str(), "wb");
   if (!f) return BSSN_ERR_INVALID_ARG;
   bool ok = std::fwrite(h.b.data(), 1, h.b.size(), f) == h.b.size();
   ok = ok && std::fwrite(state, sizeof(double), (size_t)ndata, f) == (size_t)ndata;
+  ok = ok && std::fflush(f) == 0 && fsync(fileno(f)) == 0;
   ok = (std::fclose(f) == 0) && ok;
+  ok = ok && std::rename(tmp.c_str(), path) == 0;
+  if (!ok) std::remove(tmp.c_str());
   return ok ? BSSN_OK : BSSN_ERR_INVALID_ARG;
 }
 
@@ -133,7 +145,10 @@ bssn_status_t bssn_checkpoint_read(const char* path, bssn_grid_t* grid, bssn_par
             in.get(&time) && in.get(&nstep) && in.get(&ndata) && in.get(&hash);
   ok = ok && std::memcmp(magic, MAGIC, 8) == 0 && bom == BOM && version == VERSION;
   bssn_grid_t G{nx, ny, nz, ghost, dx, dy, dz, (long long)vs};
+  bssn_params_t Pm{order, eps, lapse, shift, coeff, eta, adv};
   ok = ok && grid_valid(G) && ndata == NVARS * vs;
+  // the parameters must be ones every stepping entry point accepts, and t finite
+  ok = ok && bssn::grid_params_valid(&G, &Pm) && std::isfinite(time);
   if (ok && state) {
     ok = capacity >= (unsigned long long)ndata &&
          std::fread(state, sizeof(double), (size_t)ndata, f) == (size_t)ndata &&

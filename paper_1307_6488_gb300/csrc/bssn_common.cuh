@@ -57,6 +57,51 @@ inline Layout make_layout(const bssn_grid_t& G) {
   return L;
 }
 
+// The single-precision copies (state and D_x/D_y tables) of the FP32-RHS
+// form have their own padded layout, so that TMA can address them: rows of
+// sy floats (a multiple of 4, i.e. 16 bytes), interior x starting at column
+// xoff (a multiple of 8), the same ghost width g in y and z as the double
+// state, variables vs floats apart (a multiple of 32).
+struct Layout32 {
+  int nx, ny, nz, g, xoff;
+  long long sy, sz, vs, off0;
+};
+
+inline Layout32 make_layout32(const bssn_grid_t& G) {
+  Layout32 L;
+  L.nx = G.nx;
+  L.ny = G.ny;
+  L.nz = G.nz;
+  L.g = G.ghost;
+  L.xoff = G.ghost <= 8 ? 8 : (G.ghost + 7) / 8 * 8;
+  L.sy = ((long long)L.xoff + G.nx + G.ghost + 3) / 4 * 4;
+  L.sz = L.sy * (G.ny + 2LL * G.ghost);
+  L.vs = (L.sz * (G.nz + 2LL * G.ghost) + 31) / 32 * 32;
+  L.off0 = L.xoff + G.ghost * (L.sy + L.sz);
+  return L;
+}
+
+// padded points of one variable (the extent every index into it must respect)
+__host__ __device__ __forceinline__ long long padded_points(const Layout& L) {
+  return (L.nx + 2LL * L.g) * (L.ny + 2LL * L.g) * (L.nz + 2LL * L.g);
+}
+__host__ __device__ __forceinline__ long long padded_points32(const Layout32& L) { return L.sz * (L.nz + 2LL * L.g); }
+
+// index of point (i, j, k) (ghosts included: i in [-g, n + g))
+__host__ __device__ __forceinline__ long long idx32(const Layout32& L, int i, int j, int k) {
+  return L.off0 + i + j * L.sy + k * L.sz;
+}
+
+// Pointers of one launch of the tiled FP32-RHS stage kernel.
+struct Stage32Ptrs {
+  const double* ys64;  // stage input, double (W for 1/W; the RK3 combination)
+  const float* ys32;   // the same, single precision, Layout32 (centre values of gt and beta)
+  const double* y0;
+  double* acc;
+  double* out;   // ynext (stages) or the right-hand side (MODE 1)
+  float* out32;  // stages: single-precision copy of ynext in Layout32 (nullable)
+};
+
 // Finite-difference weights (exact rationals) per accuracy order p:
 //   first derivative  d u  ~ sum_{a=1}^{p/2} W1[a] (u_a - u_-a) / h
 //   second derivative dd u ~ sum_{a=1}^{p/2} W2[a] (u_a + u_-a - 2 u_0) / h^2

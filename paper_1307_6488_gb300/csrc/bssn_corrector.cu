@@ -829,6 +829,57 @@ __global__ void __launch_bounds__(128, 1) k_mma_rate(int iters, unsigned long lo
   if (warp == 0) tc::tmem_dealloc(taddr, 256);
 }
 
+// ---------------------------------------------------------------- failure-path probe
+// The bounded waits and the abort handling of the warp-specialised tcgen05
+// kernels, made to run out on purpose: warp 0 allocates TMEM; warp 1 issues
+// one MMA (committed to `mma_done`), then waits with the caller's short limit
+// on a barrier that nothing arrives at, gives up, records the timeout and
+// raises the CTA abort flag, and waits (bounded) for its MMA before TMEM is
+// released; warp 2 waits on a second such barrier with the kernels' default
+// 2 s limit and is released by the abort flag instead. Warp 0 frees TMEM.
+// done: bit 0 = TMEM freed, bit 1 = warp 2 left because of the abort.
+__global__ void __launch_bounds__(96, 1) k_wait_timeout_probe(unsigned long long limit_ns, unsigned int* err,
+                                                               unsigned int* done) {
+  __shared__ __align__(1024) uint8_t ops[PROBE_A + 32 * 32];
+  __shared__ uint64_t bars[3];  // 0 and 1: never arrived at; 2: MMA completion
+  __shared__ uint32_t slot;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < (int)sizeof(ops) / 4; i += blockDim.x) ((uint32_t*)ops)[i] = 0u;
+  tc::fence_proxy_async();
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int b = 0; b < 3; ++b) tc::mbar_init(&bars[b], 1);
+    tc::mbar_fence_init();
+  }
+  if (warp == 0) tc::tmem_alloc(&slot, 32);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = slot;
+  if (warp == 1 && lane == 0) {
+    const uint64_t ad = tc::smem_desc(tc::smem_u32(ops), 2048, 128, tc::SWZ_NONE);
+    const uint64_t bd = tc::smem_desc(tc::smem_u32(ops + PROBE_A), 32 * 16, 128, tc::SWZ_NONE);
+    tc::mma_bf16(taddr, ad, bd, tc::idesc_bf16_f32(128, 32), 0u);
+    tc::mma_commit(&bars[2]);
+    if (!tc::mbar_wait_or_abort(&bars[0], 0, &abort_flag, limit_ns)) {
+      if (!abort_flag) atomicOr(err, 1u);
+      abort_flag = 1;
+    }
+    tc::mbar_wait(&bars[2], 0);  // the MMA in flight lands before TMEM goes
+  }
+  if (warp == 2 && lane == 0) {
+    if (!tc::mbar_wait_or_abort(&bars[1], 0, &abort_flag) && abort_flag) atomicOr(done, 2u);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(taddr, 32);
+    if (lane == 0) atomicOr(done, 1u);
+  }
+}
+
 // ---------------------------------------------------------------- host helpers
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -1395,6 +1446,25 @@ bssn_status_t bssn_corrector_apply(bssn_corrector_t* c, const bssn_grid_t* grid,
     e = cudaGetLastError();
   }
   return status_of(c, e, s);
+}
+
+// Runs the failure-path probe once (one CTA) and reports what it did.
+bssn_status_t bssn_probe_wait_timeout(unsigned long long limit_ns, unsigned int* flags) {
+  if (!flags || limit_ns < 1000ull || limit_ns > 1000000000ull) return BSSN_ERR_INVALID_ARG;
+  unsigned int* words = nullptr;
+  cudaError_t e = cudaMalloc(&words, 2 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(words, 0, 2 * sizeof(unsigned int));
+  if (e == cudaSuccess) {
+    k_wait_timeout_probe<<<1, 96>>>(limit_ns, words, words + 1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  unsigned int h[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(h, words, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(words);
+  if (e != cudaSuccess) return BSSN_ERR_CUDA;
+  *flags = h[1];
+  return h[0] ? BSSN_ERR_TIMEOUT : BSSN_OK;
 }
 
 // Measured dense BF16 rate (TFLOP/s, all SMs) of back-to-back M=128 K=16

@@ -8,8 +8,6 @@
 // instructions per grid point as possible; loads, index arithmetic and
 // register spills are cheap by comparison.
 //
-//  * k_to_f32 (FP32 form only): one conversion of the state to single
-//    precision per stage, so that no stencil load converts.
 //  * k_diffs: for the 11 variables that need mixed second derivatives,
 //    stores the first differences u(i+a) - u(i-a) along x and along y
 //    (a = 1..p/2) over the interior extended by p/2 points in the directions
@@ -24,9 +22,12 @@
 //    derivatives), the pointwise algebra and the RK4 stage epilogue, which
 //    is always double precision.
 //
-// Tiles and staging follow the paper's kernel frames only loosely (Sec. 2.6):
-// neighbours are read through the L1/L2 caches; the first-difference tables
-// play the role of its "RHS derivatives" arrays (Sec. 2.3, loop fission).
+// The FP64 kernels read neighbours through the L1/L2 caches; the
+// first-difference tables play the role of the paper's "RHS derivatives"
+// arrays (Sec. 2.4.1, loop fission). The FP32-RHS form of single grids stages
+// ghosted tiles in shared memory instead (bssn_stage32.cuh); its per-point
+// gather here (gather_lines) serves the batched patches and the refined
+// hierarchy.
 #pragma once
 #include <type_traits>
 
@@ -37,6 +38,7 @@
 #define STAGE_F32_MIN_BLOCKS 4
 #endif
 
+#include "bssn_bounds.cuh"
 #include "bssn_common.cuh"
 #include "bssn_point.cuh"
 
@@ -90,15 +92,6 @@ __device__ __forceinline__ void brick_row(long long r, int ny, int nz, int& j, i
 constexpr int STAGE_BRICK_Y64 = 8, STAGE_BRICK_Z64 = 32;
 constexpr int STAGE_BRICK_Y32 = 4, STAGE_BRICK_Z32 = 32;
 
-// ------------------------------------------------------------------ FP32 copy
-static __global__ void __launch_bounds__(256) k_to_f32(long long n, long long vs, long long npad,
-                                                const double* __restrict__ u, float* __restrict__ f) {
-  const long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (lin >= n) return;
-  const long long v = lin / npad, q = lin - v * npad;
-  f[v * vs + q] = __double2float_rn(__ldg(u + v * vs + q));
-}
-
 // ------------------------------------------------------------------ differences
 template <int P, typename R>
 __global__ void __launch_bounds__(256) k_diffs(Layout L, const R* __restrict__ u, R* __restrict__ dX,
@@ -113,6 +106,7 @@ __global__ void __launch_bounds__(256) k_diffs(Layout L, const R* __restrict__ u
   const int k = (int)(t / ey) - H;
   const long long p = L.off0 + i + j * L.sy + k * L.sz;
   const bool doy = (j >= 0 && j < L.ny);
+  if (!in_range(p - H * L.sy, p + H * L.sy, padded_points(L))) return;
 #pragma unroll 1
   for (int m = 0; m < NM; ++m) {
     const R* v = u + mvar(m) * L.vs;
@@ -150,20 +144,6 @@ __device__ __forceinline__ void d1tab_point(const Coef<float>& C, const float* _
       dY[m * vs + p] = ry;
     }
   }
-}
-
-template <int P>
-__global__ void __launch_bounds__(256) k_d1tab(Layout L, Coef<float> C, const float* __restrict__ u,
-                                               float* __restrict__ dX, float* __restrict__ dY) {
-  constexpr int H = FD<P>::H;
-  const long long ex = L.nx, ey = L.ny + 2 * H, ez = L.nz + 2 * H;
-  const long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (lin >= ex * ey * ez) return;
-  const int i = (int)(lin % ex);
-  const long long t = lin / ex;
-  const int j = (int)(t % ey) - H;
-  const int k = (int)(t / ey) - H;
-  d1tab_point<P>(C, u, L.vs, L.sy, L.off0 + i + j * L.sy + k * L.sz, j >= 0 && j < L.ny, dX, dY);
 }
 
 // first derivative along a stride from the state: sum_a c_a (u_a - u_-a)
@@ -542,6 +522,8 @@ __global__ void __launch_bounds__(128, stage_min_blocks<R>()) k_stage(Layout L, 
 template <int P, int MODE, typename R>
 __device__ __forceinline__ void stage_point(const Layout& L, const Coef<R>& C, const Gauge& gz, const RK& rk,
                                             const StagePtrs<R>& S, long long p) {
+  // every stencil offset lies within r planes of p (bounds-check builds)
+  if (!in_range(p - FD<P>::R * L.sz, p + FD<P>::R * L.sz, padded_points(L))) return;
   // FP64: the full per-point set, ko = dissipation. FP32: the lean set
   // (contracted second derivatives), ko = advection + dissipation.
   using PT = typename std::conditional<std::is_same<R, float>::value, PointLean<R>, PointIn<R>>::type;
@@ -639,11 +621,15 @@ __global__ void __launch_bounds__(128, STAGE_F64_MIN_BLOCKS) k_constraints(Layou
 #pragma unroll
   for (int q = 0; q < 7; ++q) c[q] = 0.0;
   bool bad = false;
+  int i = 0, j = 0, k = 0;
+  long long p = 0;
   if (lin < L.npts) {
-    int i, j, k;
     i = (int)(lin % L.nx);
     brick_row<STAGE_BRICK_Y64, STAGE_BRICK_Z64>(lin / L.nx, L.ny, L.nz, j, k);  // rows in brick order, as k_stage
-    const long long p = L.off0 + i + j * L.sy + k * L.sz;
+    p = L.off0 + i + j * L.sy + k * L.sz;
+  }
+  // no early return here: every thread takes part in the block reduction
+  if (lin < L.npts && in_range(p - FD<P>::R * L.sz, p + FD<P>::R * L.sz, padded_points(L))) {
     PointIn<double> Q;
     gather<P, false, false, double>(L, C, u, dX, dY, p, Q, nullptr);
     double dAt[3][6];

@@ -19,8 +19,8 @@ struct StageArgs {
   float* out32 = nullptr;  // FP32 form: single-precision copy of out (nullable)
 };
 
-// FP64: first-difference tables (H per mixed variable); FP32_RHS: first-
-// derivative tables (one per mixed variable and axis), which need G's spacing.
+// FP64 first-difference tables (H per mixed variable). The FP32-RHS form of
+// single grids has its own tables (launch_d1tab32).
 template <int P>
 cudaError_t launch_diffs(const Layout& L, const bssn_grid_t& G, bssn_precision_t prec, const void* u, void* dX,
                          void* dY, cudaStream_t s);
@@ -40,7 +40,40 @@ cudaError_t launch_psi4(const Layout& L, const Coef<double>& C, const double* u,
                         const double origin[3], const double h[3], double* psi_re, double* psi_im, double* inv_re,
                         double* inv_im, double* E, double* B, unsigned int* flag, cudaStream_t s);
 
-cudaError_t launch_to_f32(const Layout& L, const double* u, float* f, cudaStream_t s);
+// Tiled FP32-RHS path of single grids (bssn_stage32.cu): the single-precision
+// copy and tables live in Layout32 (tables: 11 D_x arrays, then 11 D_y).
+template <int P>
+cudaError_t launch_stage32(const Layout& L, const Layout32& L32, const bssn_grid_t& G, double eps, const Gauge& gz,
+                           const RK& rk, const Stage32Ptrs& S, const float* tables, int mode, cudaStream_t s);
+template <int P>
+cudaError_t launch_d1tab32(const Layout32& L32, const bssn_grid_t& G, const float* u, float* tables,
+                           cudaStream_t s);
+cudaError_t launch_to_f32t(const Layout& L, const Layout32& L32, const double* u, float* f, cudaStream_t s);
+// Reads and clears the device word in which the tiled stage kernel records
+// a bounded wait that gave up (the caller synchronizes first).
+template <int P>
+cudaError_t stage32_take_error(unsigned int* out);
+
+// bssn_api.cu: one fused RK4 stage (tables + fused kernel) on a scratch
+// buffer laid out like `work` (shared with the allocation-free entry point),
+// and the error latch of the C ABI.
+cudaError_t rk4_stage_on_work(void* work, const bssn_grid_t& G, const bssn_params_t& P, bssn_precision_t prec,
+                              int stage, double dt, const double* y0, const double* ys, double* acc, double* ynext,
+                              cudaStream_t s);
+bssn_status_t latch_cuda(cudaError_t e);
+// The argument rules every stepping entry point applies to a grid and its
+// parameters (order 4 or 8, ghost width, gauge switches, finite constants).
+bool grid_params_valid(const bssn_grid_t* grid, const bssn_params_t* params);
+
+// Bounds-check builds: each translation unit's violation count, read and
+// cleared (always 0 in ordinary builds).
+template <int P>
+cudaError_t bounds_take_order(unsigned long long* out);
+template <int P>
+cudaError_t bounds_take_stage32(unsigned long long* out);
+cudaError_t bounds_take_batch(unsigned long long* out);
+cudaError_t bounds_take_amr(unsigned long long* out);
+cudaError_t bounds_take_cfd(unsigned long long* out);
 
 constexpr int STAGE_THREADS = 128;
 constexpr int CON_THREADS = 128;

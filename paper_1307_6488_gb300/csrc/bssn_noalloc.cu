@@ -31,12 +31,15 @@ void* g_scratch[kMaxDevices] = {};
 // Device address of the static scratch array on the current device.
 bssn_status_t scratch_on_current_device(void** out) {
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return BSSN_ERR_CUDA;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return latch_cuda(e);
   if (dev < 0 || dev >= kMaxDevices) return BSSN_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_scratch[dev]) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return BSSN_ERR_CUDA;
+    const cudaError_t e2 = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e2 != cudaSuccess) return latch_cuda(e2);
+    if (!p) return BSSN_ERR_CUDA;
     g_scratch[dev] = p;
   }
   *out = g_scratch[dev];
@@ -62,43 +65,8 @@ extern "C" bssn_status_t bssn_rk4_stage_noalloc(const bssn_grid_t* grid, const b
   void* scratch = nullptr;
   const bssn_status_t st = scratch_on_current_device(&scratch);
   if (st != BSSN_OK) return st;
-
-  // Difference tables inside the scratch: FP64 - x tables then y tables
-  // (11 x p/2 arrays of var_stride doubles each); FP32-RHS - one
-  // single-precision state copy (24 arrays of var_stride floats) followed by
-  // the single-precision x and y tables (bssn_work_bytes also counts a
-  // second copy, which only whole steps use, so this fits within it).
-  const Layout L = make_layout(*grid);
-  const size_t H = (size_t)params->fd_order / 2;
-  const size_t tab = (size_t)NM * H * (size_t)L.vs;
-  float* f32 = nullptr;
-  void* dX;
-  void* dY;
-  if (prec == BSSN_FP64) {
-    dX = scratch;
-    dY = (double*)scratch + tab;
-  } else {
-    f32 = (float*)scratch;
-    dX = f32 + (size_t)NV * L.vs;
-    dY = (float*)dX + tab;
-  }
-
-  cudaStream_t s = (cudaStream_t)stream;
-  const void* src = ys;
-  cudaError_t e = cudaSuccess;
-  if (prec == BSSN_FP32_RHS) {
-    e = launch_to_f32(L, ys, f32, s);
-    src = f32;
-  }
-  if (e == cudaSuccess)
-    e = params->fd_order == 4 ? launch_diffs<4>(L, *grid, prec, src, dX, dY, s)
-                              : launch_diffs<8>(L, *grid, prec, src, dX, dY, s);
-  if (e == cudaSuccess) {
-    StageArgs A{src, ys, y0, acc, ynext, dX, dY};
-    const RK rk = make_rk(stage, dt);
-    const Gauge gz = make_gauge(*params);
-    e = params->fd_order == 4 ? launch_stage<4>(L, *grid, params->ko_eps, prec, gz, rk, A, 0, s)
-                              : launch_stage<8>(L, *grid, params->ko_eps, prec, gz, rk, A, 0, s);
-  }
-  return e == cudaSuccess ? BSSN_OK : BSSN_ERR_CUDA;
+  // the scratch is laid out exactly like a caller's work buffer, so this is
+  // bssn_rk4_stage's own code path
+  return latch_cuda(rk4_stage_on_work(scratch, *grid, *params, prec, stage, dt, y0, ys, acc, ynext,
+                                      (cudaStream_t)stream));
 }

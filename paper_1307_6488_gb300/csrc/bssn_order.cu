@@ -3,6 +3,7 @@
 #include "bssn_kernels.cuh"
 #include "bssn_weyl.cuh"
 #include "bssn_launch.h"
+#include "bssn_bounds.cuh"
 
 #ifndef BSSN_ORDER
 #error "compile with -DBSSN_ORDER=4 or -DBSSN_ORDER=8"
@@ -17,11 +18,9 @@ cudaError_t launch_diffs<BSSN_ORDER>(const Layout& L, const bssn_grid_t& G, bssn
                                      void* dX, void* dY, cudaStream_t s) {
   constexpr int H = FD<BSSN_ORDER>::H;
   const long long n = (long long)L.nx * (L.ny + 2 * H) * (L.nz + 2 * H);
-  if (prec == BSSN_FP64)
-    k_diffs<BSSN_ORDER, double><<<blocks_for(n, 256), 256, 0, s>>>(L, (const double*)u, (double*)dX, (double*)dY);
-  else
-    k_d1tab<BSSN_ORDER><<<blocks_for(n, 256), 256, 0, s>>>(L, make_coef<BSSN_ORDER, float>(G, 0.0), (const float*)u,
-                                                           (float*)dX, (float*)dY);
+  // single grids in the FP32-RHS form take the tiled path (launch_d1tab32)
+  if (prec != BSSN_FP64) return cudaErrorInvalidValue;
+  k_diffs<BSSN_ORDER, double><<<blocks_for(n, 256), 256, 0, s>>>(L, (const double*)u, (double*)dX, (double*)dY);
   return cudaGetLastError();
 }
 
@@ -30,11 +29,8 @@ static cudaError_t stage_typed(const Layout& L, const bssn_grid_t& G, double eps
                                const StageArgs& A, int mode, cudaStream_t s) {
   StagePtrs<R> S{(const R*)A.ys, A.ys64, A.y0, A.acc, A.out, (const R*)A.dX, (const R*)A.dY, A.out32};
   const Coef<R> C = make_coef<BSSN_ORDER, R>(G, eps);
-  // FP32: 2D tiles of STAGE_F32_TILE_X x (128 / STAGE_F32_TILE_X) points
-  const int tx = std::is_same<R, float>::value ? STAGE_F32_TILE_X : 0;
-  const unsigned int nb =
-      tx == 0 ? blocks_for(L.npts, STAGE_THREADS)
-              : (unsigned int)(((L.nx + tx - 1) / tx) * (long long)((L.ny + 128 / tx - 1) / (128 / tx)) * L.nz);
+  const int tx = 0;
+  const unsigned int nb = blocks_for(L.npts, STAGE_THREADS);
   if (mode == 0)
     k_stage<BSSN_ORDER, 0, R><<<nb, STAGE_THREADS, 0, s>>>(L, C, gz, rk, S, tx);
   else
@@ -45,8 +41,9 @@ static cudaError_t stage_typed(const Layout& L, const bssn_grid_t& G, double eps
 template <>
 cudaError_t launch_stage<BSSN_ORDER>(const Layout& L, const bssn_grid_t& G, double eps, bssn_precision_t prec,
                                      const Gauge& gz, const RK& rk, const StageArgs& A, int mode, cudaStream_t s) {
-  if (prec == BSSN_FP64) return stage_typed<double>(L, G, eps, gz, rk, A, mode, s);
-  return stage_typed<float>(L, G, eps, gz, rk, A, mode, s);
+  // single grids in the FP32-RHS form take the tiled path (launch_stage32)
+  if (prec != BSSN_FP64) return cudaErrorInvalidValue;
+  return stage_typed<double>(L, G, eps, gz, rk, A, mode, s);
 }
 
 template <>
@@ -79,13 +76,10 @@ cudaError_t launch_psi4<BSSN_ORDER>(const Layout& L, const Coef<double>& C, cons
   return cudaGetLastError();
 }
 
-#if BSSN_ORDER == 4
-cudaError_t launch_to_f32(const Layout& L, const double* u, float* f, cudaStream_t s) {
-  const long long npad = (L.nx + 2LL * L.g) * (L.ny + 2LL * L.g) * (L.nz + 2LL * L.g);
-  const long long n = (long long)NV * npad;
-  k_to_f32<<<blocks_for(n, 256), 256, 0, s>>>(n, L.vs, npad, u, f);
-  return cudaGetLastError();
+
+template <>
+cudaError_t bounds_take_order<BSSN_ORDER>(unsigned long long* out) {
+  return bounds_take_local(out);
 }
-#endif
 
 }  // namespace bssn

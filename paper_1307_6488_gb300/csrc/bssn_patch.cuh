@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(256) kb_fill(const PatchDev* __restrict__ P, c
     const int k = (int)(r / ey) - L.g;
     if (i >= 0 && i < L.nx && j >= 0 && j < L.ny && k >= 0 && k < L.nz) continue;
     const long long p = L.off0 + i + j * L.sy + k * L.sz;
+    if (!in_range(p, p, padded_points(L))) continue;
     double* u = D.buf[which];
 #pragma unroll 4
     for (int v = 0; v < NV; ++v) u[v * L.vs + p] = __ldg(D.ghost + v * L.vs + p);
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(256) kb_to_f32(const PatchDev* __restrict__ P,
     const int b = find_patch(pad0, np, t);
     const PatchDev& D = P[b];
     const long long q = t - D.pad0;  // padded points are contiguous from 0
+    if (!in_range(q, q, padded_points(D.L))) continue;
     const double* u = D.buf[which];
 #pragma unroll 4
     for (int v = 0; v < NV; ++v) D.f32[v * D.L.vs + q] = __double2float_rn(__ldg(u + v * D.L.vs + q));
@@ -108,6 +110,7 @@ __global__ void __launch_bounds__(256) kb_diffs(const PatchDev* __restrict__ P, 
     const int k = (int)(r / ey) - H;
     const long long p = L.off0 + i + j * L.sy + k * L.sz;
     const bool doy = (j >= 0 && j < L.ny);
+    if (!in_range(p - H * L.sy, p + H * L.sy, padded_points(L))) continue;
     const R* u = stencil_src<R>(D, which);
     R* dX = (R*)D.dX;
     R* dY = (R*)D.dY;

@@ -2,7 +2,7 @@
 //
 // The evolution system is the vacuum BSSN system in the conformal variable
 // W = (det gamma)^(-1/6) (the paper's Sec. 1.1 cites the BSSN formulation
-// and its 24-25 variables; its Sec. 2.3 "optimization" list - constant
+// and its 24-25 variables; its Sec. 2.4.1 "optimization" list - constant
 // folding, common subexpressions - is applied here by hand):
 //
 //   d_t W     = b.dW + W/3 (alpha K - d_k b^k)

@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(128, STAGE_F64_MIN_BLOCKS) k_psi4(Layout L, Co
   i = (int)(lin % L.nx);
   brick_row<STAGE_BRICK_Y64, STAGE_BRICK_Z64>(lin / L.nx, L.ny, L.nz, j, k);  // rows in brick order, as k_stage
   const long long p = L.off0 + i + j * L.sy + k * L.sz;
+  if (!in_range(p - FD<P>::R * L.sz, p + FD<P>::R * L.sz, padded_points(L))) return;
   PointIn<double> Q;
   gather<P, false, false, double>(L, C, u, dX, dY, p, Q, nullptr);
   double dAt[3][6];

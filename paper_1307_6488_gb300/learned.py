@@ -173,7 +173,6 @@ def learned_step(stepper, corrector, state, fallback_factor=2.0, scratch=None):
     before = state.clone() if scratch is None else scratch.copy_(state)
     stepper.coarse_step(state)
     h_plain = stepper.ham_l2(state)
-    plain = state.clone()
     B.corrector_apply(corrector, p.gc, state)
     B.fill_ghosts(p.gc, p.bc, stepper.src_c if p.bc == 1 else None, state)
     h_learned = stepper.ham_l2(state)
@@ -184,7 +183,6 @@ def learned_step(stepper, corrector, state, fallback_factor=2.0, scratch=None):
         stepper.fine_step(fine)
         stepper.restrict(fine, state)
         return True, h_learned, h_plain
-    del plain
     return False, h_learned, h_plain
 
 

@@ -19,8 +19,9 @@ def need_gpu():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+    import os
     from paper_1307_6488_gb300 import build as _b
-    _b.build()
+    _b.build(bounds_check=os.environ.get("BSSN_BOUNDS_CHECK") == "1")
     return torch
 
 

@@ -26,7 +26,7 @@ def _bits(a):
 
 
 def test_roundtrip_bit_exact(L, tmp_path):
-    grid = B.make_grid(5, 4, 3, ghost=2, dx=0.1, dy=0.2, dz=0.3)
+    grid = B.make_grid(5, 4, 3, ghost=3, dx=0.1, dy=0.2, dz=0.3)
     params = B.make_params(fd_order=4, ko_eps=0.07, lapse=1, shift=1, shift_coeff=0.6, eta=1.3, advect_gauge=0)
     rng = np.random.default_rng(1)
     state = rng.normal(size=24 * grid.var_stride)
@@ -48,7 +48,7 @@ def test_roundtrip_bit_exact(L, tmp_path):
 
 
 def test_damaged_files_are_rejected(L, tmp_path):
-    grid = B.make_grid(4, ghost=2, dx=0.1)
+    grid = B.make_grid(4, ghost=3, dx=0.1)
     params = B.make_params()
     state = np.arange(24 * grid.var_stride, dtype=np.float64)
     good = tmp_path / "good.ckp"
@@ -73,7 +73,7 @@ def test_damaged_files_are_rejected(L, tmp_path):
 
 
 def test_invalid_arguments(L, tmp_path):
-    grid = B.make_grid(4, ghost=2, dx=0.1)
+    grid = B.make_grid(4, ghost=3, dx=0.1)
     params = B.make_params()
     state = np.zeros(24 * grid.var_stride)
     G, P = ctypes.byref, ctypes.byref
@@ -93,6 +93,74 @@ def test_invalid_arguments(L, tmp_path):
                                   None, 0) == E
     with pytest.raises(B.BssnError):
         B.checkpoint_write(tmp_path / "z.ckp", grid, params, 0.0, 0, state[:10])
+    # parameters the stepping entry points would reject
+    for bad_p in (B.make_params(fd_order=6), B.make_params(fd_order=8), B.make_params(lapse=3),
+                  B.make_params(ko_eps=float("nan"))):
+        with pytest.raises(B.BssnError) as e:
+            B.checkpoint_write(tmp_path / "w.ckp", grid, bad_p, 0.0, 0, state)
+        assert e.value.status == E
+    assert not (tmp_path / "w.ckp").exists()
+
+
+# byte offsets of header fields (the layout bssn_checkpoint.cu writes)
+OFF = dict(ghost=28, order=64, eps=68, lapse=76, shift=80, coeff=84, eta=92, adv=100, t=104)
+
+
+def test_damaged_parameters_are_rejected(L, tmp_path):
+    """A file whose parameters no stepping entry point would accept is
+    rejected on reading, one damaged field at a time (the data hash does not
+    cover the header, so only this check can catch it)."""
+    import struct
+    grid = B.make_grid(6, ghost=5, dx=0.1)
+    params = B.make_params(fd_order=8)
+    state = np.zeros(24 * grid.var_stride)
+    good = tmp_path / "good.ckp"
+    B.checkpoint_write(good, grid, params, 0.5, 3, state)
+    raw = bytearray(good.read_bytes())
+    B.checkpoint_read(good)  # the untouched file reads
+
+    def patched(off, fmt, value):
+        b = bytearray(raw)
+        struct.pack_into(fmt, b, off, value)
+        return bytes(b)
+
+    cases = {
+        "order 6": patched(OFF["order"], "<i", 6),
+        "order 4 is fine but ghost 2 is too small": patched(OFF["ghost"], "<i", 2),
+        "lapse 3": patched(OFF["lapse"], "<i", 3),
+        "shift -1": patched(OFF["shift"], "<i", -1),
+        "advect_gauge 2": patched(OFF["adv"], "<i", 2),
+        "ko_eps nan": patched(OFF["eps"], "<d", float("nan")),
+        "ko_eps negative": patched(OFF["eps"], "<d", -0.1),
+        "eta inf": patched(OFF["eta"], "<d", float("inf")),
+        "shift_coeff nan": patched(OFF["coeff"], "<d", float("nan")),
+        "t nan": patched(OFF["t"], "<d", float("nan")),
+    }
+    for name, blob in cases.items():
+        p = tmp_path / "bad.ckp"
+        p.write_bytes(blob)
+        with pytest.raises(B.BssnError) as e:
+            B.checkpoint_read(p, with_state=False)
+        assert e.value.status == B.ERR_INVALID_ARG, name
+
+
+def test_failed_write_keeps_the_previous_checkpoint(L, tmp_path):
+    """The file is written under a temporary name and renamed only when every
+    write succeeded: with the temporary name taken by a directory, the write
+    fails and the checkpoint already at the path still reads back intact."""
+    grid = B.make_grid(4, ghost=3, dx=0.1)
+    params = B.make_params()
+    old = np.arange(24 * grid.var_stride, dtype=np.float64)
+    path = tmp_path / "run.ckp"
+    B.checkpoint_write(path, grid, params, 1.0, 10, old)
+    (tmp_path / ("run.ckp.tmp%d" % os.getpid())).mkdir()
+    with pytest.raises(B.BssnError):
+        B.checkpoint_write(path, grid, params, 2.0, 20, old + 1)
+    _, _, t, step, s2 = B.checkpoint_read(path)
+    assert (t, step) == (1.0, 10)
+    assert np.array_equal(s2, old)
+    # no stray files besides the blocked temporary name
+    assert sorted(f.name for f in tmp_path.iterdir()) == ["run.ckp", "run.ckp.tmp%d" % os.getpid()]
 
 
 def _flat(u, grid):
@@ -152,5 +220,41 @@ def test_resume_on_the_gpu_is_bit_identical(L, tmp_path):
     g2, p2, t, step, f = B.checkpoint_read(path)
     c = torch.from_numpy(f).to("cuda")
     B.rk4_step(g2, p2, B.FP64, dt, 0, None, c, bufs, work)
+    torch.cuda.synchronize()
+    assert torch.equal(a, c)
+
+
+@pytest.mark.gpu
+def test_resume_with_a_static_boundary_on_the_gpu(L, tmp_path):
+    """A static-boundary run (fill mode 1) resumed from its checkpoint: the
+    ghost cells keep their t = 0 values and are part of the saved state, so a
+    copy of the loaded state serves as ghost_src. Two FP64 RK4 steps of
+    Brill-Lindquist data at 8th order, a checkpoint, one more step: the same
+    bits as three steps straight."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    u, h = inputs.brill_lindquist(20, 5, lo=-2.5, hi=2.5, masses=(0.5, 0.5), centers=((-0.7, 0.1, 0.05),
+                                                                                    (0.7, -0.1, 0.05)))
+    grid = B.make_grid(20, ghost=5, dx=h)
+    p = B.make_params(fd_order=8)
+    dt = 0.25 * h
+    bufs = B.alloc_state(grid, n=3)
+    work = B.alloc_work(grid, p)
+    src = B.upload(u, grid)
+    a = B.upload(u, grid)
+    b = B.upload(u, grid)
+    for _ in range(3):
+        B.rk4_step(grid, p, B.FP64, dt, 1, src, a, bufs, work)
+    for _ in range(2):
+        B.rk4_step(grid, p, B.FP64, dt, 1, src, b, bufs, work)
+    torch.cuda.synchronize()
+    path = tmp_path / "bl.ckp"
+    B.checkpoint_write(path, grid, p, 2 * dt, 2, b.cpu().numpy())
+    del b
+    g2, p2, t, step, f = B.checkpoint_read(path)
+    c = torch.from_numpy(f).to("cuda")
+    ghost_src = c.clone()
+    B.rk4_step(g2, p2, B.FP64, dt, 1, ghost_src, c, bufs, work)
     torch.cuda.synchronize()
     assert torch.equal(a, c)

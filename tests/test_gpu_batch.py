@@ -51,6 +51,11 @@ def step_single(u, g, h, p, prec, dt):
     return B.download(s, grid)
 
 
+# two single-precision evaluations of the same step, differing in rounding
+# order only, relative to the step's change per tensor field
+FP32_ORDER_TOL = 1e-4
+
+
 @pytest.mark.parametrize("order,prec", [(4, B.FP64), (8, B.FP64), (4, B.FP32_RHS)])
 @pytest.mark.parametrize("autotune", [0, 1])
 def test_batch_step_matches_single_grid(order, prec, autotune):
@@ -79,7 +84,12 @@ def test_batch_step_matches_single_grid(order, prec, autotune):
             want = step_single(step_single(u, g, h, p, prec, dt), g, h, p, prec, dt)
             got = B.download(st, grid)
             err = rel_err_tensor(got - u, want - u, g)
-            assert np.max(err) < RHS_TOL, (n, dict(zip(inputs.VARS, err)))
+            # FP32-RHS: the patches' per-point gather and the single grid's
+            # tiled kernel evaluate the same single-precision arithmetic in a
+            # different order (upwinding from paired sums), so they agree to
+            # single-precision rounding, not bit for bit
+            tol = RHS_TOL if prec == B.FP64 else FP32_ORDER_TOL
+            assert np.max(err) < tol, (n, dict(zip(inputs.VARS, err)))
     finally:
         B.plan_destroy(plan)
 

@@ -1,5 +1,5 @@
 """Pins for the oracle's SOLA Navier-Stokes kernels (oracle/cfd.py), the
-paper's three-kernel CFD benchmark (Sec. 4), not GPU:
+paper's three-kernel CFD benchmark (Sec. 3.2), not GPU:
   * a uniform flow with periodic boundaries is an exact fixed point;
   * fluid at rest under gravity with the hydrostatic pressure stays at rest;
   * total momentum is conserved with periodic boundaries by the velocity

@@ -13,7 +13,13 @@ import pytest
 from paper_1307_6488_gb300 import binding as B
 from paper_1307_6488_gb300 import inputs
 
-from gpu_common import RHS_TOL, grid_for, interior, need_gpu, perturbed_bl
+import oracle
+
+from gpu_common import RHS_TOL, grid_for, interior, need_gpu, oracle_params, perturbed_bl, rel_err_tensor
+
+# the single-precision right-hand side against the FP64 oracle, per tensor
+# field (the bound of the FP32-RHS tests)
+FP32_RHS_TOL = 3e-4
 
 pytestmark = pytest.mark.gpu
 
@@ -57,6 +63,13 @@ def test_noalloc_matches_stage_on_two_calls_in_a_row(prec):
     (ref1, racc1), (new1, nacc1) = _stage_both_ways(grid, p, prec, 0, dt, y0, y0, acc0)
     assert _max_rel(new1, ref1, g) < RHS_TOL
     assert _max_rel(nacc1, racc1, g) < RHS_TOL
+    # and directly against the oracle: after stage 0, acc = dt/6 k(y0)
+    k = oracle.rhs(u, g, h, oracle_params(p), ko=True)
+    want = dt / 6 * k
+    if prec == B.FP64:
+        assert _max_rel(nacc1, want, g) < RHS_TOL
+    else:
+        assert np.max(rel_err_tensor(nacc1, want, g)) < FP32_RHS_TOL
     ys_np = inputs.periodic_wrap(ref1.copy(), g)
     ys = B.upload(ys_np, grid)
     acc1 = B.upload(racc1, grid)
@@ -83,11 +96,16 @@ def test_noalloc_fourth_order_after_eighth():
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch():
-    need_gpu()
+    torch = need_gpu()
     grid = B.make_grid(64, ghost=5, dx=0.1)
     p = B.make_params(fd_order=8)
     assert B.work_bytes(grid, p) > (64 << 20)
-    fake = 1 << 20  # never dereferenced: the size check comes before anything else
+    # real states of this grid, so that even a call that got past the size
+    # check would only touch live memory; the outputs must stay untouched
+    y0, ys, acc, out = (B.alloc_state(grid) for _ in range(4))
+    out.fill_(1.5)
     with pytest.raises(B.BssnError) as err:
-        B.rk4_stage_noalloc(grid, p, B.FP64, 0, 0.01, fake, fake * 2, fake * 3, fake * 4)
+        B.rk4_stage_noalloc(grid, p, B.FP64, 0, 0.01, y0, ys, acc, out)
     assert err.value.status == B.ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert bool((out == 1.5).all())
