@@ -5,7 +5,7 @@
 // A block of 128 threads owns a tile of 8 x 4 x 4 interior points, one
 // point per thread. For each of the 24 variables in turn, one thread issues
 // the TMA copies of that variable's stencil region around the tile into one
-// slot of a 5-deep ring in shared memory:
+// slot of a 3-deep ring in shared memory:
 //   SX  the tile's rows widened by 8 points on each side in x (the copy
 //       starts 8 points left of the tile so that it stays 16-byte aligned;
 //       the stencil uses 5),
@@ -13,7 +13,7 @@
 // and, for the 11 variables with mixed second derivatives, the D_x u table
 // widened by p/2 in y and in z and the D_y u table widened by p/2 in z. An
 // mbarrier per slot signals the copy's completion and a second one, on which
-// all 128 threads arrive, frees the slot for the variable 5 places later.
+// all 128 threads arrive, frees the slot for the variable 3 places later.
 // Every value a thread reads comes from shared memory at a fixed offset from
 // its own point, and feeds the first derivative, the diagonal second
 // derivative, the Kreiss-Oliger term and the upwinded advection of that
@@ -54,8 +54,11 @@ namespace bssn {
 
 // ---------------------------------------------------------------- tile
 constexpr int T32X = 8, T32Y = 4, T32Z = 4, T32N = T32X * T32Y * T32Z;
+#ifndef T32_MIN_BLOCKS
+#define T32_MIN_BLOCKS 3
+#endif
 #ifndef T32_NBUF_DEF
-#define T32_NBUF_DEF 5
+#define T32_NBUF_DEF 3
 #endif
 constexpr int T32_NBUF = T32_NBUF_DEF;
 constexpr int T32_NTAB = 2 * NM;  // D_x tables of the 11 mixed variables, then their D_y tables
@@ -76,8 +79,8 @@ struct Tile32 {
   static constexpr unsigned BYTES_MIXED = 4u * SLOT;
   // ring, per-thread derivative record (rec::N floats per thread), full and
   // empty barriers, the abort flag; 128 bytes of slack to align the ring
-  static constexpr size_t SMEM = 128 + (size_t)T32_NBUF * SLOT * 4 + (size_t)114 * T32N * 4 +
-                                 2 * T32_NBUF * sizeof(uint64_t) + 16;
+  static constexpr size_t RING = (size_t)T32_NBUF * SLOT * 4;
+  static constexpr size_t SMEM = 128 + RING + (size_t)90 * T32N * 4 + 2 * T32_NBUF * sizeof(uint64_t) + 16;
   static_assert(N_X % 32 == 0 && N_Y % 32 == 0 && N_Z % 32 == 0 && N_TY % 32 == 0 && N_TZ % 32 == 0,
                 "TMA destinations must stay 128-byte aligned");
 };
@@ -155,7 +158,7 @@ static __device__ unsigned int g_stage32_err;
 // derivatives are stored per variable as a triple (d = x, y, z) in the order
 // W, gt11..gt33, K, Gt1..Gt3, alpha, beta1..beta3.
 namespace rec {
-constexpr int U = 0, EXT = 24, D1 = 48, DDW = 93, DDA = 99, LAPG = 105, LAPB = 111, N = 114;
+constexpr int EXT = 0, D1 = 24, DDW = 69, DDA = 75, LAPG = 81, LAPB = 87, N = 90;
 }
 // first-derivative triple of variable v in the record, or -1
 __host__ __device__ constexpr int d1_slot(int v) {
@@ -169,14 +172,14 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 // MODE 0: RK stage (right-hand side + dissipation, then the update).
 // MODE 1: right-hand side (+ advection, no dissipation: pass eps = 0) into out.
 template <int P, int MODE>
-__global__ void __launch_bounds__(T32N, 2)
+__global__ void __launch_bounds__(T32N, T32_MIN_BLOCKS)
     k_stage32t(Layout L, Layout32 L32, Coef32 C, Gauge gz, RK rk, Stage32Ptrs S,
                const __grid_constant__ Stage32Maps M, int ntx, int nty) {
   using T = Tile32<P>;
   constexpr int R = T::R, H = T::H;
   extern __shared__ __align__(128) unsigned char sm_raw[];
   float* sm = reinterpret_cast<float*>(sm_raw + ((128u - (tc::smem_u32(sm_raw) & 127u)) & 127u));
-  float* recb = sm + T32_NBUF * T::SLOT;
+  float* recb = sm + T::RING / 4;
   uint64_t* full = reinterpret_cast<uint64_t*>(recb + rec::N * T32N);
   uint64_t* empty = full + T32_NBUF;
   volatile int& abort_flag = *reinterpret_cast<volatile int*>(empty + T32_NBUF);
@@ -295,7 +298,6 @@ __global__ void __launch_bounds__(T32N, 2)
     const int d1s = d1_slot(v);
     const bool advected = v < V_ALPHA || (v == V_ALPHA ? adv_alpha : adv_shift);
     const float u0 = SY[syi];
-    my[(rec::U + v) * T32N] = u0;
     const float m2u0 = -2.f * u0;
     float d1v[3], d2v[3], e = 0.f;
 #pragma unroll
@@ -403,10 +405,11 @@ __global__ void __launch_bounds__(T32N, 2)
     return;
   }
 
-  // the per-point set from the record
+  // the per-point set: centre values from the single-precision copy (in L2:
+  // the copies just read them), derivatives from the record
   PointLean<float> Q;
 #pragma unroll
-  for (int v = 0; v < NV; ++v) Q.u[v] = my[(rec::U + v) * T32N];
+  for (int v = 0; v < NV; ++v) Q.u[v] = __ldg(S.ys32 + v * L32.vs + q);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     Q.dW[d] = my[(rec::D1 + 3 * d1_slot(V_W) + d) * T32N];
@@ -447,27 +450,37 @@ __global__ void __launch_bounds__(T32N, 2)
 #pragma unroll
     for (int v = 0; v < NV; ++v) S.out[v * vs + p] = kd[v];
   } else {
+    // every input of the update is read before any output is written:
+    // ynext may be y0, and the loads can then all be in flight at once
+    double y0r[NV], br[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) y0r[v] = __ldg(S.y0 + v * vs + p);
+    if (rk.method == 3) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) br[v] = __ldg(S.ys64 + v * vs + p);
+    } else if (rk.stage > 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) br[v] = S.acc[v * vs + p];
+    }
     double yn[NV];
     if (rk.method == 3) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const long long o = v * vs + p;
-        yn[v] = fma(rk.cdt, kd[v], fma(rk.a1, __ldg(S.ys64 + o), rk.a0 * __ldg(S.y0 + o)));
-        S.out[o] = yn[v];
+        yn[v] = fma(rk.cdt, kd[v], fma(rk.a1, br[v], rk.a0 * y0r[v]));
+        S.out[v * vs + p] = yn[v];
       }
     } else {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const long long o = v * vs + p;
-        const double y0v = __ldg(S.y0 + o);
         if (rk.stage == 0) {
           S.acc[o] = rk.bdt * kd[v];
-          yn[v] = fma(rk.cdt, kd[v], y0v);
+          yn[v] = fma(rk.cdt, kd[v], y0r[v]);
         } else if (rk.stage < 3) {
-          S.acc[o] = fma(rk.bdt, kd[v], S.acc[o]);
-          yn[v] = fma(rk.cdt, kd[v], y0v);
+          S.acc[o] = fma(rk.bdt, kd[v], br[v]);
+          yn[v] = fma(rk.cdt, kd[v], y0r[v]);
         } else {
-          yn[v] = y0v + fma(rk.bdt, kd[v], S.acc[o]);
+          yn[v] = y0r[v] + fma(rk.bdt, kd[v], br[v]);
         }
         S.out[o] = yn[v];
       }
