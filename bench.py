@@ -66,7 +66,10 @@ FP64_FMA_PER_CLK_SM = 2
 CFD_TRAFFIC = {"src_sha": "1559830c488ce0a5", "bytes_per_launch": 286361600 + 225778176}
 
 # the sources that make up the fused FP64 stage kernel k_stage<8,0,double>
-STAGE_SOURCES = ("bssn_common.cuh", "bssn_point.cuh", "bssn_kernels.cuh", "bssn_order.cu")
+STAGE_SOURCES = ("bssn_common.cuh", "bssn_point.cuh", "bssn_kernels.cuh", "bssn_order.cu", "bssn_bounds.cuh")
+# and the tiled FP32-RHS stage kernel k_stage32t<8,0>
+STAGE32_SOURCES = ("bssn_common.cuh", "bssn_point.cuh", "bssn_stage32.cuh", "bssn_stage32.cu", "bssn_cvt.cuh",
+                   "bssn_tc.cuh", "bssn_bounds.cuh")
 
 
 def src_sha(files):
@@ -79,6 +82,10 @@ def src_sha(files):
 
 def kernel_src_sha():
     return src_sha(STAGE_SOURCES)
+
+
+def kernel32_src_sha():
+    return src_sha(STAGE32_SOURCES)
 
 
 # Stencil applications per interior point and right-hand side (counts of the
@@ -1132,7 +1139,7 @@ def run_gpu(args):
                                  "frac": (864 * pts / (f32["stage_ms"] * 1e-3) / 1e9 / MEASURED["hbm_gbs"])
                                  if MEASURED.get("hbm_gbs") else None,
                                  "traffic": TRAFFIC_F32["bytes_per_launch_128"]
-                                 if TRAFFIC_F32["src_sha"] == sha and n == N else None},
+                                 if TRAFFIC_F32["src_sha"] == kernel32_src_sha() and n == N else None},
                          "err_vs_fp64_max_rel_per_tensor": float(np.max(err32)),
                          "err_vs_fp64_per_var": [float(x) for x in err32],
                          "ham_l2_after": float(f32["l2"][0]), "det_gt_minus_1_l2_after": float(f32["alg"][0]),

@@ -12,8 +12,9 @@
 //   SY  the tile widened by r = p/2 + 1 rows in y, SZ by r planes in z,
 // and, for the 11 variables with mixed second derivatives, the D_x u table
 // widened by p/2 in y and in z and the D_y u table widened by p/2 in z. An
-// mbarrier per slot signals the copy's completion and a second one, on which
-// all 128 threads arrive, frees the slot for the variable 3 places later.
+// mbarrier per slot signals the copy's completion; the last of the four warps
+// to finish with a slot (a per-slot counter) refills it with the variable 3
+// places later, so no thread waits for the others.
 // Every value a thread reads comes from shared memory at a fixed offset from
 // its own point, and feeds the first derivative, the diagonal second
 // derivative, the Kreiss-Oliger term and the upwinded advection of that
@@ -80,7 +81,9 @@ struct Tile32 {
   // ring, per-thread derivative record (rec::N floats per thread), full and
   // empty barriers, the abort flag; 128 bytes of slack to align the ring
   static constexpr size_t RING = (size_t)T32_NBUF * SLOT * 4;
-  static constexpr size_t SMEM = 128 + RING + (size_t)90 * T32N * 4 + 2 * T32_NBUF * sizeof(uint64_t) + 16;
+  // ring, record, full barriers, per-slot counters, abort flag, issued count
+  static constexpr size_t SMEM = 128 + RING + (size_t)90 * T32N * 4 + T32_NBUF * sizeof(uint64_t) +
+                                 (T32_NBUF + 2) * sizeof(int) + 16;
   static_assert(N_X % 32 == 0 && N_Y % 32 == 0 && N_Z % 32 == 0 && N_TY % 32 == 0 && N_TZ % 32 == 0,
                 "TMA destinations must stay 128-byte aligned");
 };
@@ -181,8 +184,9 @@ __global__ void __launch_bounds__(T32N, T32_MIN_BLOCKS)
   float* sm = reinterpret_cast<float*>(sm_raw + ((128u - (tc::smem_u32(sm_raw) & 127u)) & 127u));
   float* recb = sm + T::RING / 4;
   uint64_t* full = reinterpret_cast<uint64_t*>(recb + rec::N * T32N);
-  uint64_t* empty = full + T32_NBUF;
-  volatile int& abort_flag = *reinterpret_cast<volatile int*>(empty + T32_NBUF);
+  int* cnt = reinterpret_cast<int*>(full + T32_NBUF);  // warps done with each slot
+  volatile int& abort_flag = *reinterpret_cast<volatile int*>(cnt + T32_NBUF);
+  int* issued_p = cnt + T32_NBUF + 1;  // variables whose copies were issued
 
   const int t = threadIdx.x;
   const int tx = t & (T32X - 1), ty = (t / T32X) & (T32Y - 1), tz = t / (T32X * T32Y);
@@ -199,17 +203,14 @@ __global__ void __launch_bounds__(T32N, T32_MIN_BLOCKS)
 #pragma unroll
     for (int q = 0; q < T32_NBUF; ++q) {
       tc::mbar_init(&full[q], 1);
-      tc::mbar_init(&empty[q], T32N);
+      cnt[q] = 0;
     }
     tc::mbar_fence_init();
-  }
-  __syncthreads();
-  int issued = 0;  // thread 0: variables whose copies were issued
-  if (t == 0) {
 #pragma unroll
     for (int v = 0; v < T32_NBUF; ++v) issue_var<P>(M, L32, v, x0, y0, z0, sm + v * T::SLOT, &full[v]);
-    issued = T32_NBUF;
+    *issued_p = T32_NBUF;
   }
+  __syncthreads();
 
   // the epilogue's double-precision operands (y0; acc from stage 1 on; ys
   // for RK3) of the tile's rows move into L2 while the stencils run
@@ -283,7 +284,8 @@ __global__ void __launch_bounds__(T32N, T32_MIN_BLOCKS)
   for (int v = 0; v < NV; ++v) {
     const int s = v % T32_NBUF;
     const uint32_t par = (uint32_t)(v / T32_NBUF) & 1u;
-    if (!tc::mbar_wait_or_abort(&full[s], par, &abort_flag, STAGE32_WAIT_NS)) {
+    // the outcome is made warp-uniform, so that the warp stays converged
+    if (!__all_sync(0xffffffffu, tc::mbar_wait_or_abort(&full[s], par, &abort_flag, STAGE32_WAIT_NS))) {
       if (!abort_flag) atomicOr(&g_stage32_err, 1u);
       abort_flag = 1;
       ok = false;
@@ -384,26 +386,22 @@ __global__ void __launch_bounds__(T32N, T32_MIN_BLOCKS)
         dddb[2] += ib == 0 ? d2s[2] : (ib == 1 ? d2s[4] : d2s[5]);
       }
     }
-    // free the slot; thread 0 refills it with the variable T32_NBUF later
-    tc::mbar_arrive(&empty[s]);
-    if (t == 0 && v + T32_NBUF < NV) {
-      if (!tc::mbar_wait_or_abort(&empty[s], par, &abort_flag, STAGE32_WAIT_NS)) {
-        if (!abort_flag) atomicOr(&g_stage32_err, 1u);
-        abort_flag = 1;
-        ok = false;
-        break;
+    // done with the slot: the last warp to finish with it refills it with
+    // the variable T32_NBUF later (no thread waits for the others)
+    __syncwarp();
+    if ((t & 31) == 0) {
+      __threadfence_block();
+      if (atomicAdd(&cnt[s], 1) == T32N / 32 - 1) {
+        cnt[s] = 0;
+        if (v + T32_NBUF < NV && !abort_flag) {
+          tc::fence_proxy_async();
+          issue_var<P>(M, L32, v + T32_NBUF, x0, y0, z0, sm + s * T::SLOT, &full[s]);
+          atomicMax(issued_p, v + T32_NBUF + 1);
+        }
       }
-      issue_var<P>(M, L32, v + T32_NBUF, x0, y0, z0, sm + s * T::SLOT, &full[s]);
-      issued = v + T32_NBUF + 1;
     }
   }
-  if (!ok) {
-    // leave only once the copies this block started have landed
-    if (t == 0)
-      for (int v = consumed; v < issued; ++v)
-        tc::mbar_wait(&full[v % T32_NBUF], (uint32_t)(v / T32_NBUF) & 1u, STAGE32_WAIT_NS);
-    return;
-  }
+  if (ok) {
 
   // the per-point set: centre values from the single-precision copy (in L2:
   // the copies just read them), derivatives from the record
@@ -436,8 +434,7 @@ __global__ void __launch_bounds__(T32N, T32_MIN_BLOCKS)
   }
   float rhs[NV];
   rhs_point<float>(Q, gz, iW, rhs);
-  if (!valid) return;
-  if (!in_range(p, p, padded_points(L)) || !in_range(q, q, padded_points32(L32))) return;
+  if (valid && in_range(p, p, padded_points(L)) && in_range(q, q, padded_points32(L32))) {
   const long long vs = L.vs;
   double kd[NV];
   {
@@ -492,6 +489,13 @@ __global__ void __launch_bounds__(T32N, T32_MIN_BLOCKS)
       for (int v = 0; v < NV; ++v) S.out32[v * L32.vs + q] = y32[v];
     }
   }
+  }
+  }
+  // a wait that gave up ends the block (every thread gets here); it leaves
+  // only once the copies it started have landed
+  if (__syncthreads_or(!ok) && t == 0)
+    for (int v = consumed; v < *issued_p; ++v)
+      tc::mbar_wait(&full[v % T32_NBUF], (uint32_t)(v / T32_NBUF) & 1u, STAGE32_WAIT_NS);
 }
 
 // ---------------------------------------------------------------- helpers
