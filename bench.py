@@ -43,20 +43,24 @@ except (OSError, ValueError):
     MEASURED = {}
 
 # DRAM traffic of the fused stage kernel per launch, from one ncu capture of
-# the same source (profiles/); ignored when the kernel source has changed.
-# Captured at 96^3 (884,736 points: 3.249 GB read + 2.783 GB written per
-# launch, 6.84 kB per point at 4 blocks/SM, rows traversed in bricks) and
-# scaled to 128^3 by
-# the point count, since the traffic is per point (state, tables and the
-# per-thread stack).
-TRAFFIC = {"src_sha": "05abd4d45060a217", "bytes_per_launch_128": (3.248892416e9 + 2.782864640e9) * 128 ** 3 / 96 ** 3}
+# the same source (profiles/k_stage_fp64_bl64.md); ignored when the kernel
+# source has changed. Captured at 64^3 (262,144 points: 921.1 MB read + 797.5
+# MB written per launch, 6.56 kB per point at 4 blocks/SM, rows traversed in
+# bricks) and scaled to 128^3 by the point count, since the traffic is per
+# point (state, tables and the per-thread stack).
+TRAFFIC = {"src_sha": "1bd173c68c3b6f9f", "bytes_per_launch_128": (921128448 + 797547008) * 128 ** 3 / 64 ** 3}
 # FP64 pipe utilisation of the same launch (sm__pipe_fp64_cycles_active,
-# percent of peak over active cycles), for the same source.
-FP64_PIPE_BUSY = {"src_sha": "05abd4d45060a217", "pct_of_active_cycles": 85.18}
-# The same for the FP32-RHS stage kernel k_stage<8,0,float> as bssn_rk4_step
-# runs it (writing the next stage's single-precision input too; one launch
-# at 96^3: 0.569 GB read + 0.757 GB written, 1.50 kB per point), scaled to 128^3.
-TRAFFIC_F32 = {"src_sha": "05abd4d45060a217", "bytes_per_launch_128": (0.568696832e9 + 0.756768256e9) * 128 ** 3 / 96 ** 3}
+# percent of peak over active cycles) and the FP64 instructions it executed
+# per interior point (smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul}
+# _pred_on.sum / 64^3), for the same source.
+FP64_PIPE_BUSY = {"src_sha": "1bd173c68c3b6f9f", "pct_of_active_cycles": 82.57,
+                  "dfma_per_point": 636223488 / 64 ** 3, "dadd_per_point": 409468928 / 64 ** 3,
+                  "dmul_per_point": 101187584 / 64 ** 3}
+# The same for the tiled FP32-RHS stage kernel k_stage32t<8,0> as
+# bssn_rk4_step runs it (writing the next stage's single-precision input too;
+# one launch at 64^3: 225.3 MB read + 117.1 MB written, 1.31 kB per point,
+# profiles/k_stage32t_fp32_bl64.md), scaled to 128^3 by the point count.
+TRAFFIC_F32 = {"src_sha": "5b1793e82e768f56", "bytes_per_launch_128": (225.346304e6 + 117.100544e6) * 128 ** 3 / 64 ** 3}
 N_SM = 152
 FP64_FMA_PER_CLK_SM = 2
 
@@ -94,6 +98,19 @@ def kernel32_src_sha():
 # derivatives of W, gt_ij, alpha, beta^i; upwinded advection of all 24
 # variables along 3 axes, summed over the axes (2 adds per variable).
 N_FIRST, N_SECOND, N_MIXED, N_ADV, N_ADV_SUM = 45, 33, 33, 72, 48
+
+
+def executed_fp64(stage_ms, pts, sm_mhz, per_clk, sha):
+    """FP64 instructions the fused stage kernel executes per point (ncu
+    counts for this source, else None) and their issue rate per SM clock as a
+    fraction of the measured FP64 FMA rate per SM clock."""
+    if FP64_PIPE_BUSY["src_sha"] != sha:
+        return None
+    c = FP64_PIPE_BUSY
+    inst = c["dfma_per_point"] + c["dadd_per_point"] + c["dmul_per_point"]
+    per_clk_run = inst * pts / (stage_ms * 1e-3) / (N_SM * sm_mhz * 1e6)
+    return {"fp64_inst_per_point": inst, "fp64_flop_per_point": 2 * c["dfma_per_point"] + c["dadd_per_point"]
+            + c["dmul_per_point"], "inst_per_clk_sm": per_clk_run, "frac_of_measured_issue_rate": per_clk_run / per_clk}
 
 
 def algorithmic_flops(order=ORDER):
@@ -1108,7 +1125,11 @@ def run_gpu(args):
                              "achieved_gbs": 1568 * pts / (f64["stage_ms"] * 1e-3) / 1e9,
                              "frac": (1568 * pts / (f64["stage_ms"] * 1e-3) / 1e9 / MEASURED["hbm_gbs"])
                              if MEASURED.get("hbm_gbs") else None},
-                     "fp64_pipe_busy_ncu": FP64_PIPE_BUSY if FP64_PIPE_BUSY["src_sha"] == sha else None},
+                     "fp64_pipe_busy_ncu": FP64_PIPE_BUSY if FP64_PIPE_BUSY["src_sha"] == sha else None,
+                     # what the kernel executes (ncu instruction counts of the same source): FP64
+                     # instructions per point and stage, and their rate per SM clock against the
+                     # probe's measured FMA rate per SM clock (the FP64 pipe's issue ceiling)
+                     "executed": executed_fp64(f64["stage_ms"], pts, sm_mhz, per_clk, sha)},
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
                          "sample": f"{cpu_steps} oracle RK4 step(s) of the same workload on a 32^3 block "
                                    f"({cpu_s:.1f} s)",
@@ -1130,6 +1151,7 @@ def run_gpu(args):
                                           "writing the next stage's single-precision input",
                          "stage_ms_from": "the fused stage kernel timed on two further steps of per-stage calls "
                                           "(without the single-precision stores)",
+                         "kernel": "k_stage32t<8,0> (tiled FP32-RHS stage: TMA-staged ghosted tiles)",
                          "achieved_tflops": achieved32 / 1e12, "frac_of_fp32_peak": achieved32 / peak32,
                          # algorithmic bytes of the stage kernel per point and stage, averaged over
                          # the four stages: FP32 stencil input 96, FP32 tables 88, FP64 W 8, y0 192,

@@ -114,6 +114,13 @@ void bssn_clear_error(void);
 int bssn_bounds_check_enabled(void);
 bssn_status_t bssn_bounds_violations(unsigned long long* count, void* stream);
 
+/* Root-mean-square over interior points of a - b for each of the 24
+ * variables (DEVICE states a, b of grid; HOST out_rms[24]), in double
+ * precision with a fixed summation order. work: >= bssn_work_bytes() of the
+ * grid at any order its ghost width allows (ghost >= 3). Synchronizes. */
+bssn_status_t bssn_rms_diff(const bssn_grid_t* grid, const double* a, const double* b, double* out_rms, void* work,
+                           unsigned long long work_bytes, void* stream);
+
 /* Waits for `stream` to finish and reports device-side failures of the
  * kernels that run on it: BSSN_ERR_TIMEOUT if a bounded wait inside a
  * single-grid FP32-RHS stage kernel gave up since the last check (the
@@ -506,6 +513,12 @@ bssn_status_t bssn_corrector_grads(bssn_corrector_t* c, float* host);
 /* HOST arrays of 24: input offset, input scale (> 0), output scale (> 0). */
 bssn_status_t bssn_corrector_set_scales(bssn_corrector_t* c, const double* in_offset, const double* in_scale,
                                         const double* out_scale);
+/* Per-sample output scale (HOST double[24], each > 0; 1 after create): the
+ * packed training targets become (target - coarse) * out_scale / step_scale
+ * and bssn_corrector_apply adds output * step_scale / out_scale, so that the
+ * network learns corrections relative to the size of the sample's own coarse
+ * step. Applies to the packs and applies that follow. */
+bssn_status_t bssn_corrector_set_step_scale(bssn_corrector_t* c, const double* step_scale);
 /* Network output for S samples of raw input x (DEVICE, BF16 bits,
  * [S][n][n][n][32] channels last): out (DEVICE FP32 [S][n^3][32]).
  * Returns BSSN_ERR_TIMEOUT if a bounded device wait gave up. Synchronizes. */

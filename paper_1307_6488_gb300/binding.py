@@ -150,6 +150,17 @@ def bounds_violations(stream=None):
     return st, c.value
 
 
+def rms_diff(grid, a, b, work, stream=None):
+    """bssn_rms_diff: per-variable RMS of a - b over interior points (numpy, 24)."""
+    L = lib()
+    L.bssn_rms_diff.argtypes = [ctypes.POINTER(Grid), _p, _p, _p, _p, ctypes.c_ulonglong, _p]
+    L.bssn_rms_diff.restype = ctypes.c_int
+    out = np.zeros(NVAR)
+    _check(L.bssn_rms_diff(ctypes.byref(grid), _ptr(a), _ptr(b), out.ctypes.data_as(_p), _ptr(work), _nbytes(work),
+                           _stream(stream)), "rms_diff")
+    return out
+
+
 def check_device(stream=None):
     """bssn_check_device: synchronizes the stream; raises BssnError with
     ERR_TIMEOUT if a bounded wait of a tiled FP32-RHS stage kernel gave up
@@ -321,6 +332,14 @@ def corrector_grads(c):
 def corrector_set_scales(c, in_offset, in_scale, out_scale):
     a = [np.ascontiguousarray(x, dtype=np.float64) for x in (in_offset, in_scale, out_scale)]
     _check(_corr_lib().bssn_corrector_set_scales(c, *[x.ctypes.data_as(_p) for x in a]), "corrector_set_scales")
+
+
+def corrector_set_step_scale(c, step_scale):
+    a = np.ascontiguousarray(step_scale, dtype=np.float64)
+    L = _corr_lib()
+    L.bssn_corrector_set_step_scale.argtypes = [_p, _p]
+    L.bssn_corrector_set_step_scale.restype = ctypes.c_int
+    _check(L.bssn_corrector_set_step_scale(c, a.ctypes.data_as(_p)), "corrector_set_step_scale")
 
 
 def corrector_forward_raw(c, S, x_bf16, out, stream=None):

@@ -68,6 +68,8 @@ bool params_ok(const bssn_grid_t* G, const bssn_params_t* P) {
 // (2 x 11 x p/2 arrays of var_stride doubles); for BSSN_FP32_RHS, two single
 // precision copies of the state (24 x var_stride floats each: a whole step
 // alternates between them) followed by the single precision tables.
+constexpr int RMS_BLOCKS = 304, RMS_THREADS = 256;
+
 struct WorkLayout {
   size_t tables;     // doubles
   size_t partials;   // doubles
@@ -83,7 +85,9 @@ WorkLayout work_layout(const bssn_grid_t& G, const bssn_params_t& P) {
   // two single-precision copies and the 22 D_x / D_y tables, Layout32
   const size_t f32 = ((2 * (size_t)NV + 2 * NM) * (size_t)L32.vs + 1) / 2;  // floats -> doubles, rounded up
   W.tables = dbl > f32 ? dbl : f32;
-  W.partials = (size_t)con_blocks(L) * 14;
+  // constraint partials (14 per block), or the per-variable RMS partials
+  // (RMS_BLOCKS x 24) and their 24 sums, whichever is larger
+  W.partials = std::max((size_t)con_blocks(L) * 14, (size_t)RMS_BLOCKS * NV + NV);
   W.finals = 16;
   W.total_bytes = (W.tables + W.partials + W.finals) * sizeof(double);
   return W;
@@ -371,6 +375,50 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe(double* out, unsigned l
   }
 }
 
+// Per-variable sums of squares of (a - b) over interior points: one partial
+// per block and variable (grid-stride over the points), then a fixed-order
+// sum of the partials, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(RMS_THREADS) k_sq_diff(Layout L, const double* __restrict__ a,
+                                                         const double* __restrict__ b, double* __restrict__ part) {
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L.npts;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % L.nx);
+    const long long r = i / L.nx;
+    const int y = (int)(r % L.ny), z = (int)(r / L.ny);
+    const long long p = L.off0 + x + y * L.sy + z * L.sz;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double d = __ldg(a + v * L.vs + p) - __ldg(b + v * L.vs + p);
+      acc[v] = fma(d, d, acc[v]);
+    }
+  }
+  __shared__ double red[RMS_THREADS / 32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double x = acc[v];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) red[warp][v] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double x = 0.0;
+    for (int w = 0; w < RMS_THREADS / 32; ++w) x += red[w][threadIdx.x];
+    part[(long long)blockIdx.x * NV + threadIdx.x] = x;
+  }
+}
+
+__global__ void k_sum_parts(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  if (threadIdx.x >= NV) return;
+  double x = 0.0;
+  for (int b = 0; b < nb; ++b) x += part[(long long)b * NV + threadIdx.x];
+  out[threadIdx.x] = x;
+}
+
 // Both conversion paths on the same inputs (self-test of bssn_cvt.cuh).
 __global__ void k_test_conversions(long long n, const double* __restrict__ din, const float* __restrict__ fin,
                                    float* f_bits, float* f_hw, double* d_bits, double* d_hw) {
@@ -450,6 +498,32 @@ bssn_status_t bssn_bounds_violations(unsigned long long* count, void* stream) {
   if (e != cudaSuccess) return latch(e);
   *count = total;
   return total ? BSSN_ERR_BOUNDS : BSSN_OK;
+}
+
+bssn_status_t bssn_rms_diff(const bssn_grid_t* grid, const double* a, const double* b, double* out_rms, void* work,
+                           unsigned long long work_bytes, void* stream) {
+  if (!grid_ok(grid) || !aligned16(a) || !aligned16(b) || !aligned16(work) || !out_rms) return BSSN_ERR_INVALID_ARG;
+  const bssn_params_t P{4, 0.0, 0, 0, 0.75, 2.0, 1};  // any valid parameters: the layout depends on the grid only
+  bssn_grid_t G = *grid;
+  if (G.ghost < 3) return BSSN_ERR_INVALID_ARG;
+  if (work_bytes < work_layout(G, P).total_bytes) return BSSN_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Layout L = make_layout(G);
+  const WorkPtrs w = work_ptrs(work, G, P, BSSN_FP64);
+  const int nb = (int)std::min<long long>(RMS_BLOCKS, (L.npts + RMS_THREADS - 1) / RMS_THREADS);
+  k_sq_diff<<<nb, RMS_THREADS, 0, s>>>(L, a, b, w.part);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    k_sum_parts<<<1, 32, 0, s>>>(w.part, nb, w.part + (size_t)RMS_BLOCKS * NV);
+    e = cudaGetLastError();
+  }
+  double host[NV];
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host, w.part + (size_t)RMS_BLOCKS * NV, sizeof(host), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return latch(e);
+  for (int v = 0; v < NV; ++v) out_rms[v] = std::sqrt(host[v] / (double)L.npts);
+  return BSSN_OK;
 }
 
 bssn_status_t bssn_check_device(void* stream) {

@@ -7,10 +7,12 @@
 // channels carry zeros, the extra output channels have zero weights and get
 // zero gradients), so one tensor-core shape serves all three convolutions:
 //   forward and input-gradient ("dgrad") - an implicit GEMM with M = 128
-//     points (one tile = 128 consecutive points of a z-plane), N = 32 output
-//     channels, K = 27 taps x 32 channels: per tap the A tile is one TMA box
-//     {32 ch, X, 128/X rows, 1} of the zero-haloed channels-last activation
-//     (64-byte swizzle), the B tile the tap's 32 x 32 weight block;
+//     output entries, N = 32 output channels, K = 27 taps x 32 channels. A
+//     TMA box brings a whole slab (R + 2 rows of one input plane, all 32
+//     channels, chunk-major, unswizzled) into shared memory once; the A
+//     operand of each of the 9 in-plane taps is that slab seen through a
+//     descriptor shifted by the tap's entry offset, and each slab serves the
+//     three output planes it neighbours (k_conv_tc below);
 //   weight gradient ("wgrad") - M = 4 taps x 32 input channels, N = 32 output
 //     channels, K = points (one x-row of 64 points per step), from
 //     channels-first copies of the activation (three copies pre-shifted by
@@ -726,7 +728,7 @@ __global__ void k_pack_state(Geom G, Layout L, int s, const double* __restrict__
   }
 }
 
-// Training target of sample s: (target_v - coarse_v) * out_scale_v.
+// Training target of sample s: (target_v - coarse_v) * out_scale_v / step_scale_v.
 __global__ void k_pack_target(Geom G, Layout L, int s, const double* __restrict__ coarse,
                               const double* __restrict__ target, const double* __restrict__ coef,
                               float* __restrict__ t) {
@@ -739,12 +741,14 @@ __global__ void k_pack_target(Geom G, Layout L, int s, const double* __restrict_
     float* o = t + ((long long)s * pts + i) * CH;
 #pragma unroll
     for (int c = 0; c < CH; ++c)
-      o[c] = c < NV ? (float)((target[c * L.vs + p] - coarse[c * L.vs + p]) * coef[2 * NV + c]) : 0.f;
+      o[c] = c < NV ? (float)((target[c * L.vs + p] - coarse[c * L.vs + p]) * coef[2 * NV + c] / coef[3 * NV + c])
+                    : 0.f;
   }
 }
 
 // One training pair packed into unpadded BF16 buffers: x = network input of
-// the coarse state, t = normalised correction (target - coarse) (if target).
+// the coarse state, t = normalised correction (target - coarse) * out_scale /
+// step_scale (if target).
 __global__ void k_pack_pair(Geom G, Layout L, const double* __restrict__ coarse, const double* __restrict__ target,
                             const double* __restrict__ coef, __nv_bfloat16* __restrict__ x,
                             __nv_bfloat16* __restrict__ t) {
@@ -759,7 +763,9 @@ __global__ void k_pack_pair(Geom G, Layout L, const double* __restrict__ coarse,
     for (int c = 0; c < CH; ++c) {
       const double u = c < NV ? coarse[c * L.vs + p] : 0.0;
       hx[c] = __float2bfloat16_rn(c < NV ? (float)((u - coef[c]) * coef[NV + c]) : 0.f);
-      if (target) ht[c] = __float2bfloat16_rn(c < NV ? (float)((target[c * L.vs + p] - u) * coef[2 * NV + c]) : 0.f);
+      if (target)
+        ht[c] = __float2bfloat16_rn(
+            c < NV ? (float)((target[c * L.vs + p] - u) * coef[2 * NV + c] / coef[3 * NV + c]) : 0.f);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) ((uint4*)(x + i * CH))[q] = ((const uint4*)hx)[q];
@@ -774,7 +780,7 @@ __global__ void k_bf16_to_f32(long long n, const __nv_bfloat16* __restrict__ in,
     out[i] = __bfloat162float(in[i]);
 }
 
-// state += network output / out_scale (interior, sample 0).
+// state += network output * step_scale / out_scale (interior, sample 0).
 __global__ void k_apply(Geom G, Layout L, const float* __restrict__ out, const double* __restrict__ coef,
                         double* __restrict__ u) {
   const long long pts = (long long)G.Z * G.Y * G.X;
@@ -784,7 +790,7 @@ __global__ void k_apply(Geom G, Layout L, const float* __restrict__ out, const d
     const int y = (int)(r % G.Y), z = (int)(r / G.Y);
     const long long p = L.off0 + x + y * L.sy + z * L.sz;
 #pragma unroll 4
-    for (int c = 0; c < NV; ++c) u[c * L.vs + p] += (double)out[i * CH + c] / coef[2 * NV + c];
+    for (int c = 0; c < NV; ++c) u[c * L.vs + p] += (double)out[i * CH + c] * coef[3 * NV + c] / coef[2 * NV + c];
   }
 }
 
@@ -957,7 +963,7 @@ struct bssn_corrector {
   float* adam_v = nullptr;
   __nv_bfloat16* wf = nullptr;   // [NL][27][32][32]
   __nv_bfloat16* wb = nullptr;
-  double* coef = nullptr;        // in_offset[24], in_scale[24], out_scale[24]
+  double* coef = nullptr;        // in_offset[24], in_scale[24], out_scale[24], step_scale[24]
   unsigned int* err = nullptr;
   int wg_blocks = 0, rows_per_cta = 0;
   int sms = 0;        // streaming multiprocessors (one conv CTA each)
@@ -1207,7 +1213,7 @@ bssn_status_t bssn_corrector_create(bssn_corrector_t** out, int n, int max_batch
   c->wf = (__nv_bfloat16*)p;
   if (e == cudaSuccess) e = calloc_dev(c, (size_t)NL * NTAP * CH * CH * 2, &p);
   c->wb = (__nv_bfloat16*)p;
-  if (e == cudaSuccess) e = calloc_dev(c, 3 * NV * sizeof(double), &p);
+  if (e == cudaSuccess) e = calloc_dev(c, 4 * NV * sizeof(double), &p);
   c->coef = (double*)p;
   if (e == cudaSuccess) e = calloc_dev(c, sizeof(unsigned int), &p);
   c->err = (unsigned int*)p;
@@ -1259,10 +1265,9 @@ bssn_status_t bssn_corrector_create(bssn_corrector_t** out, int n, int max_batch
     }
     e = cudaMemcpy(c->params, h.data(), np * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = refresh_weights(c, 0);
-    const std::vector<double> one(3 * NV, 1.0);
-    std::vector<double> cf(3 * NV, 1.0);
+    std::vector<double> cf(4 * NV, 1.0);
     for (int v = 0; v < NV; ++v) cf[v] = 0.0;
-    if (e == cudaSuccess) e = cudaMemcpy(c->coef, cf.data(), 3 * NV * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->coef, cf.data(), 4 * NV * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
   if (e != cudaSuccess) {
@@ -1324,6 +1329,15 @@ bssn_status_t bssn_corrector_set_scales(bssn_corrector_t* c, const double* in_of
     h[2 * NV + v] = out_scale[v];
   }
   return cudaMemcpy(c->coef, h, sizeof(h), cudaMemcpyHostToDevice) == cudaSuccess ? BSSN_OK : BSSN_ERR_CUDA;
+}
+
+bssn_status_t bssn_corrector_set_step_scale(bssn_corrector_t* c, const double* step_scale) {
+  if (!c || !step_scale) return BSSN_ERR_INVALID_ARG;
+  for (int v = 0; v < NV; ++v)
+    if (!(step_scale[v] > 0) || !std::isfinite(step_scale[v])) return BSSN_ERR_INVALID_ARG;
+  return cudaMemcpy(c->coef + 3 * NV, step_scale, NV * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess
+             ? BSSN_OK
+             : BSSN_ERR_CUDA;
 }
 
 bssn_status_t bssn_corrector_forward_raw(bssn_corrector_t* c, int S, const void* x_bf16, float* out, void* stream) {

@@ -49,26 +49,44 @@ class Problem:
 
 
 class Stepper:
-    """Device buffers and plain steps for one Problem."""
+    """Device buffers and plain steps for one Problem. The coarse steps use
+    `prec`; the fine steps use `fine_prec` (default: the same)."""
 
-    def __init__(self, prob, prec=B.FP64):
+    def __init__(self, prob, prec=B.FP64, fine_prec=None):
         self.p = prob
         self.prec = prec
+        self.fine_prec = prec if fine_prec is None else fine_prec
         self.src_c = B.upload(prob.uc, prob.gc)
         self.src_f = B.upload(prob.uf, prob.gf)
         self.bufs_c = B.alloc_state(prob.gc, n=3)
         self.bufs_f = B.alloc_state(prob.gf, n=3)
         self.work_c = B.alloc_work(prob.gc, prob.params, prec)
-        self.work_f = B.alloc_work(prob.gf, prob.params, prec)
+        self.work_f = B.alloc_work(prob.gf, prob.params, self.fine_prec)
         self.work_con = B.alloc_work(prob.gc, prob.params, B.FP64)
+        self.ko_buf = self.zero = None
 
     def coarse_step(self, state):
         B.rk4_step(self.p.gc, self.p.params, self.prec, self.p.dt_c, self.p.bc, self.src_c, state, self.bufs_c,
                    self.work_c)
 
     def fine_step(self, state):
-        B.rk4_step(self.p.gf, self.p.params, self.prec, self.p.dt_f, self.p.bc, self.src_f, state, self.bufs_f,
+        B.rk4_step(self.p.gf, self.p.params, self.fine_prec, self.p.dt_f, self.p.bc, self.src_f, state, self.bufs_f,
                    self.work_f)
+
+    def step_change(self, after, before):
+        """Per-variable RMS over interior points of a coarse step's change."""
+        return B.rms_diff(self.p.gc, after, before, self.work_con)
+
+    def roughness(self, after, before=None):
+        """Per-variable RMS over interior points of the Kreiss-Oliger operator
+        applied to a coarse state (its 2r-th undivided differences over h): a
+        measure of the coarse grid's local truncation error, computed from
+        the state alone."""
+        if self.ko_buf is None:
+            self.ko_buf = B.alloc_state(self.p.gc)
+            self.zero = torch.zeros_like(self.ko_buf)
+        B.ko_dissipation(self.p.gc, self.p.params, B.FP64, after, self.ko_buf)
+        return B.rms_diff(self.p.gc, self.ko_buf, self.zero, self.work_con)
 
     def restrict(self, fine, coarse):
         B.restrict(self.p.gf, fine, self.p.gc, coarse)
@@ -84,9 +102,11 @@ class Stepper:
         return float(l2[0]) if st == B.OK else float("inf")
 
 
-def trajectory_pairs(stepper, nsteps):
-    """Coarse pairs (input, target) as device state tensors along one fine
-    trajectory of nsteps + 2 fine steps."""
+def trajectory_pairs(stepper, nsteps, measure="roughness"):
+    """Coarse pairs (input, target, size) along one fine trajectory of
+    nsteps + 2 fine steps: input and target are device states, size the
+    per-variable vector (numpy, 24) that Stepper.<measure>(input, R(f_k))
+    returns for the coarse step's output."""
     p = stepper.p
     f = stepper.src_f.clone()
     restricted = []
@@ -98,10 +118,24 @@ def trajectory_pairs(stepper, nsteps):
         if k >= 2:
             x = restricted[k - 2].clone()
             stepper.coarse_step(x)
-            pairs.append((x, restricted[k]))
+            pairs.append((x, restricted[k], getattr(stepper, measure)(x, restricted[k - 2])))
             restricted[k - 2] = None
         stepper.fine_step(f)
     return pairs
+
+
+def step_reference(pairs):
+    """Per-variable reference of the pairs' size vectors: their RMS over the
+    pairs (floored so that it is never zero)."""
+    S = np.array([q[2] for q in pairs])
+    ref = np.sqrt((S ** 2).mean(axis=0))
+    return np.maximum(ref, 1e-12 + 1e-6 * ref.max())
+
+
+def step_scale(change, ref, floor=1e-4):
+    """Output scale of one sample: its size vector relative to the
+    reference, per variable, floored at `floor`."""
+    return np.maximum(np.asarray(change) / ref, floor)
 
 
 def default_scales(pairs, grid):
@@ -109,7 +143,7 @@ def default_scales(pairs, grid):
     (host statistics of the interior): offset = mean, scale = 1/std
     (floored), output scale = 1/rms(target - input)."""
     xs, ds = [], []
-    for x, t in pairs:
+    for x, t, *_ in pairs:
         a = B.download(x, grid)[:, grid.ghost:-grid.ghost, grid.ghost:-grid.ghost, grid.ghost:-grid.ghost]
         b = B.download(t, grid)[:, grid.ghost:-grid.ghost, grid.ghost:-grid.ghost, grid.ghost:-grid.ghost]
         xs.append(a.reshape(NV, -1))
@@ -125,17 +159,21 @@ def default_scales(pairs, grid):
 
 
 class Dataset:
-    """Packed BF16 pairs on the device."""
+    """Packed BF16 pairs on the device. With step_ref, each pair's target is
+    taken relative to its own coarse step's change (step_scale)."""
 
-    def __init__(self, corrector, n):
+    def __init__(self, corrector, n, step_ref=None):
         self.c = corrector
         self.n = n
+        self.step_ref = step_ref
         self.x, self.t = [], []
 
     def add(self, pairs, grid):
-        for inp, tgt in pairs:
+        for inp, tgt, *rest in pairs:
             xb = torch.empty((self.n ** 3, CH), dtype=torch.bfloat16, device="cuda")
             tb = torch.empty_like(xb)
+            if self.step_ref is not None:
+                B.corrector_set_step_scale(self.c, step_scale(rest[0], self.step_ref))
             B.corrector_pack(self.c, grid, inp, tgt, xb, tb)
             self.x.append(xb)
             self.t.append(tb)
@@ -166,13 +204,16 @@ def train(corrector, data, epochs, batch, lr, seed=0, lr_final=None, log=None):
     return losses
 
 
-def learned_step(stepper, corrector, state, fallback_factor=2.0, scratch=None):
+def learned_step(stepper, corrector, state, fallback_factor=2.0, scratch=None, step_ref=None, measure="roughness"):
     """One learned coarse step in place. Returns (used_fallback, H_learned,
-    H_plain)."""
+    H_plain). With step_ref, the correction is scaled by this step's own
+    size vector (Stepper.<measure>, as the training targets were)."""
     p = stepper.p
     before = state.clone() if scratch is None else scratch.copy_(state)
     stepper.coarse_step(state)
     h_plain = stepper.ham_l2(state)
+    if step_ref is not None:
+        B.corrector_set_step_scale(corrector, step_scale(getattr(stepper, measure)(state, before), step_ref))
     B.corrector_apply(corrector, p.gc, state)
     B.fill_ghosts(p.gc, p.bc, stepper.src_c if p.bc == 1 else None, state)
     h_learned = stepper.ham_l2(state)
@@ -186,7 +227,7 @@ def learned_step(stepper, corrector, state, fallback_factor=2.0, scratch=None):
     return False, h_learned, h_plain
 
 
-def evaluate(stepper, corrector, nsteps, fallback_factor=2.0):
+def evaluate(stepper, corrector, nsteps, fallback_factor=2.0, step_ref=None, measure="roughness"):
     """Evolve nsteps coarse steps three ways - plain coarse, learned, and the
     fine method restricted - and return the errors of plain and learned
     against the restricted fine solution (RMS over interior points and
@@ -203,7 +244,7 @@ def evaluate(stepper, corrector, nsteps, fallback_factor=2.0):
     fallbacks = 0
     for _ in range(nsteps):
         stepper.coarse_step(plain)
-        fb, _, _ = learned_step(stepper, corrector, learned, fallback_factor)
+        fb, _, _ = learned_step(stepper, corrector, learned, fallback_factor, step_ref=step_ref, measure=measure)
         fallbacks += int(fb)
         stepper.fine_step(fine)
         stepper.fine_step(fine)

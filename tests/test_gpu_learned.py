@@ -75,6 +75,54 @@ def test_apply_adds_unscaled_network_output(setup):
     np.testing.assert_array_equal(got, want)
 
 
+def test_step_scale_divides_targets_and_multiplies_corrections(setup):
+    torch, grid, u, tgt, off, isc, osc, c = setup
+    sc = np.random.default_rng(5).uniform(0.25, 4.0, 24)
+    B.corrector_set_step_scale(c, sc)
+    try:
+        xb = torch.empty((N ** 3, 32), dtype=torch.bfloat16, device="cuda")
+        tb = torch.empty_like(xb)
+        state = B.upload(u, grid)
+        B.corrector_pack(c, grid, state, B.upload(tgt, grid), xb, tb)
+        I, T = interior_points(u), interior_points(tgt)
+        t = tb.cpu().view(torch.int16).numpy()
+        np.testing.assert_array_equal(t[:, :24], bf16_bits(torch, (T - I) * osc / sc))
+        out = torch.empty((N ** 3, 32), dtype=torch.float32, device="cuda")
+        B.corrector_forward_raw(c, 1, xb, out)
+        B.corrector_apply(c, grid, state)
+        torch.cuda.synchronize()
+        o = out.cpu().numpy().astype(np.float64)
+        want = u.copy()
+        want[:, G:-G, G:-G, G:-G] += (o[:, :24] * sc / osc).T.reshape(24, N, N, N)
+        np.testing.assert_array_equal(B.download(state, grid), want)
+        with pytest.raises(B.BssnError):
+            B.corrector_set_step_scale(c, np.where(np.arange(24) == 3, 0.0, 1.0))
+    finally:
+        B.corrector_set_step_scale(c, np.ones(24))
+
+
+def test_rms_diff_and_roughness(setup):
+    torch, grid, u, tgt, off, isc, osc, c = setup
+    from paper_1307_6488_gb300 import learned as LR
+    params = B.make_params(fd_order=4, ko_eps=0.1, lapse=0, shift=0, eta=2.0)
+    work = B.alloc_work(grid, params, B.FP64)
+    a, b = B.upload(u, grid), B.upload(tgt, grid)
+    got = B.rms_diff(grid, a, b, work)
+    want = np.sqrt(((interior_points(u) - interior_points(tgt)) ** 2).mean(axis=0))
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=0)
+    assert np.all(B.rms_diff(grid, a, a, work) == 0)
+    # roughness: the RMS of the Kreiss-Oliger operator's output over the interior
+    st = LR.Stepper.__new__(LR.Stepper)
+    st.p = type("P", (), {"gc": grid, "params": params})()
+    st.work_con, st.ko_buf, st.zero = work, None, None
+    r = st.roughness(a)
+    ko = B.alloc_state(grid)
+    B.ko_dissipation(grid, params, B.FP64, a, ko)
+    k = interior_points(B.download(ko, grid))
+    np.testing.assert_allclose(r, np.sqrt((k ** 2).mean(axis=0)), rtol=1e-12, atol=0)
+    assert np.all(r > 0)
+
+
 def _bl_stepper(masses=(0.45, 0.55), separation=2.7):
     from paper_1307_6488_gb300 import learned as LR
     return LR, LR.Stepper(LR.Problem("bl", N, masses=masses, separation=separation))
