@@ -506,7 +506,9 @@ long long bssn_corrector_param_count(void);
 /* Copy the FP32 parameters from (write = 0) or to (write = 1) the HOST array. */
 bssn_status_t bssn_corrector_params(bssn_corrector_t* c, float* host, int write);
 /* Copy layer `layer`'s (0..4) pre-activation output of the last forward pass,
- * S samples, to out (DEVICE FP32 [S][n^3][32]). Synchronizes. */
+ * S samples, to out (DEVICE FP32 [S][n^3][32]). Synchronizes. After
+ * bssn_corrector_forward_raw the last layer's output is only in that call's
+ * own out buffer (layer 4 here then holds the last training or apply pass). */
 bssn_status_t bssn_corrector_layer_output(bssn_corrector_t* c, int layer, int S, float* out);
 /* Copy the gradient of the last loss evaluation to the HOST array (packed). */
 bssn_status_t bssn_corrector_grads(bssn_corrector_t* c, float* host);

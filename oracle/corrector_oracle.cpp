@@ -1,7 +1,8 @@
 // Corrector oracle: plain FP64 CPU reference of the learned corrector's
 // arithmetic - 3x3x3 convolution (zero padding) forward and backward, the
-// exact erf-based GELU and its derivative, and the whole network's mean
-// squared error with its gradient.
+// tanh form of GELU (Hendrycks and Gimpel, "Gaussian Error Linear Units",
+// 2016: 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)))) and its derivative,
+// and the whole network's mean squared error with its gradient.
 //
 // TEST INFRASTRUCTURE ONLY (see bssn_oracle.cpp); shares no code with the
 // CUDA library.
@@ -19,10 +20,14 @@
 
 namespace {
 
-inline double gelu(double x) { return 0.5 * x * (1.0 + std::erf(x / std::sqrt(2.0))); }
+// u(x) = sqrt(2/pi) (x + 0.044715 x^3); GELU(x) = x (1 + tanh u) / 2
+inline double gelu_u(double x) { return std::sqrt(2.0 / M_PI) * (x + 0.044715 * x * x * x); }
+inline double gelu(double x) { return 0.5 * x * (1.0 + std::tanh(gelu_u(x))); }
+// d/dx: (1 + tanh u) / 2 + x (1 - tanh^2 u) u'(x) / 2
 inline double gelu_grad(double x) {
-  const double pdf = std::exp(-0.5 * x * x) / std::sqrt(2.0 * M_PI);
-  return 0.5 * (1.0 + std::erf(x / std::sqrt(2.0))) + x * pdf;
+  const double t = std::tanh(gelu_u(x));
+  const double du = std::sqrt(2.0 / M_PI) * (1.0 + 3.0 * 0.044715 * x * x);
+  return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * du;
 }
 
 struct Box {

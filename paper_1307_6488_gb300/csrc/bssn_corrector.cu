@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -43,8 +44,6 @@ namespace {
 constexpr int CH = 32;
 constexpr int NL = 5;
 constexpr int NTAP = 27;
-constexpr int BM = 128;
-constexpr int A_BYTES = BM * CH * 2;      // 8 KB per A tile
 constexpr int W_TAP_BYTES = CH * CH * 2;  // 2 KB per tap
 constexpr int WG_STAGES = 4;
 constexpr int XOFF = 8;                   // interior column of the channels-first copies
@@ -84,17 +83,25 @@ __device__ __forceinline__ void store_point(const Geom& G, __nv_bfloat16* buf, i
 #pragma unroll
   for (int q = 0; q < 4; ++q) p[q * cs] = ((const uint4*)h)[q];
 }
-__device__ __forceinline__ void load_point(const Geom& G, const __nv_bfloat16* buf, int s, int z, int y, int x,
-                                           __nv_bfloat16* h) {
-  const uint4* p = (const uint4*)buf + chunk_off(G, s, z + 1, 0, y + 1, x + 1);
-  const long long cs = chunk_stride(G);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) ((uint4*)h)[q] = __ldg(p + q * cs);
-}
 
-__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+// The activation: the tanh form of GELU (Hendrycks and Gimpel 2016),
+// x (1 + tanh u) / 2 with u = sqrt(2/pi) (x + 0.044715 x^3), on the hardware
+// tanh (tanh.approx.f32, relative error ~2^-11, far below the BF16 rounding
+// of the stored activation); a few instructions against ~25 for erff.
+__device__ __forceinline__ float tanh_hw(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float gelu_f(float x) {
+  const float u = 0.7978845608028654f * fmaf(0.044715f * x, x * x, x);
+  return 0.5f * x * (1.f + tanh_hw(u));
+}
 __device__ __forceinline__ float gelu_grad_f(float x) {
-  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+  const float u = 0.7978845608028654f * fmaf(0.044715f * x, x * x, x);
+  const float t = tanh_hw(u);
+  const float du = 0.7978845608028654f * fmaf(0.134145f * x, x, 1.f);
+  return 0.5f * (1.f + t) + 0.5f * x * (1.f - t * t) * du;
 }
 
 // ---------------------------------------------------------------- forward / dgrad
@@ -115,34 +122,59 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
 // are discarded), the A operand of every tap is the same slab seen through a
 // shifted no-swizzle descriptor (core matrices 8 entries x 16 bytes, SBO =
 // 128 bytes, LBO = one chunk), and T tiles of 128 entries cover the R rows.
-//   warp 4 (one lane)  loads the 27 weight taps once and streams slabs into a
-//                      4-deep ring (an input plane serves three output planes);
-//   warp 5 (one lane)  issues 27 taps x 2 MMAs (K = 16) per tile into one of
-//                      two TMEM accumulator sets (T x 32 columns each) and
-//                      releases a slab at its last use; it never waits for
-//                      an MMA to finish;
-//   warps 0-3          read the accumulators out (TMEM lanes 32w .. 32w+31)
-//                      and run the epilogue while the next output plane
-//                      accumulates into the other set.
+//
+// The three dz taps share their A operand. Input plane i feeds output planes
+// i + 1, i and i - 1 through the weights of dz = 0, 1, 2, so one MMA with N =
+// 96 (the three dz blocks of one in-plane tap stacked along N; the weights sit
+// in shared memory as [dy dx][dz][32 co][32 ci]) adds all three
+// contributions, each into its own output plane's accumulator. TMEM holds, per
+// tile, K blocks of 32 columns; output plane z0 + q of a unit accumulates in
+// block L - 1 - q, so the blocks of planes i + 1, i, i - 1 are adjacent and in
+// dz order. At the unit's first and last two input planes fewer outputs lie
+// in the unit and the MMA narrows to N = 32 or 64. Every MMA accumulates:
+// the epilogue writes zeros into a block when it has read it (and into every
+// block at the start), before handing it back.
+//   warp 16 (one lane) loads the 27 weight taps once and streams slabs into a
+//                      4-deep ring;
+//   warp 17            issues 9 taps x 2 MMAs (K = 16) per tile and input
+//                      plane (the whole warp runs the loop, one elected lane
+//                      issues), releases the slab when they finish and hands
+//                      a block to the epilogue after its last contribution;
+//                      it never waits for an MMA to finish;
+//   warps 0-15         read the accumulators out (warp w: TMEM lanes
+//                      32 (w % 4) .. +31, channels 8 (w / 4) .. +7), run the
+//                      epilogue and zero the block; four warps per lane
+//                      quarter keep enough loads and stores in flight.
 // Every wait is bounded; a role that times out sets the error word and the
 // CTA-wide abort flag, the others leave their loops, in-flight copies and
 // MMAs are waited for (bounded) and TMEM is freed.
-constexpr int CONV_THREADS = 192;
+constexpr int CONV_THREADS = 576;
+constexpr int EPI_WARPS = 16;
+constexpr int WG_THREADS = 192;
 constexpr int SLABS = 4;
+constexpr int KMAX = 16;  // accumulator blocks per tile at T = 1 (512 TMEM columns)
 
 struct ConvPlan {
   int R;              // output rows per unit
   int T;              // 128-entry M tiles covering R rows of X+1 entries
-  int L;              // output planes per unit (set per call)
+  int K;              // accumulator blocks (of 32 columns) per tile: the most planes a unit may have
+  int L;              // output planes per unit (set per call, <= K)
   int nyb, nzs;       // row blocks, plane runs
   int chunk_bytes;    // (R+2)(X+1) x 16
   int plane_bytes;    // 4 chunks
+  int slab_stride;    // plane_bytes rounded up to 128 (TMA destinations are 128-byte aligned)
   int tail_bytes;     // past the last slab: reads of discarded rows
-  int tmem_cols;      // power of two >= 2 T 32
+  int tmem_cols;      // power of two >= T K 32
   int smem;           // dynamic shared memory
   int slab_off;       // offset of slab 0 from the 1024-aligned base
   int bar_off;        // offset of the barriers
 };
+
+// 8 channels (one 16-byte chunk, channels 8 q .. 8 q + 7) of interior point (s, z, y, x)
+__device__ __forceinline__ void store_chunk(const Geom& G, __nv_bfloat16* buf, int s, int z, int y, int x, int q,
+                                            const __nv_bfloat16* v) {
+  *((uint4*)buf + chunk_off(G, s, z + 1, q, y + 1, x + 1)) = *(const uint4*)v;
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(CONV_THREADS, 1)
@@ -151,14 +183,14 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
               const float* __restrict__ zprev, int gelu, unsigned int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* Wt = base;                // 27 taps x [32 co][32 ci], 64-byte swizzle
-  uint8_t* slab = base + P.slab_off;  // SLABS x plane_bytes; the 16 bytes before it are zero
+  uint8_t* Wt = base;                // [9 (dy, dx)][3 dz][32 co][32 ci], 64-byte swizzle
+  uint8_t* slab = base + P.slab_off;  // SLABS x slab_stride; the 16 bytes before it are zero
   uint64_t* bars = (uint64_t*)(base + P.bar_off);
   uint64_t* full = bars;
   uint64_t* empty = bars + SLABS;
-  uint64_t* tfull = bars + 2 * SLABS;   // [2] accumulator set complete
-  uint64_t* tempty = tfull + 2;         // [2] accumulator set read out (one arrive per epilogue warp)
-  uint64_t* wbar = tempty + 2;
+  uint64_t* tfull = bars + 2 * SLABS;   // [KMAX] block complete
+  uint64_t* tempty = tfull + KMAX;      // [KMAX] block read out and zeroed (one arrive per epilogue warp)
+  uint64_t* wbar = tempty + KMAX;
   uint64_t* drain = wbar + 1;           // all MMAs of this CTA finished
   uint32_t* tslot = (uint32_t*)(drain + 1);
   __shared__ volatile int abort_flag;
@@ -175,11 +207,16 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
     len = min(P.L, G.Z - z0);
   };
 
-  // zero the entry before slab 0 and the tail (read only for discarded rows)
+  // zero the entry before slab 0, the gap after each slab (its last entry is
+  // the entry before the next slab: the x = -1 pad of tap dx = -1 at the
+  // first output entry) and the tail (read only for discarded rows)
   {
     uint32_t* lead = (uint32_t*)(slab - 128);
     if (tid < 32) lead[tid] = 0u;
-    uint32_t* tail = (uint32_t*)(slab + SLABS * P.plane_bytes);
+    const int gap = P.slab_stride - P.plane_bytes;
+    for (int i = tid; i < SLABS * (gap / 4); i += blockDim.x)
+      ((uint32_t*)(slab + (i / (gap / 4)) * P.slab_stride + P.plane_bytes))[i % (gap / 4)] = 0u;
+    uint32_t* tail = (uint32_t*)(slab + SLABS * P.slab_stride);
     for (int i = tid; i < P.tail_bytes / 4; i += blockDim.x) tail[i] = 0u;
     tc::fence_proxy_async();
   }
@@ -189,9 +226,9 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
       tc::mbar_init(&full[i], 1);
       tc::mbar_init(&empty[i], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < KMAX; ++b) {
       tc::mbar_init(&tfull[b], 1);
-      tc::mbar_init(&tempty[b], 4);
+      tc::mbar_init(&tempty[b], EPI_WARPS);
     }
     tc::mbar_init(wbar, 1);
     tc::mbar_init(drain, 1);
@@ -202,14 +239,22 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t taddr = *tslot;
-  constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, 32);
   const bool any = (int)blockIdx.x < units;
+  const uint32_t tile_cols = (uint32_t)(P.K * 32);
+  // the next layer may be scheduled onto SMs as this grid's CTAs leave them
+  if (tid == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
-  if (warp == 4) {
+  if (warp == EPI_WARPS) {
     // ---- TMA producer
     if (lane == 0 && any) {
       tc::mbar_expect_tx(wbar, NTAP * W_TAP_BYTES);
-      for (int k = 0; k < NTAP; ++k) tc::tma_load_2d(Wt + k * W_TAP_BYTES, &tmW, 0, k * CH, wbar);
+      // tap k = 9 dz + 3 (dy + 1) + (dx + 1) goes to slot 3 (k % 9) + k / 9
+      for (int k = 0; k < NTAP; ++k)
+        tc::tma_load_2d(Wt + (3 * (k % 9) + k / 9) * W_TAP_BYTES, &tmW, 0, k * CH, wbar);
+      // launched as a programmatic dependent of the previous layer: everything
+      // above overlapped its tail; its output is read only from here on (a
+      // no-op for an ordinary launch)
+      asm volatile("griddepcontrol.wait;" ::: "memory");
       uint32_t g = 0;  // slabs issued (sequence over all units)
       bool ok = true;
       for (int u = blockIdx.x; ok && u < units; u += gridDim.x) {
@@ -226,7 +271,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
           tc::mbar_expect_tx(&full[buf], (uint32_t)P.plane_bytes);
           // padded plane z0 + k holds input plane z0 - 1 + k; padded row yb R
           // is output row yb R - 1
-          tc::tma_load_5d(slab + buf * P.plane_bytes, &tmA, 0, 1, yb * P.R, 0, s * (G.Z + 2) + z0 + k, &full[buf]);
+          tc::tma_load_5d(slab + buf * P.slab_stride, &tmA, 0, 1, yb * P.R, 0, s * (G.Z + 2) + z0 + k, &full[buf]);
           ++g;
         }
       }
@@ -235,85 +280,107 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
         (void)tc::mbar_wait(&full[q % SLABS], (q / SLABS) & 1, 100000000ull);
       (void)tc::mbar_wait(wbar, 0, 100000000ull);
     }
-  } else if (warp == 5) {
-    // ---- MMA issuer
-    if (lane == 0 && any) {
-      bool ok = tc::mbar_wait_or_abort(wbar, 0, &abort_flag);
+  } else if (warp == EPI_WARPS + 1) {
+    // ---- MMA issuer: the whole warp runs the loop on warp-uniform
+    // descriptors and one elected lane issues each MMA and commit
+    if (any) {
+      bool ok = tc::warp_wait_or_abort(wbar, 0, &abort_flag);
       const uint32_t slab0 = tc::smem_u32(slab);
       const uint64_t w_desc0 = tc::smem_desc(tc::smem_u32(Wt), 16, 512, tc::SWZ_64B);
-      // entry shift of tap (dy, dx) relative to the output entry, as a
-      // descriptor address increment (entries of 16 bytes): (1 + dy)(X+1) + dx
-      int tap_off[9];
-#pragma unroll
-      for (int t = 0; t < 9; ++t) tap_off[t] = XS * (t / 3) + (t % 3) - 1;
+      constexpr uint32_t IDESC32 = tc::idesc_bf16_f32(128, 32), IDESC64 = tc::idesc_bf16_f32(128, 64),
+                         IDESC96 = tc::idesc_bf16_f32(128, 96);
       const uint32_t k_half = (uint32_t)(2 * P.chunk_bytes) >> 4;
-      uint32_t g = 0, step = 0;  // slab sequence at the unit's first plane; output planes done
-      for (int u = blockIdx.x; ok && u < units; u += gridDim.x) {
+      uint32_t g = 0;  // slab sequence at the unit's first input plane
+      uint32_t use = 0;  // units done: each unit uses every block once
+      for (int u = blockIdx.x; ok && u < units; u += gridDim.x, ++use) {
         int s, yb, z0, len;
         unit_pos(u, s, yb, z0, len);
-        for (int o = 0; ok && o < len; ++o, ++step) {
-          const uint32_t a = step & 1;
-          if (step >= 2 && !tc::mbar_wait_or_abort(&tempty[a], ((step >> 1) - 1) & 1, &abort_flag)) {
+        const uint32_t par = use & 1;
+        for (int k = 0; ok && k < len + 2; ++k) {
+          // input plane z0 - 1 + k feeds output planes q = k - dz (dz = 0, 1, 2)
+          // of the unit that exist: q_lo .. q_hi
+          const int q_hi = min(len - 1, k), q_lo = max(0, k - 2);
+          const int n = q_hi - q_lo + 1;
+          const int dz0 = k - q_hi;
+          // the first contribution to plane q = k: its block must be empty
+          if (k < len && !tc::warp_wait_or_abort(&tempty[P.L - 1 - k], par, &abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t gg = g + (uint32_t)k;
+          const uint32_t buf = gg % SLABS;
+          if (!tc::warp_wait_or_abort(&full[buf], (gg / SLABS) & 1, &abort_flag)) {
             ok = false;
             break;
           }
           tc::fence_after_sync();
-          const uint32_t dbase = taddr + a * (uint32_t)(P.T * 32);
-          for (int dz = 0; dz < 3; ++dz) {
-            const uint32_t accum0 = dz ? 1u : 0u;  // the first MMA of a tile starts the sum
-            const uint32_t gg = g + o + dz;  // the slab of input plane z0 + o + dz - 1
-            const uint32_t buf = gg % SLABS;
-            if (!tc::mbar_wait_or_abort(&full[buf], (gg / SLABS) & 1, &abort_flag)) {
-              ok = false;
-              break;
-            }
-            tc::fence_after_sync();
-            // descriptors change only in the start-address field (bits 0-13,
-            // bytes / 16): an entry shift adds the entry count, the second K
-            // half adds two chunks, the next tap's weights add 2 KB
-            const uint64_t a_plane = tc::smem_desc(slab0 + buf * (uint32_t)P.plane_bytes, (uint32_t)P.chunk_bytes, 128,
-                                                   tc::SWZ_NONE);
-            const uint64_t b_plane = w_desc0 + (uint64_t)(dz * 9 * (W_TAP_BYTES >> 4));
-            for (int j = 0; j < P.T; ++j) {
-              const uint64_t a_tile = a_plane + (uint64_t)(128 * j);  // 128 entries (of 16 bytes) per tile
-              const uint32_t d = dbase + (uint32_t)(j * 32);
+          // descriptors change only in the start-address field (bits 0-13,
+          // bytes / 16): tap (dy, dx) shifts A by (1 + dy)(X+1) + dx entries,
+          // the second K half adds two chunks (A) or 32 bytes (B), the next
+          // tap's weights add 6 KB and the next dz block 2 KB
+          const uint64_t a_plane =
+              tc::smem_desc(slab0 + buf * (uint32_t)P.slab_stride, (uint32_t)P.chunk_bytes, 128, tc::SWZ_NONE);
+          const uint64_t b_plane = w_desc0 + (uint64_t)(dz0 * (W_TAP_BYTES >> 4));
+          const uint32_t idesc = n == 3 ? IDESC96 : (n == 2 ? IDESC64 : IDESC32);
+          const uint32_t dcol = (uint32_t)(32 * (P.L - 1 - q_hi));
+          for (int j = 0; j < P.T; ++j) {
+            const uint64_t a_tile = a_plane + (uint64_t)(128 * j) - 1;  // 128 entries (of 16 bytes) per tile
+            const uint32_t d = taddr + (uint32_t)j * tile_cols + dcol;
 #pragma unroll
-              for (int t = 0; t < 9; ++t) {
+            for (int t = 0; t < 9; ++t) {
+              const uint64_t a_tap = a_tile + (uint64_t)(XS * (t / 3) + (t % 3));
 #pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                  const uint64_t ad = a_tile + (uint64_t)(int64_t)tap_off[t] + (uint64_t)(kk * k_half);
-                  const uint64_t bd = b_plane + (uint64_t)(t * (W_TAP_BYTES >> 4) + 2 * kk);
-                  tc::mma_bf16(d, ad, bd, IDESC, (t | kk) ? 1u : accum0);
-                }
-              }
+              for (int kk = 0; kk < 2; ++kk)
+                tc::mma_bf16_elect(d, a_tap + (uint64_t)(kk * k_half),
+                                   b_plane + (uint64_t)(t * (3 * W_TAP_BYTES >> 4) + 2 * kk), idesc, 1u);
             }
-            // release slabs at their last use: input plane o at dz = 0, the
-            // last two planes of the unit after the unit's last output plane
-            if (dz == 0) tc::mma_commit(&empty[buf]);
-            if (dz > 0 && o == len - 1) tc::mma_commit(&empty[buf]);
           }
-          if (ok) tc::mma_commit(&tfull[a]);
+          tc::mma_commit_elect(&empty[buf]);  // the slab is free once these MMAs finish
+          // plane q = k - 2 has had its last contribution
+          if (k >= 2) tc::mma_commit_elect(&tfull[P.L - 1 - (k - 2)]);
+        }
+        // planes past the end of the grid (a short last run) are handed over
+        // empty so that every block completes once per unit
+        for (int q = len; ok && q < P.L; ++q) {
+          if (!tc::warp_wait_or_abort(&tempty[P.L - 1 - q], par, &abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc::mma_commit_elect(&tfull[P.L - 1 - q]);
         }
         g += (uint32_t)(len + 2);
       }
-      if (!ok) {
+      if (!ok && lane == 0) {
         if (!abort_flag) atomicOr(err, 1u);
         abort_flag = 1;
       }
-      // every MMA this thread issued has finished before TMEM is freed
-      tc::mma_commit(drain);
-      (void)tc::mbar_wait(drain, 0, 100000000ull);
+      // every MMA this warp issued has finished before TMEM is freed
+      tc::mma_commit_elect(drain);
+      (void)tc::warp_wait(drain, 0, 100000000ull);
     }
   } else {
-    // ---- epilogue (warps 0-3)
-    uint32_t step = 0;
+    // ---- epilogue (warps 0-15): lanes 32 (warp % 4) .. +31, channels 8 cq .. 8 cq + 7
+    const int cq = warp >> 2;
+    const uint32_t lane_base = taddr + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(8 * cq);
+    float bq[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) bq[c] = MODE == 0 ? __ldg(bias + 8 * cq + c) : 0.f;
+    // every block starts zeroed and empty
+    for (int j = 0; j < P.T; ++j)
+      for (int b = 0; b < P.K; ++b) tc::tmem_st8_zero(lane_base + (uint32_t)j * tile_cols + (uint32_t)(32 * b));
+    tc::tmem_wait_st();
+    tc::fence_before_sync();
+    __syncwarp();
+    if (lane == 0)
+      for (int b = 0; b < P.K; ++b) tc::mbar_arrive(&tempty[b]);
+    uint32_t use = 0;
     bool ok = true;
-    for (int u = blockIdx.x; ok && u < units; u += gridDim.x) {
+    for (int u = blockIdx.x; ok && u < units; u += gridDim.x, ++use) {
       int s, yb, z0, len;
       unit_pos(u, s, yb, z0, len);
-      for (int o = 0; o < len; ++o, ++step) {
-        const uint32_t a = step & 1;
-        ok = tc::mbar_wait_or_abort(&tfull[a], (step >> 1) & 1, &abort_flag);
+      for (int q = 0; q < P.L; ++q) {
+        const int b = P.L - 1 - q;
+        ok = tc::mbar_wait_or_abort(&tfull[b], use & 1, &abort_flag);
         ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
         if (!ok) {
           if (lane == 0) {
@@ -323,54 +390,53 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
           break;
         }
         tc::fence_after_sync();
-        const int z = z0 + o;
-        for (int j = 0; j < P.T; ++j) {
-          float acc[32];
-          tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + a * (uint32_t)(P.T * 32) + (uint32_t)(j * 32), acc);
-          if (j == P.T - 1) {
-            // registers hold the last tile: hand the set back to the MMA warp
-            tc::fence_before_sync();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&tempty[a]);
-          }
-          const int e = XS + 128 * j + 32 * warp + lane;
+        const int z = z0 + q;
+        for (int j = 0; q < len && j < P.T; ++j) {
+          const uint32_t col = lane_base + (uint32_t)j * tile_cols + (uint32_t)(32 * b);
+          float acc[8];
+          tc::tmem_ld8(col, acc);
+          tc::tmem_st8_zero(col);
+          const int e = XS + 128 * j + 32 * (warp & 3) + lane;
           const int row = e / XS, x = e - row * XS;
           const int y = yb * P.R + row - 1;
           if (x >= G.X || row > P.R || y >= G.Y) continue;
           const long long pt = (((long long)s * G.Z + z) * G.Y + y) * G.X + x;
+          __align__(16) __nv_bfloat16 hv[8];
           if (MODE == 0) {
 #pragma unroll
-            for (int c = 0; c < 32; ++c) acc[c] += __ldg(bias + c);
+            for (int c = 0; c < 8; ++c) acc[c] += bq[c];
             if (zout) {
-              float4* zo = (float4*)(zout + pt * CH);
-#pragma unroll
-              for (int q = 0; q < 8; ++q)
-                zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+              float4* zo = (float4*)(zout + pt * CH + 8 * cq);
+              zo[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+              zo[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
             }
             if (act_out) {
-              __align__(16) __nv_bfloat16 h[32];
 #pragma unroll
-              for (int c = 0; c < 32; ++c) h[c] = __float2bfloat16_rn(gelu ? gelu_f(acc[c]) : acc[c]);
-              store_point(G, act_out, s, z, y, x, h);
+              for (int c = 0; c < 8; ++c) hv[c] = __float2bfloat16_rn(gelu ? gelu_f(acc[c]) : acc[c]);
+              store_chunk(G, act_out, s, z, y, x, cq, hv);
             }
           } else {
             if (zprev) {
-              const float4* zp = (const float4*)(zprev + pt * CH);
+              const float4* zp = (const float4*)(zprev + pt * CH + 8 * cq);
 #pragma unroll
-              for (int q = 0; q < 8; ++q) {
-                const float4 v = __ldg(zp + q);
-                acc[4 * q] *= gelu_grad_f(v.x);
-                acc[4 * q + 1] *= gelu_grad_f(v.y);
-                acc[4 * q + 2] *= gelu_grad_f(v.z);
-                acc[4 * q + 3] *= gelu_grad_f(v.w);
+              for (int q4 = 0; q4 < 2; ++q4) {
+                const float4 v = __ldg(zp + q4);
+                acc[4 * q4] *= gelu_grad_f(v.x);
+                acc[4 * q4 + 1] *= gelu_grad_f(v.y);
+                acc[4 * q4 + 2] *= gelu_grad_f(v.z);
+                acc[4 * q4 + 3] *= gelu_grad_f(v.w);
               }
             }
-            __align__(16) __nv_bfloat16 h[32];
 #pragma unroll
-            for (int c = 0; c < 32; ++c) h[c] = __float2bfloat16_rn(acc[c]);
-            store_point(G, act_out, s, z, y, x, h);
+            for (int c = 0; c < 8; ++c) hv[c] = __float2bfloat16_rn(acc[c]);
+            store_chunk(G, act_out, s, z, y, x, cq, hv);
           }
         }
+        // zeros written, then the block goes back to the MMA warp
+        tc::tmem_wait_st();
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&tempty[b]);
       }
     }
   }
@@ -382,11 +448,11 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
 // ---------------------------------------------------------------- wgrad
 // D[(q, ci)][co] = sum over this CTA's rows of sum_x act(p + off_{tap q}, ci) g(p, co),
 // tap q = min(4 * group + q, 26); one K step = one x-row of 64 points.
-// Warp-specialised like k_conv_tc: warp 4 streams rows through the TMA ring,
+// Warp-specialised: warp 4 streams rows through the TMA ring,
 // warp 5 issues the MMAs without waiting on them, warps 0-3 read the single
 // accumulator out at the end.
 template <int XW>
-__global__ void __launch_bounds__(CONV_THREADS, 2)
+__global__ void __launch_bounds__(WG_THREADS, 2)
     k_wgrad_tc(const __grid_constant__ CUtensorMap tmXm, const __grid_constant__ CUtensorMap tmX0,
                const __grid_constant__ CUtensorMap tmXp, const __grid_constant__ CUtensorMap tmG, Geom G,
                int rows_per_cta, float* __restrict__ partial, unsigned int* err) {
@@ -621,22 +687,6 @@ __global__ void k_pad_copy(Geom G, const __nv_bfloat16* __restrict__ in, __nv_bf
     const long long r2 = r / G.Y;
     const int z = (int)(r2 % G.Z), s = (int)(r2 / G.Z);
     store_point(G, out, s, z, y, x, in + i * CH);
-  }
-}
-
-// Padded BF16 interior -> unpadded FP32 [pts][32].
-__global__ void k_unpad_f32(Geom G, const __nv_bfloat16* __restrict__ in, float* __restrict__ out) {
-  const long long pts = (long long)G.S * G.Z * G.Y * G.X;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < pts; i += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(i % G.X);
-    const long long r = i / G.X;
-    const int y = (int)(r % G.Y);
-    const long long r2 = r / G.Y;
-    const int z = (int)(r2 % G.Z), s = (int)(r2 / G.Z);
-    __align__(16) __nv_bfloat16 h[CH];
-    load_point(G, in, s, z, y, x, h);
-#pragma unroll 8
-    for (int c = 0; c < CH; ++c) out[i * CH + c] = __bfloat162float(h[c]);
   }
 }
 
@@ -967,7 +1017,7 @@ struct bssn_corrector {
   unsigned int* err = nullptr;
   int wg_blocks = 0, rows_per_cta = 0;
   int sms = 0;        // streaming multiprocessors (one conv CTA each)
-  ConvPlan conv{};    // slab geometry of the convolutions (R, T, sizes)
+  int conv_smem = 0;  // the most dynamic shared memory a convolution plan of this grid asks for
   long long adam_t = 0;
 };
 
@@ -993,52 +1043,69 @@ Geom geom_for(const bssn_corrector* c, int S) {
   return G;
 }
 
-// Slab geometry for an X-wide grid: the row count R whose R (X+1) output
-// entries fill the T 128-entry tiles best, with four slabs, the weights and
-// the tail within the shared-memory limit, T <= 8 (two accumulator sets in
-// 512 TMEM columns) and 128-byte aligned slabs. Returns false if none fits.
-bool make_conv_plan(int X, int Y, ConvPlan* out) {
+// Slab geometry for an X-wide grid and R output rows per unit: T 128-entry
+// tiles cover the R (X+1) entries, K = 16 / T blocks of 32 TMEM columns per
+// tile (512 columns), four slabs (128-byte aligned), the weights and the tail
+// within the shared-memory limit. Returns false if it does not fit.
+bool make_conv_plan(int X, int R, ConvPlan* out) {
   const int XS = X + 1;
-  double best = -1.0;
-  for (int R = 1; R <= Y; ++R) {
-    ConvPlan P{};
-    P.R = R;
-    P.T = (R * XS + 127) / 128;
-    P.chunk_bytes = (R + 2) * XS * 16;
-    P.plane_bytes = 4 * P.chunk_bytes;
-    if (P.T > 8 || P.plane_bytes % 128) continue;
-    const int over = XS + 128 * P.T + XS + 1 - (R + 2) * XS;  // entries read past a slab (discarded rows)
-    P.tail_bytes = over > 0 ? (over * 16 + 127) / 128 * 128 : 0;
-    P.slab_off = NTAP * W_TAP_BYTES + 128;
-    P.bar_off = P.slab_off + SLABS * P.plane_bytes + P.tail_bytes;
-    P.smem = 1024 + P.bar_off + 256;
-    int cols = 32;
-    while (cols < 2 * P.T * 32) cols *= 2;
-    P.tmem_cols = cols;
-    if (P.smem > 232448) continue;
-    const double eff = (double)R * X / (P.T * 128.0);
-    if (eff >= best) {
-      best = eff;
-      *out = P;
-    }
-  }
-  return best > 0.0;
+  ConvPlan P{};
+  P.R = R;
+  P.T = (R * XS + 127) / 128;
+  if (P.T > 8) return false;
+  P.K = KMAX / P.T;
+  P.chunk_bytes = (R + 2) * XS * 16;
+  P.plane_bytes = 4 * P.chunk_bytes;
+  P.slab_stride = (P.plane_bytes + 127) / 128 * 128;
+  const int over = XS + 128 * P.T + XS + 1 - (R + 2) * XS;  // entries read past a slab (discarded rows)
+  P.tail_bytes = over > 0 ? (over * 16 + 127) / 128 * 128 : 0;
+  P.slab_off = NTAP * W_TAP_BYTES + 128;
+  P.bar_off = P.slab_off + SLABS * P.slab_stride + P.tail_bytes;
+  // at least half the SM's shared memory: one CTA per SM, the only one that
+  // can hold the 512 TMEM columns
+  P.smem = std::max(1024 + P.bar_off + 512, 118784);
+  int cols = 32;
+  while (cols < P.T * P.K * 32) cols *= 2;
+  P.tmem_cols = cols;
+  if (P.smem > 232448) return false;
+  *out = P;
+  return true;
 }
 
-// Work units for S samples: (sample, row block, run of L planes); L picked
-// so that ceil(units / SMs) (L + 1/2) is smallest. Returns the grid size.
+// The largest dynamic shared memory any row count of an X-wide, Y-high grid
+// asks for (0 if none fits).
+int conv_smem_max(int X, int Y) {
+  int m = 0;
+  for (int R = 1; R <= Y; ++R) {
+    ConvPlan P;
+    if (make_conv_plan(X, R, &P) && P.smem > m) m = P.smem;
+  }
+  return m;
+}
+
+// Work units for S samples: (sample, row block of R rows, run of L <= K
+// planes). A unit issues T tiles x (L + 2) input planes of MMAs, so R and L
+// are picked to make ceil(units / SMs) T (L + 2) smallest (then the fewest
+// units). Returns the grid size, 0 if no plan fits.
 int conv_units(const bssn_corrector* c, const Geom& G, ConvPlan* P) {
-  *P = c->conv;
-  P->nyb = (G.Y + P->R - 1) / P->R;
   double best = 1e300;
-  for (int L = 1; L <= G.Z; ++L) {
-    const long long units = (long long)G.S * P->nyb * ((G.Z + L - 1) / L);
-    const double cost = (double)((units + c->sms - 1) / c->sms) * (L + 0.5);
-    if (cost < best) {
-      best = cost;
-      P->L = L;
+  long long best_units = 0;
+  for (int R = 1; R <= G.Y; ++R) {
+    ConvPlan Q;
+    if (!make_conv_plan(G.X, R, &Q)) continue;
+    Q.nyb = (G.Y + R - 1) / R;
+    for (int L = 1; L <= Q.K && L <= G.Z; ++L) {
+      const long long units = (long long)G.S * Q.nyb * ((G.Z + L - 1) / L);
+      const double cost = (double)((units + c->sms - 1) / c->sms) * Q.T * (L + 2);
+      if (cost < best || (cost == best && units < best_units)) {
+        best = cost;
+        best_units = units;
+        *P = Q;
+        P->L = L;
+      }
     }
   }
+  if (best == 1e300) return 0;
   P->nzs = (G.Z + P->L - 1) / P->L;
   const long long units = (long long)G.S * P->nyb * P->nzs;
   return (int)(units < c->sms ? units : c->sms);
@@ -1047,20 +1114,36 @@ int conv_units(const bssn_corrector* c, const Geom& G, ConvPlan* P) {
 // one layer forward on act[l] (sample count in G) -> z[l] and act[l+1]
 cudaError_t layer_forward(bssn_corrector* c, const Geom& G, int l, float* zout, __nv_bfloat16* act_out, int gelu,
                           cudaStream_t s) {
-  CUtensorMap ta, tw;
-  if (!map_slab(&ta, c->act[l], G, c->conv.R) || !map_w(&tw, c->wf + (size_t)l * NTAP * CH * CH))
-    return cudaErrorInvalidValue;
   ConvPlan P;
   const int grid = conv_units(c, G, &P);
+  CUtensorMap ta, tw;
+  if (grid < 1 || !map_slab(&ta, c->act[l], G, P.R) || !map_w(&tw, c->wf + (size_t)l * NTAP * CH * CH))
+    return cudaErrorInvalidValue;
   const float* bias = c->params + (size_t)l * LAYER_PARAMS + NTAP * CH * CH;
-  k_conv_tc<0><<<grid, CONV_THREADS, P.smem, s>>>(ta, tw, G, P, bias, zout, act_out, nullptr, gelu, c->err);
-  return cudaGetLastError();
+  // programmatic dependent launch: the CTAs' set-up (barriers, TMEM, the
+  // weights) overlaps the previous kernel's tail; the producer waits for the
+  // previous kernel before it loads an activation slab
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(CONV_THREADS);
+  cfg.dynamicSmemBytes = (size_t)P.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_conv_tc<0>, ta, tw, G, P, bias, zout, act_out, (const float*)nullptr, gelu,
+                            c->err);
 }
 
-cudaError_t network_forward(bssn_corrector* c, const Geom& G, cudaStream_t s) {
+// the whole network; the last layer writes its output to `last` if given
+// (the caller's buffer, same [S][n^3][32] layout), else to z[NL-1]
+cudaError_t network_forward(bssn_corrector* c, const Geom& G, cudaStream_t s, float* last = nullptr) {
   cudaError_t e = cudaSuccess;
   for (int l = 0; l < NL && e == cudaSuccess; ++l)
-    e = layer_forward(c, G, l, c->z[l], l < NL - 1 ? c->act[l + 1] : nullptr, l < NL - 1 ? 1 : 0, s);
+    e = layer_forward(c, G, l, l == NL - 1 && last ? last : c->z[l], l < NL - 1 ? c->act[l + 1] : nullptr,
+                      l < NL - 1 ? 1 : 0, s);
   return e;
 }
 
@@ -1090,10 +1173,10 @@ cudaError_t network_backward(bssn_corrector* c, const Geom& G, cudaStream_t s) {
     if (!map_cf(&tg, c->cfg, G, c->xp)) return cudaErrorInvalidValue;
     if (e == cudaSuccess) {
       if (G.X == 64)
-        k_wgrad_tc<64><<<dim3(7, nb), CONV_THREADS, WG<64>::SMEM, s>>>(tm[0], tm[1], tm[2], tg, G, rpc, c->partial,
+        k_wgrad_tc<64><<<dim3(7, nb), WG_THREADS, WG<64>::SMEM, s>>>(tm[0], tm[1], tm[2], tg, G, rpc, c->partial,
                                                                        c->err);
       else
-        k_wgrad_tc<32><<<dim3(7, nb), CONV_THREADS, WG<32>::SMEM, s>>>(tm[0], tm[1], tm[2], tg, G, rpc, c->partial,
+        k_wgrad_tc<32><<<dim3(7, nb), WG_THREADS, WG<32>::SMEM, s>>>(tm[0], tm[1], tm[2], tg, G, rpc, c->partial,
                                                                        c->err);
       e = cudaGetLastError();
     }
@@ -1107,11 +1190,11 @@ cudaError_t network_backward(bssn_corrector* c, const Geom& G, cudaStream_t s) {
       e = cudaGetLastError();
     }
     if (e == cudaSuccess && l > 0) {
-      CUtensorMap ta, tw;
-      if (!map_slab(&ta, c->g[cur], G, c->conv.R) || !map_w(&tw, c->wb + (size_t)l * NTAP * CH * CH))
-        return cudaErrorInvalidValue;
       ConvPlan P;
       const int grid = conv_units(c, G, &P);
+      CUtensorMap ta, tw;
+      if (grid < 1 || !map_slab(&ta, c->g[cur], G, P.R) || !map_w(&tw, c->wb + (size_t)l * NTAP * CH * CH))
+        return cudaErrorInvalidValue;
       k_conv_tc<1><<<grid, CONV_THREADS, P.smem, s>>>(ta, tw, G, P, nullptr, nullptr, c->g[1 - cur], c->z[l - 1], 0,
                                                       c->err);
       e = cudaGetLastError();
@@ -1217,16 +1300,17 @@ bssn_status_t bssn_corrector_create(bssn_corrector_t** out, int n, int max_batch
   c->coef = (double*)p;
   if (e == cudaSuccess) e = calloc_dev(c, sizeof(unsigned int), &p);
   c->err = (unsigned int*)p;
-  if (e == cudaSuccess && !make_conv_plan(n, n, &c->conv)) e = cudaErrorInvalidValue;
+  c->conv_smem = conv_smem_max(n, n);
+  if (e == cudaSuccess && c->conv_smem == 0) e = cudaErrorInvalidValue;
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_conv_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->conv.smem);
+    e = cudaFuncSetAttribute(k_conv_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->conv_smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->conv.smem);
+    e = cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->conv_smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_wgrad_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, WG<64>::SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_wgrad_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, WG<32>::SMEM);
-  // the tensor-core kernels run two CTAs per SM: ask for the full carveout
+  // ask for the full shared-memory carveout for the tensor-core kernels
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_tc<0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess)
@@ -1349,9 +1433,7 @@ bssn_status_t bssn_corrector_forward_raw(bssn_corrector_t* c, int S, const void*
     k_pad_copy<<<1024, 256, 0, s>>>(G, (const __nv_bfloat16*)x_bf16, c->act[0]);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = network_forward(c, G, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(out, c->z[NL - 1], (size_t)S * c->n * c->n * c->n * CH * 4, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = network_forward(c, G, s, out);
   return status_of(c, e, s);
 }
 

@@ -67,14 +67,18 @@ def net32():
     B.corrector_destroy(c)
 
 
-def test_every_layer_matches_oracle_conv(net32):
+@pytest.mark.parametrize("S", [1, 2])
+def test_every_layer_matches_oracle_conv(net32, S):
     """Pre-activation of each layer against the oracle convolution of that
-    layer's BF16 input (the previous layer's GELU output rounded to BF16)."""
+    layer's BF16 input (the previous layer's GELU output rounded to BF16).
+    At 32^3 the work units hold 3 (S = 1) or 6 (S = 2) output planes of 3
+    rows, so both leave a short last run of planes and a short last block of
+    rows."""
     torch = need_gpu()
-    n, S = 32, 1
+    n = 32
     p = seeded_params(11)
     B.corrector_params(net32, p)
-    rng = np.random.default_rng(12)
+    rng = np.random.default_rng(12 + S)
     x = np.zeros((S, n, n, n, CH))
     x[..., :24] = bf16_round(rng.standard_normal((S, n, n, n, 24)))
     out = torch.empty((S * n ** 3, CH), dtype=torch.float32, device="cuda")
@@ -82,7 +86,10 @@ def test_every_layer_matches_oracle_conv(net32):
     act = x
     for l in range(5):
         z = torch.empty_like(out)
-        B.corrector_layer_output(net32, l, S, z)
+        if l < 4:
+            B.corrector_layer_output(net32, l, S, z)
+        else:
+            z = out  # forward_raw writes the last layer straight into out
         zg = z.cpu().numpy().reshape(S, n, n, n, CH)
         W = p[l * LAYER:l * LAYER + NTAP * CH * CH].reshape(NTAP, CH, CH).astype(np.float64)
         b = p[l * LAYER + NTAP * CH * CH:(l + 1) * LAYER].astype(np.float64)
@@ -90,7 +97,33 @@ def test_every_layer_matches_oracle_conv(net32):
         err = rel(zg, want)
         assert err < 2e-3, (l, err)
         act = bf16_round(oracle.gelu(zg))  # the next layer's input as the GPU forms it
-    np.testing.assert_array_equal(out.cpu().numpy(), z.cpu().numpy())
+
+
+def test_first_layer_at_64_cubed():
+    """The 64^3 grid of the learned form: units of 3 rows (two 128-entry
+    tiles) and 5 planes, N = 96 stacked MMAs, against the oracle."""
+    torch = need_gpu()
+    n = 64
+    c = B.corrector_create(n, 1, seed=3)
+    try:
+        p = seeded_params(31)
+        B.corrector_params(c, p)
+        rng = np.random.default_rng(32)
+        x = np.zeros((1, n, n, n, CH))
+        x[..., :24] = bf16_round(rng.standard_normal((1, n, n, n, 24)))
+        out = torch.empty((n ** 3, CH), dtype=torch.float32, device="cuda")
+        B.corrector_forward_raw(c, 1, to_bf16_tensor(x), out)
+        z = torch.empty_like(out)
+        B.corrector_layer_output(c, 0, 1, z)
+        zg = z.cpu().numpy().reshape(1, n, n, n, CH)
+        W = p[:NTAP * CH * CH].reshape(NTAP, CH, CH).astype(np.float64)
+        b = p[NTAP * CH * CH:LAYER].astype(np.float64)
+        want = oracle.conv3d_fwd(x, W, b)
+        assert rel(zg, want) < 2e-3
+        # every point, not only on average
+        assert np.max(np.abs(zg - want)) < 2e-2 * np.max(np.abs(want))
+    finally:
+        B.corrector_destroy(c)
 
 
 def test_loss_and_gradient_match_oracle(net32):

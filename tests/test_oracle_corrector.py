@@ -46,10 +46,21 @@ def test_conv_backward_is_the_adjoint():
     np.testing.assert_allclose(db, g.sum(axis=(0, 1, 2, 3)), rtol=1e-13)
 
 
-def test_gelu_closed_form():
-    x = np.linspace(-6, 6, 101)
+def test_gelu_tanh_form():
+    """The activation is the tanh form of GELU (Hendrycks and Gimpel 2016).
+    Pinned by what holds for it independently of its formula: it is within
+    5e-4 of the exact x Phi(x) everywhere (the published approximation's
+    maximum deviation is 4.7e-4, near x = -2.7), GELU(x) - GELU(-x) = x (the
+    inner function is odd), it tends to x and to 0 in the two tails, and its
+    derivative matches a central difference."""
+    x = np.linspace(-8, 8, 1601)
     phi = np.array([0.5 * (1 + math.erf(v / math.sqrt(2))) for v in x])
-    np.testing.assert_allclose(oracle.gelu(x), x * phi, rtol=1e-14, atol=1e-300)
+    g = oracle.gelu(x)
+    dev = np.abs(g - x * phi)
+    assert dev.max() < 5e-4 and dev.max() > 4e-4
+    np.testing.assert_allclose(g - oracle.gelu(-x), x, rtol=0, atol=1e-14)
+    big = np.array([12.0, -12.0])
+    np.testing.assert_allclose(oracle.gelu(big), [12.0, 0.0], atol=1e-12)
     h = 1e-6
     fd = (oracle.gelu(x + h) - oracle.gelu(x - h)) / (2 * h)
     np.testing.assert_allclose(oracle.gelu(x, grad=True), fd, rtol=1e-7, atol=1e-9)
