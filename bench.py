@@ -797,16 +797,18 @@ def run_gpu(args):
         physical time, and state the error of each against the restricted
         fine solution."""
         from paper_1307_6488_gb300 import learned as LR
-        nc, per_traj = 64, 10
+        nc, per_traj = 64, 20
         ntraj = max(1, args.learned_pairs // per_traj)
+        # trajectory settings only; each problem's initial data is made when
+        # its trajectory runs and freed after
         rng = np.random.default_rng(0)
-        probs = []
+        specs = []
         for i in range(ntraj):
             if i % 5 == 4:
-                probs.append(LR.Problem("gw", nc, amplitude=float(rng.uniform(0.02, 0.1))))
+                specs.append(("gw", dict(amplitude=float(rng.uniform(0.02, 0.1)))))
             else:
                 m = rng.uniform(0.3, 0.7, 2)
-                probs.append(LR.Problem("bl", nc, masses=tuple(m), separation=float(rng.uniform(2, 4))))
+                specs.append(("bl", dict(masses=tuple(m), separation=float(rng.uniform(2, 4)))))
         corr = B.corrector_create(nc, 4, seed=1)
         try:
             torch.cuda.synchronize()
@@ -814,11 +816,13 @@ def run_gpu(args):
             data = LR.Dataset(corr, nc)
             # normalisation scales from the first (pilot) trajectories, which
             # include a gauge wave; every pair is packed to BF16 as soon as
-            # the scales are known, so only packed pairs stay resident
-            pilot = min(len(probs), 5)
+            # the scales are known, so only packed pairs stay resident. The
+            # fine trajectories run in the FP32-RHS form (FP64 state).
+            pilot = min(len(specs), 5)
             pending = []
-            for i, pr in enumerate(probs):
-                ps = LR.trajectory_pairs(LR.Stepper(pr), per_traj)
+            for i, (kind, kw) in enumerate(specs):
+                pr = LR.Problem(kind, nc, **kw)
+                ps = LR.trajectory_pairs(LR.Stepper(pr, fine_prec=B.FP32_RHS), per_traj)
                 if i >= pilot:
                     data.add(ps, pr.gc)
                     continue
@@ -894,7 +898,7 @@ def run_gpu(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ms_forward = e0.elapsed_time(e1) / reps
-            mma32 = B.probe_mma_rate(32)
+            mma96 = B.probe_mma_rate(96)
         finally:
             B.corrector_destroy(corr)
         torch.cuda.empty_cache()
@@ -909,11 +913,15 @@ def run_gpu(args):
                 "fallbacks_in_timed_steps": int(fb),
                 "network_forward_ms_64cubed": ms_forward,
                 "network_roofline": {"bound": "tensor", "achieved": conv_tflops,
-                                     "peak": mma32, "unit": "TFLOP/s", "frac": conv_tflops / mma32,
+                                     "peak": MEASURED.get("bf16_tflops", 1922.5), "unit": "TFLOP/s",
+                                     "frac": conv_tflops / MEASURED.get("bf16_tflops", 1922.5),
                                      "flops_per_point": net_flops,
-                                     "peak_source": "measured rate of back-to-back M=128 N=32 K=16 BF16 tcgen05 "
-                                                    "MMAs (bssn_probe_mma_rate), the instruction ceiling of the "
-                                                    "N = 32-channel convolutions",
+                                     "peak_source": "measured dense BF16 (cuBLAS burst)",
+                                     "mma_n96_ceiling": mma96,
+                                     "frac_of_mma_n96_ceiling": conv_tflops / mma96,
+                                     "mma_n96_source": "measured rate of back-to-back M=128 N=96 K=16 BF16 tcgen05 "
+                                                       "MMAs issued as the convolutions issue them "
+                                                       "(bssn_probe_mma_rate)",
                                      "frac_of_dense_bf16": conv_tflops / MEASURED.get("bf16_tflops", 1922.5)},
                 "accuracy_8_coarse_steps": acc,
                 "accuracy_note": "err_* = RMS over interior points and variables of (x - restricted fine) / "
@@ -924,9 +932,9 @@ def run_gpu(args):
                              "loss_last20_mean": float(np.mean(losses[-20:])), "gen_s": t_gen, "train_s": t_train,
                              "ms_per_train_step": 1e3 * t_train / max(1, train_steps)},
                 "config": "coarse 64^3 / fine 128^3 on [-8,8]^3 (gauge wave [-0.5,0.5]^3), 4 ghosts, 4th order, "
-                          "1+log + Gamma-driver, KO 0.1, dt_c = 0.25 h_c, FP64 evolution; corrector 5 x conv3d "
-                          "3^3, 32 channels, GELU, BF16 tcgen05 with FP32 accumulation; fallback if H L2 > 2x "
-                          "plain coarse"}
+                          "1+log + Gamma-driver, KO 0.1, dt_c = 0.25 h_c, FP64 evolution (training trajectories: "
+                          "fine steps in the FP32-RHS form); corrector 5 x conv3d 3^3, 32 channels, GELU (tanh "
+                          "form), BF16 tcgen05 with FP32 accumulation; fallback if H L2 > 2x plain coarse"}
 
     if args.corrector_only:
         # the network's kernels alone on seeded packed data (64^3, batch 4):
@@ -970,6 +978,12 @@ def run_gpu(args):
         res = run_cfd()
         if rank == 0:
             print(json.dumps({"cfd_only": True, **res}))
+        return
+
+    if args.learned_only:
+        res = run_learned()
+        if rank == 0:
+            print(json.dumps({"learned_only": True, **res}))
         return
 
     if args.amr_only:
@@ -1187,13 +1201,15 @@ def main():
     ap.add_argument("--no-amr", action="store_true", help="skip the refined-hierarchy (Berger-Oliger) form")
     ap.add_argument("--no-cfd", action="store_true", help="skip the CFD (SOLA Navier-Stokes) benchmark form")
     ap.add_argument("--cfd-only", action="store_true", help="run only the CFD benchmark form and print its numbers")
+    ap.add_argument("--learned-only", action="store_true",
+                    help="run only the learned-corrector form and print its numbers")
     ap.add_argument("--amr-only", action="store_true",
                     help="run only the refined-hierarchy forms (FP64 and FP32-RHS) and print their numbers")
     ap.add_argument("--no-fp32-config", action="store_true",
                     help="skip the FP32-RHS 256^3 throughput and 96^3 100-step accuracy runs")
-    ap.add_argument("--learned-pairs", type=int, default=200,
-                    help="training pairs for the learned form (10 per fine trajectory; the full set is 2000)")
-    ap.add_argument("--learned-epochs", type=int, default=20)
+    ap.add_argument("--learned-pairs", type=int, default=2000,
+                    help="training pairs for the learned form (20 per fine trajectory)")
+    ap.add_argument("--learned-epochs", type=int, default=5)
     ap.add_argument("--corrector-only", action="store_true",
                     help="only the learned corrector's kernels (training steps and forward passes, 64^3): for ncu")
     ap.add_argument("--profile", action="store_true",

@@ -649,11 +649,13 @@ bssn_status_t bssn_probe_wait_timeout(unsigned long long limit_ns, unsigned int*
 bssn_status_t bssn_probe_fp_rates(double* out);
 
 /* Measures the rate of back-to-back dense BF16 tcgen05 MMAs (M = 128, K = 16,
- * FP32 accumulation, one CTA per SM, operands fixed in shared memory) with
- * N = n output columns (32, 64, 128 or 256) and writes it to *tflops (HOST),
- * in TFLOP/s over all SMs. The convolutions issue N = 32 (one column per
- * output channel); their roofline is this rate at n = 32. Synchronizes the
- * device. Not a computation of the paper. */
+ * FP32 accumulation, one CTA per SM, operands in shared memory, issued from
+ * warp-uniform code by one elected lane with the A start moving by 0-2
+ * entries between MMAs as the convolution taps do) with N = n output columns
+ * (32, 64, 96, 128 or 256) and writes it to *tflops (HOST), in TFLOP/s over
+ * all SMs. The forward and input-gradient convolutions issue N = 96 (three
+ * output planes of 32 channels); their instruction ceiling is this rate at
+ * n = 96. Synchronizes the device. Not a computation of the paper. */
 bssn_status_t bssn_probe_mma_rate(int n, double* tflops);
 
 #ifdef __cplusplus

@@ -525,12 +525,13 @@ __global__ void __launch_bounds__(WG_THREADS, 2)
         (void)tc::mbar_wait(&full[k % WG_STAGES], (k / WG_STAGES) & 1, 100000000ull);
     }
   } else if (warp == 5) {
-    // ---- MMA issuer: never waits for an MMA, only for data
-    if (lane == 0 && nrows > 0) {
+    // ---- MMA issuer: never waits for an MMA, only for data; the whole warp
+    // runs the loop on warp-uniform descriptors, one elected lane issues
+    if (nrows > 0) {
       bool ok = true;
       for (int k = 0; k < nrows; ++k) {
         const int slot = k % WG_STAGES;
-        if (!tc::mbar_wait_or_abort(&full[slot], (k / WG_STAGES) & 1, &abort_flag)) {
+        if (!tc::warp_wait_or_abort(&full[slot], (k / WG_STAGES) & 1, &abort_flag)) {
           ok = false;
           break;
         }
@@ -539,15 +540,15 @@ __global__ void __launch_bounds__(WG_THREADS, 2)
         const uint64_t bd = tc::smem_desc(tc::smem_u32(Bst + slot * W::B_BYTES), 16, W::SBO, W::SWZ);
 #pragma unroll
         for (int j = 0; j < W::KSTEPS; ++j)
-          tc::mma_bf16(taddr, ad + 2 * j, bd + 2 * j, IDESC, (k > 0 || j > 0) ? 1u : 0u);
-        tc::mma_commit(&empty[slot]);
+          tc::mma_bf16_elect(taddr, ad + 2 * j, bd + 2 * j, IDESC, (k > 0 || j > 0) ? 1u : 0u);
+        tc::mma_commit_elect(&empty[slot]);
       }
-      if (!ok) {
+      if (!ok && lane == 0) {
         if (!abort_flag) atomicOr(err, 4u);
         abort_flag = 1;
       }
       // completes once every MMA issued above has finished (also on abort)
-      tc::mma_commit(done);
+      tc::mma_commit_elect(done);
     }
   }
   // ---- epilogue (warps 0-3; the other two warps only meet the barriers)
@@ -845,9 +846,11 @@ __global__ void k_apply(Geom G, Layout L, const float* __restrict__ out, const d
 }
 
 // ---------------------------------------------------------------- MMA rate probe
-// Back-to-back kind::f16 MMAs (M = 128, K = 16, N = NC) on fixed no-swizzle
-// operands in shared memory, one CTA per SM: the instruction-rate ceiling of
-// the shapes the convolutions issue (N = 32 output channels).
+// Back-to-back kind::f16 MMAs (M = 128, K = 16, N = NC) on no-swizzle
+// operands in shared memory, one CTA per SM, issued the way the convolutions
+// issue them: warp 0 runs the loop on warp-uniform descriptors whose A start
+// moves by 0-2 entries from one MMA to the next (the taps' shifts) and one
+// elected lane issues. The instruction-rate ceiling of those shapes.
 constexpr int PROBE_A = 128 * 32, PROBE_B = 256 * 32, PROBE_SMEM = 1024 + PROBE_A + PROBE_B + 256;
 
 template <int NC>
@@ -868,17 +871,22 @@ __global__ void __launch_bounds__(128, 1) k_mma_rate(int iters, unsigned long lo
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t taddr = *slot;
-  if (tid == 0) {
+  if (warp == 0) {
     // A 128 x 16 and B NC x 16, K-major, core matrices 8 rows x 16 bytes
     const uint64_t ad = tc::smem_desc(tc::smem_u32(base), 2048, 128, tc::SWZ_NONE);
     const uint64_t bd = tc::smem_desc(tc::smem_u32(base + PROBE_A), NC * 16, 128, tc::SWZ_NONE);
     constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, NC);
     const uint64_t t0 = tc::global_ns();
-    for (int i = 0; i < iters; ++i) tc::mma_bf16(taddr, ad, bd, IDESC, i ? 1u : 0u);
-    tc::mma_commit(bar);
-    const bool ok = tc::mbar_wait(bar, 0);
-    ns[blockIdx.x] = tc::global_ns() - t0;
-    if (!ok) atomicOr(err, 1u);
+    for (int i = 0; i < iters; i += 6) {
+#pragma unroll
+      for (int t = 0; t < 6; ++t) tc::mma_bf16_elect(taddr, ad + (uint64_t)(t % 3), bd, IDESC, (i | t) ? 1u : 0u);
+    }
+    tc::mma_commit_elect(bar);
+    const bool ok = tc::warp_wait(bar, 0);
+    if (tid == 0) {
+      ns[blockIdx.x] = tc::global_ns() - t0;
+      if (!ok) atomicOr(err, 1u);
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -1566,20 +1574,24 @@ bssn_status_t bssn_probe_wait_timeout(unsigned long long limit_ns, unsigned int*
 // Measured dense BF16 rate (TFLOP/s, all SMs) of back-to-back M=128 K=16
 // tcgen05 MMAs with N = n (32, 64, 128 or 256) columns.
 bssn_status_t bssn_probe_mma_rate(int n, double* tflops) {
-  if (!tflops || (n != 32 && n != 64 && n != 128 && n != 256)) return BSSN_ERR_INVALID_ARG;
+  if (!tflops || (n != 32 && n != 64 && n != 96 && n != 128 && n != 256)) return BSSN_ERR_INVALID_ARG;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return BSSN_ERR_CUDA;
   void (*kern)(int, unsigned long long*, unsigned int*) =
-      n == 32 ? k_mma_rate<32> : n == 64 ? k_mma_rate<64> : n == 128 ? k_mma_rate<128> : k_mma_rate<256>;
+      n == 32    ? k_mma_rate<32>
+      : n == 64  ? k_mma_rate<64>
+      : n == 96  ? k_mma_rate<96>
+      : n == 128 ? k_mma_rate<128>
+                 : k_mma_rate<256>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, PROBE_SMEM);
   unsigned long long* ns = nullptr;
   unsigned int* err = nullptr;
   if (e == cudaSuccess) e = cudaMalloc(&ns, sizeof(unsigned long long) * sms);
   if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(unsigned int));
-  const int iters = 4096;
+  const int iters = 4098;  // a multiple of 6
   std::vector<unsigned long long> h(sms);
   unsigned int herr = 0;
   for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first launch warms up

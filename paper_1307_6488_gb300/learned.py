@@ -102,11 +102,11 @@ class Stepper:
         return float(l2[0]) if st == B.OK else float("inf")
 
 
-def trajectory_pairs(stepper, nsteps, measure="roughness"):
+def trajectory_pairs(stepper, nsteps, measure=None):
     """Coarse pairs (input, target, size) along one fine trajectory of
-    nsteps + 2 fine steps: input and target are device states, size the
+    nsteps + 2 fine steps: input and target are device states; size is the
     per-variable vector (numpy, 24) that Stepper.<measure>(input, R(f_k))
-    returns for the coarse step's output."""
+    returns for the coarse step's output, or None without a measure."""
     p = stepper.p
     f = stepper.src_f.clone()
     restricted = []
@@ -118,7 +118,8 @@ def trajectory_pairs(stepper, nsteps, measure="roughness"):
         if k >= 2:
             x = restricted[k - 2].clone()
             stepper.coarse_step(x)
-            pairs.append((x, restricted[k], getattr(stepper, measure)(x, restricted[k - 2])))
+            size = getattr(stepper, measure)(x, restricted[k - 2]) if measure else None
+            pairs.append((x, restricted[k], size))
             restricted[k - 2] = None
         stepper.fine_step(f)
     return pairs
