@@ -320,6 +320,15 @@ bssn_status_t bssn_restrict(const bssn_grid_t* fine, const double* fine_state, c
 bssn_status_t bssn_prolong(const bssn_grid_t* coarse, const double* coarse_state, const bssn_grid_t* fine,
                            double* fine_state, void* stream);
 
+/* out = y + (a - b) at every interior point of all 24 variables of one grid
+ * (DEVICE states in the grid's padded layout, 16-byte aligned; ghosts are
+ * not touched). out may be any of y, a, b. The learned evolution's fine
+ * fallback uses it to add the restricted fine increment R(F F P y) - R(P y)
+ * to the coarse state y, so that the round trip R P (not the identity, see
+ * above) does not enter the result. Asynchronous on `stream`. */
+bssn_status_t bssn_add_difference(const bssn_grid_t* grid, const double* y, const double* a, const double* b,
+                                  double* out, void* stream);
+
 /* ---------------------------------------------------------------- refined hierarchy (Berger-Oliger)
  * Time stepping of a hierarchy of patches refined by 2 per level in space
  * and time, the block-structured adaptive refinement the paper runs through

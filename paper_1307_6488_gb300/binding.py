@@ -399,7 +399,8 @@ def _transfer_lib():
     if not getattr(L, "_transfer_typed", False):
         L.bssn_restrict.argtypes = [ctypes.POINTER(Grid), _p, ctypes.POINTER(Grid), _p, ctypes.c_int, _p]
         L.bssn_prolong.argtypes = [ctypes.POINTER(Grid), _p, ctypes.POINTER(Grid), _p, _p]
-        for n in ("bssn_restrict", "bssn_prolong"):
+        L.bssn_add_difference.argtypes = [ctypes.POINTER(Grid), _p, _p, _p, _p, _p]
+        for n in ("bssn_restrict", "bssn_prolong", "bssn_add_difference"):
             getattr(L, n).restype = ctypes.c_int
         L._transfer_typed = True
     return L
@@ -411,6 +412,13 @@ def restrict(fine_grid, fine_state, coarse_grid, coarse_state, order=4, stream=N
     centre (fine ghosts >= 1, filled)."""
     _check(_transfer_lib().bssn_restrict(ctypes.byref(fine_grid), _ptr(fine_state), ctypes.byref(coarse_grid),
                                          _ptr(coarse_state), order, _stream(stream)), "restrict")
+
+
+def add_difference(grid, y, a, b, out, stream=None):
+    """bssn_add_difference: out = y + (a - b) at interior points."""
+    L = _transfer_lib()
+    _check(L.bssn_add_difference(ctypes.byref(grid), _ptr(y), _ptr(a), _ptr(b), _ptr(out), _stream(stream)),
+           "add_difference")
 
 
 def prolong(coarse_grid, coarse_state, fine_grid, fine_state, stream=None):

@@ -2,7 +2,8 @@
 // (cell-centred, the "ratio 2" levels of block-structured refinement the
 // paper plans for, Sec. 4). Used by the learned corrector: restriction turns
 // fine results into training targets, prolongation starts the fine-grid
-// fallback step.
+// fallback step, and the fallback adds the restricted fine increment to the
+// coarse state (bssn_add_difference).
 //
 //   restriction:   order 2: coarse(i,j,k) = mean of the 8 fine cells
 //                  (2i+a, 2j+b, 2k+c); order 4: tricubic Lagrange
@@ -16,6 +17,7 @@
 //                  (-7, 105, 35, -5)/128 on coarse i-1..i+2 (offset +1/4).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "../../include/bssn.h"
@@ -117,6 +119,24 @@ bool pair_ok(const bssn_grid_t* C, const bssn_grid_t* F) {
   return grid_basic_ok(C) && grid_basic_ok(F) && F->nx == 2 * C->nx && F->ny == 2 * C->ny && F->nz == 2 * C->nz;
 }
 
+// out = y + (a - b) at the interior points of all 24 variables. out may be
+// any of the inputs: every element is read and written by one thread.
+__global__ void __launch_bounds__(256) k_add_difference(Layout L, const double* y, const double* a, const double* b,
+                                                        double* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L.npts;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % L.nx);
+    const long long r = i / L.nx;
+    const int yy = (int)(r % L.ny), z = (int)(r / L.ny);
+    const long long p = L.off0 + x + yy * L.sy + z * L.sz;
+#pragma unroll 4
+    for (int v = 0; v < NV; ++v) {
+      const long long q = v * L.vs + p;
+      out[q] = y[q] + (a[q] - b[q]);
+    }
+  }
+}
+
 bool a16(const void* p) { return p && ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace
@@ -144,6 +164,15 @@ bssn_status_t bssn_prolong(const bssn_grid_t* coarse, const double* coarse_state
     return BSSN_ERR_INVALID_ARG;
   const Layout F = make_layout(*fine), C = make_layout(*coarse);
   k_prolong<<<(unsigned int)((F.npts + 255) / 256), 256, 0, (cudaStream_t)stream>>>(C, F, coarse_state, fine_state);
+  return cudaGetLastError() == cudaSuccess ? BSSN_OK : BSSN_ERR_CUDA;
+}
+
+bssn_status_t bssn_add_difference(const bssn_grid_t* grid, const double* y, const double* a, const double* b,
+                                  double* out, void* stream) {
+  if (!grid_basic_ok(grid) || !a16(y) || !a16(a) || !a16(b) || !a16(out)) return BSSN_ERR_INVALID_ARG;
+  const Layout L = make_layout(*grid);
+  const long long blocks = std::min<long long>((L.npts + 255) / 256, 4096);
+  k_add_difference<<<(unsigned int)blocks, 256, 0, (cudaStream_t)stream>>>(L, y, a, b, out);
   return cudaGetLastError() == cudaSuccess ? BSSN_OK : BSSN_ERR_CUDA;
 }
 

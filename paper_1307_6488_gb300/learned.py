@@ -9,9 +9,9 @@ trajectories f_0, f_1, ... of the plain method with dt_f = dt_c / 2:
     target = R(f_{k+2})
 and the network learns target - input. At run time a step is
     y_plain = coarse_step(y);  y_learned = y_plain + correction(y_plain)
-and it falls back to the fine method (prolong y, two fine steps, restrict)
-when the Hamiltonian-constraint L2 of y_learned exceeds `fallback_factor`
-times that of y_plain.
+and it falls back to the fine method (prolong y, two fine steps, restrict,
+applied as an increment to y: fallback_step) when the Hamiltonian-constraint
+L2 of y_learned exceeds `fallback_factor` times that of y_plain.
 """
 import numpy as np
 import torch
@@ -205,6 +205,25 @@ def train(corrector, data, epochs, batch, lr, seed=0, lr_final=None, log=None):
     return losses
 
 
+def fallback_step(stepper, before, out):
+    """The plain fine method over one coarse step, as an increment: out =
+    y + R(F F P y) - R(P y) for y = before (P prolongation, F a fine step,
+    R restriction). Restricting the prolonged state does not give y back
+    exactly (a fourth-order difference of the state itself, large against
+    one step's change), so only the fine method's change is taken from the
+    fine grid."""
+    p = stepper.p
+    fine = B.alloc_state(p.gf)
+    stepper.prolong(before, fine)
+    base = B.alloc_state(p.gc)
+    stepper.restrict(fine, base)
+    stepper.fine_step(fine)
+    stepper.fine_step(fine)
+    stepper.restrict(fine, out)
+    B.add_difference(p.gc, before, out, base, out)
+    B.fill_ghosts(p.gc, p.bc, stepper.src_c if p.bc == 1 else None, out)
+
+
 def learned_step(stepper, corrector, state, fallback_factor=2.0, scratch=None, step_ref=None, measure="roughness"):
     """One learned coarse step in place. Returns (used_fallback, H_learned,
     H_plain). With step_ref, the correction is scaled by this step's own
@@ -219,11 +238,7 @@ def learned_step(stepper, corrector, state, fallback_factor=2.0, scratch=None, s
     B.fill_ghosts(p.gc, p.bc, stepper.src_c if p.bc == 1 else None, state)
     h_learned = stepper.ham_l2(state)
     if not (h_learned <= fallback_factor * h_plain):
-        fine = B.alloc_state(p.gf)
-        stepper.prolong(before, fine)
-        stepper.fine_step(fine)
-        stepper.fine_step(fine)
-        stepper.restrict(fine, state)
+        fallback_step(stepper, before, state)
         return True, h_learned, h_plain
     return False, h_learned, h_plain
 

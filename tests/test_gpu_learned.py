@@ -137,14 +137,75 @@ def test_fallback_is_the_fine_method(setup):
     # factor 0: the learned step is never accepted
     used, h_learned, h_plain = LR.learned_step(st, c, y, fallback_factor=0.0)
     assert used and h_plain > 0
+    # y + R(F F P y) - R(P y), formed here on the host from the same kernels
     fine = B.alloc_state(st.p.gf)
     st.prolong(before, fine)
+    base = B.alloc_state(st.p.gc)
+    st.restrict(fine, base)
     st.fine_step(fine)
     st.fine_step(fine)
     ref = B.alloc_state(st.p.gc)
     st.restrict(fine, ref)
     torch.cuda.synchronize()
-    np.testing.assert_array_equal(B.download(y, st.p.gc), B.download(ref, st.p.gc))
+    g = st.p.g
+    I = (slice(None),) + (slice(g, -g),) * 3
+    y0, r0, r2 = (B.download(t, st.p.gc) for t in (before, base, ref))
+    want = y0[I] + (r2[I] - r0[I])
+    np.testing.assert_array_equal(B.download(y, st.p.gc)[I], want)
+
+
+def test_add_difference_is_elementwise(setup):
+    torch, grid, u, tgt, off, isc, osc, c = setup
+    rng = np.random.default_rng(9)
+    w = rng.standard_normal(u.shape)
+    y, a, b = B.upload(u, grid), B.upload(tgt, grid), B.upload(w, grid)
+    out = B.upload(np.full(u.shape, 7.0), grid)
+    B.add_difference(grid, y, a, b, out)
+    got = B.download(out, grid)
+    I = (slice(None),) + (slice(G, -G),) * 3
+    np.testing.assert_array_equal(got[I], u[I] + (tgt[I] - w[I]))
+    ghost = np.ones(u.shape, bool)
+    ghost[I] = False
+    assert np.all(got[ghost] == 7.0)
+    # in place on an input
+    B.add_difference(grid, y, a, b, y)
+    np.testing.assert_array_equal(B.download(y, grid)[I], u[I] + (tgt[I] - w[I]))
+
+
+def test_fallback_is_closer_to_the_fine_method_than_a_plain_step():
+    """On the smooth gauge wave the fallback step must land closer to the
+    restricted fine solution than the plain coarse step does (the plain
+    fine method is the judge of the error), and closer than restricting the
+    fine steps of the prolonged state outright. It cannot reach the fine
+    method itself: the fine steps start from an interpolated state whose
+    interpolation error their second derivatives amplify."""
+    need_gpu()
+    from paper_1307_6488_gb300 import learned as LR
+    st = LR.Stepper(LR.Problem("gw", N, amplitude=0.07))
+    fine = st.src_f.clone()
+    start = B.alloc_state(st.p.gc)
+    st.restrict(fine, start)
+    plain = start.clone()
+    st.coarse_step(plain)
+    fb = B.alloc_state(st.p.gc)
+    LR.fallback_step(st, start, fb)
+    st.fine_step(fine)
+    st.fine_step(fine)
+    ref = B.alloc_state(st.p.gc)
+    st.restrict(fine, ref)
+    g = st.p.g
+    I = (slice(None),) + (slice(g, -g),) * 3
+    r = B.download(ref, st.p.gc)[I]
+    e_plain = np.abs(B.download(plain, st.p.gc)[I] - r).max()
+    e_fb = np.abs(B.download(fb, st.p.gc)[I] - r).max()
+    direct = B.alloc_state(st.p.gf)
+    st.prolong(start, direct)
+    st.fine_step(direct)
+    st.fine_step(direct)
+    old = B.alloc_state(st.p.gc)
+    st.restrict(direct, old)
+    e_old = np.abs(B.download(old, st.p.gc)[I] - r).max()
+    assert e_fb < 0.8 * e_plain and e_fb < e_old, (e_fb, e_plain, e_old)
 
 
 def test_fallback_triggers_on_a_harmful_correction(setup):
