@@ -238,13 +238,19 @@ __global__ void __launch_bounds__(T32N, T32_MIN_BLOCKS)
   const long long p = L.off0 + ic + jc * L.sy + kc * L.sz;
   const long long q = idx32(L32, ic, jc, kc);
 
+  // this point's centre values, loaded before the variable loop so that
+  // their latency hides behind it (the loop needs fewer registers than the
+  // algebra, where they are used)
+  float uc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) uc[v] = __ldg(S.ys32 + v * L32.vs + q);
   // per-point weights from the centre values: gt^ij for the contractions,
   // beta for the advection
   float hgu[6], gu2[6], qw[3][R + 1], bh[3];
   {
     float g6[6];
 #pragma unroll
-    for (int w = 0; w < 6; ++w) g6[w] = __ldg(S.ys32 + (V_GT11 + w) * L32.vs + q);
+    for (int w = 0; w < 6; ++w) g6[w] = uc[V_GT11 + w];
     float gu[6];
     inverse_metric<float>(g6, gu);
 #pragma unroll
@@ -255,7 +261,7 @@ __global__ void __launch_bounds__(T32N, T32_MIN_BLOCKS)
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const float be = __ldg(S.ys32 + (V_BETA1 + d) * L32.vs + q);
+      const float be = uc[V_BETA1 + d];
       bh[d] = be * C.ih[d];
       const float ab = fabsf(be) * C.ih[d];
 #pragma unroll
@@ -403,11 +409,10 @@ __global__ void __launch_bounds__(T32N, T32_MIN_BLOCKS)
   }
   if (ok) {
 
-  // the per-point set: centre values from the single-precision copy (in L2:
-  // the copies just read them), derivatives from the record
+  // the per-point set: centre values, derivatives from the record
   PointLean<float> Q;
 #pragma unroll
-  for (int v = 0; v < NV; ++v) Q.u[v] = __ldg(S.ys32 + v * L32.vs + q);
+  for (int v = 0; v < NV; ++v) Q.u[v] = uc[v];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     Q.dW[d] = my[(rec::D1 + 3 * d1_slot(V_W) + d) * T32N];
