@@ -72,7 +72,7 @@ CFD_TRAFFIC = {"src_sha": "1559830c488ce0a5", "bytes_per_launch": 286361600 + 22
 # the sources that make up the fused FP64 stage kernel k_stage<8,0,double>
 STAGE_SOURCES = ("bssn_common.cuh", "bssn_point.cuh", "bssn_kernels.cuh", "bssn_order.cu", "bssn_bounds.cuh")
 # and the tiled FP32-RHS stage kernel k_stage32t<8,0>
-STAGE32_SOURCES = ("bssn_common.cuh", "bssn_point.cuh", "bssn_stage32.cuh", "bssn_stage32.cu", "bssn_cvt.cuh",
+STAGE32_SOURCES = ("bssn_common.cuh", "bssn_point.cuh", "bssn_stage32.cuh", "bssn_stage32_types.h", "bssn_stage32.cu", "bssn_cvt.cuh",
                    "bssn_tc.cuh", "bssn_bounds.cuh")
 
 
@@ -438,7 +438,8 @@ def run_gpu(args):
     def run_batched(prec):
         """192 seeded uneven patches (sides 16..96, 4 ratio-2 levels around the
         punctures, 4 ghosts, tricubic Brill-Lindquist fill), 4th order, one
-        graph launch per RK4 step over all patches."""
+        graph launch per RK4 step over all patches. The FP32-RHS form runs the
+        single grids' TMA-tiled stage kernel over the patches."""
         patches = inputs.patch_tree()
         pb = B.make_params(fd_order=4, ko_eps=0.1, lapse=0, shift=0, eta=2.0)
         blocks = []
@@ -453,6 +454,7 @@ def run_gpu(args):
                 v4[inputs.IDX["gt11"] + inputs.SYM[i][i]] = 1.0
             blocks.append((gq, st, st.clone()))
         dtb = 0.25 * min(q["h"] for q in patches)
+        nlev = len({float(q["h"]) for q in patches})
         t_tune = time.perf_counter()
         plan = B.plan_create(blocks, pb, prec, 1)
         t_tune = time.perf_counter() - t_tune
@@ -478,7 +480,12 @@ def run_gpu(args):
                 "patches": len(patches), "interior_points": int(pts), "tiles": int(tiles),
                 "tile_shapes_chosen": np.bincount(shapes, minlength=7).tolist(), "plan_create_s": t_tune,
                 "fd_order": 4, "dt": dtb, "graph_launches_per_step": 1,
-                "kernel_nodes_per_step": 13 if prec == B.FP64 else 17}
+                # FP64: per stage ghost fill, tables, stage (persistent kernels over all
+                # patches); FP32-RHS: ghost fill, single-precision copy, tables, and one
+                # tiled stage launch per spacing; then a final ghost fill
+                "kernel_nodes_per_step": 13 if prec == B.FP64 else 4 * (3 + nlev) + 1,
+                "stage_kernel": "kb_stage<4,double> (persistent, autotuned tiles)" if prec == B.FP64 else
+                                "k_stage32t_batch<4> (TMA-staged 8x4x4 tiles, one launch per spacing)"}
 
     def run_amr(prec):
         """Berger-Oliger hierarchy around the two punctures: 5 levels, 96^3
@@ -980,6 +987,12 @@ def run_gpu(args):
             print(json.dumps({"cfd_only": True, **res}))
         return
 
+    if args.batched_only:
+        res = {"batched_fp64": run_batched(B.FP64), "batched_fp32_rhs": run_batched(B.FP32_RHS)}
+        if rank == 0:
+            print(json.dumps({"batched_only": True, **res}))
+        return
+
     if args.learned_only:
         res = run_learned()
         if rank == 0:
@@ -1201,6 +1214,8 @@ def main():
     ap.add_argument("--no-amr", action="store_true", help="skip the refined-hierarchy (Berger-Oliger) form")
     ap.add_argument("--no-cfd", action="store_true", help="skip the CFD (SOLA Navier-Stokes) benchmark form")
     ap.add_argument("--cfd-only", action="store_true", help="run only the CFD benchmark form and print its numbers")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched-patch forms (FP64 and FP32-RHS) and print their numbers")
     ap.add_argument("--learned-only", action="store_true",
                     help="run only the learned-corrector form and print its numbers")
     ap.add_argument("--amr-only", action="store_true",

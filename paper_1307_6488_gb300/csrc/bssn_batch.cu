@@ -71,6 +71,20 @@ struct bssn_plan {
   std::vector<void*> allocations;
   std::vector<int> shape;  // per patch
   int grid_stage = 0, grid_other = 0;
+  // FP32-RHS form: the tiled kernels of bssn_stage32.cuh over a second table,
+  // ordered by spacing so that each spacing's patches are one range
+  std::vector<Patch32> host32;
+  Patch32* dev32 = nullptr;
+  long long* d_tile32 = nullptr;
+  long long* d_pad32 = nullptr;
+  long long* d_ext32 = nullptr;
+  long long ntiles32 = 0, npad32 = 0, next32 = 0;
+  struct Level {
+    int p0, np;
+    long long tbase, ntiles;
+    Coef32 C;
+  };
+  std::vector<Level> levels;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   double graph_dt = NAN;
@@ -158,12 +172,36 @@ cudaError_t other_all(bssn_plan* pl, int kind, int which, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// One FP32-RHS stage of all patches with the tiled kernels: single-precision
+// copy of the stage input, D_x / D_y tables, then one stage launch per
+// spacing.
+cudaError_t stage32_all(bssn_plan* pl, const RK& rk, int in, int out, cudaStream_t s) {
+  const int g = pl->grid_other;
+  cudaError_t e = launch_to_f32t_batch(pl->dev32, pl->d_pad32, pl->np, pl->npad32, in, g, s);
+  if (e == cudaSuccess)
+    e = pl->order == 4 ? launch_d1tab32_batch<4>(pl->dev32, pl->d_ext32, pl->np, pl->next32, g, s)
+                       : launch_d1tab32_batch<8>(pl->dev32, pl->d_ext32, pl->np, pl->next32, g, s);
+  for (const auto& lv : pl->levels) {
+    if (e != cudaSuccess) break;
+    e = pl->order == 4 ? launch_stage32_batch<4>(pl->dev32, pl->d_tile32, lv.p0, lv.np, lv.tbase, lv.ntiles, lv.C,
+                                                 pl->gz, rk, in, out, s)
+                       : launch_stage32_batch<8>(pl->dev32, pl->d_tile32, lv.p0, lv.np, lv.tbase, lv.ntiles, lv.C,
+                                                 pl->gz, rk, in, out, s);
+  }
+  return e;
+}
+
 // The launch sequence of one RK4 step (captured into the graph).
 cudaError_t enqueue_step(bssn_plan* pl, double dt, cudaStream_t s) {
   const int ins[4] = {0, 1, 2, 1};
   const int outs[4] = {1, 2, 1, 0};
   cudaError_t e = cudaSuccess;
   for (int st = 0; st < 4 && e == cudaSuccess; ++st) {
+    if (pl->prec == BSSN_FP32_RHS) {
+      e = other_all(pl, 0, ins[st], s);
+      if (e == cudaSuccess) e = stage32_all(pl, make_rk(st, dt), ins[st], outs[st], s);
+      continue;
+    }
     e = other_all(pl, 0, ins[st], s);
     if (e == cudaSuccess && pl->prec == BSSN_FP32_RHS) e = other_all(pl, 1, ins[st], s);
     if (e == cudaSuccess) e = other_all(pl, 2, ins[st], s);
@@ -256,16 +294,13 @@ bssn_status_t bssn_plan_create(bssn_plan_t** out, const bssn_block_t* blocks, in
     e = cudaMemcpy(D.buf[1], B.state, n * sizeof(double), cudaMemcpyDeviceToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(D.buf[2], B.state, n * sizeof(double), cudaMemcpyDeviceToDevice);
     if (e == cudaSuccess) e = cudaMemset(D.buf[3], 0, n * sizeof(double));
-    const size_t tab = (size_t)NM * H * B.grid.var_stride;
-    const size_t esz = prec == BSSN_FP64 ? sizeof(double) : sizeof(float);
-    if (e == cudaSuccess) e = plan_alloc(pl, 2 * tab * esz, &p);
     if (e != cudaSuccess) break;
-    D.dX = p;
-    D.dY = (char*)p + tab * esz;
-    if (prec == BSSN_FP32_RHS) {
-      e = plan_alloc(pl, n * sizeof(float), &p);
+    if (prec == BSSN_FP64) {
+      const size_t tab = (size_t)NM * H * B.grid.var_stride;
+      e = plan_alloc(pl, 2 * tab * sizeof(double), &p);
       if (e != cudaSuccess) break;
-      D.f32 = (float*)p;
+      D.dX = p;
+      D.dY = (char*)p + tab * sizeof(double);
     }
     if (pl->order == 4) {
       D.c64 = make_coef<4, double>(B.grid, params->ko_eps);
@@ -277,6 +312,65 @@ bssn_status_t bssn_plan_create(bssn_plan_t** out, const bssn_block_t* blocks, in
     pl->points += D.L.npts;
   }
   void* p = nullptr;
+  // FP32-RHS: per patch a single-precision copy and tables in Layout32, and
+  // the tiled kernels' table, sorted by spacing (one stage launch each)
+  if (e == cudaSuccess && prec == BSSN_FP32_RHS) {
+    std::vector<int> ord(nblocks);
+    for (int b = 0; b < nblocks; ++b) ord[b] = b;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+      const bssn_grid_t &A = blocks[a].grid, &Bg = blocks[b].grid;
+      return std::make_tuple(A.dx, A.dy, A.dz) < std::make_tuple(Bg.dx, Bg.dy, Bg.dz);
+    });
+    pl->host32.resize(nblocks);
+    std::vector<long long> t0(nblocks), q0(nblocks), x0(nblocks);
+    long long nt = 0, nq = 0, nx = 0;
+    for (int i = 0; i < nblocks && e == cudaSuccess; ++i) {
+      const int b = ord[i];
+      const bssn_grid_t& G = blocks[b].grid;
+      const Layout32 L32 = make_layout32(G);
+      e = plan_alloc(pl, (size_t)(NV + 2 * NM) * L32.vs * sizeof(float), &p);
+      if (e != cudaSuccess) break;
+      float* f32 = (float*)p;
+      float* tab = f32 + (size_t)NV * L32.vs;
+      Patch32& Q = pl->host32[i];
+      std::memset((void*)&Q, 0, sizeof(Q));
+      const bool ok = pl->order == 4 ? make_patch32<4>(&Q, G, params->ko_eps, pl->host[b].buf, f32, tab)
+                                     : make_patch32<8>(&Q, G, params->ko_eps, pl->host[b].buf, f32, tab);
+      if (!ok) {
+        e = cudaErrorInvalidValue;
+        break;
+      }
+      Q.tile0 = t0[i] = nt;
+      nt += (long long)Q.ntx * Q.nty * ((G.nz + 3) / 4);
+      Q.pad0 = q0[i] = nq;
+      nq += (G.nx + 2LL * G.ghost) * (G.ny + 2LL * G.ghost) * (G.nz + 2LL * G.ghost);
+      Q.ext0 = x0[i] = nx;
+      nx += (long long)G.nx * (G.ny + 2 * H) * (G.nz + 2 * H);
+      if (i == 0 || G.dx != blocks[ord[i - 1]].grid.dx || G.dy != blocks[ord[i - 1]].grid.dy ||
+          G.dz != blocks[ord[i - 1]].grid.dz)
+        pl->levels.push_back({i, 0, Q.tile0, 0, Q.C});
+      pl->levels.back().np += 1;
+      pl->levels.back().ntiles = nt - pl->levels.back().tbase;
+    }
+    pl->ntiles32 = nt;
+    pl->npad32 = nq;
+    pl->next32 = nx;
+    if (e == cudaSuccess) e = plan_alloc(pl, sizeof(Patch32) * nblocks, &p);
+    if (e == cudaSuccess) pl->dev32 = (Patch32*)p;
+    if (e == cudaSuccess) e = plan_alloc(pl, 3 * sizeof(long long) * nblocks, &p);
+    if (e == cudaSuccess) {
+      pl->d_tile32 = (long long*)p;
+      pl->d_pad32 = pl->d_tile32 + nblocks;
+      pl->d_ext32 = pl->d_pad32 + nblocks;
+      e = cudaMemcpy(pl->dev32, pl->host32.data(), sizeof(Patch32) * nblocks, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(pl->d_tile32, t0.data(), sizeof(long long) * nblocks, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->d_pad32, q0.data(), sizeof(long long) * nblocks, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->d_ext32, x0.data(), sizeof(long long) * nblocks, cudaMemcpyHostToDevice);
+    // the tiles are the tiled kernel's 8 x 4 x 4 (shape 6)
+    pl->shape.assign(nblocks, 6);
+    if (e == cudaSuccess) e = pl->order == 4 ? stage32_batch_init<4>() : stage32_batch_init<8>();
+  }
   if (e == cudaSuccess) e = plan_alloc(pl, sizeof(PatchDev) * (nblocks + 1), &p);
   if (e == cudaSuccess) pl->dev = (PatchDev*)p;
   if (e == cudaSuccess) e = plan_alloc(pl, sizeof(long long) * (nblocks + 1), &p);
@@ -304,13 +398,13 @@ bssn_status_t bssn_plan_create(bssn_plan_t** out, const bssn_block_t* blocks, in
 
   // empirical tile-shape tuning, per size class, cached per process; the
   // stage is timed on real difference tables of the initial state
-  if (e == cudaSuccess && autotune) {
+  // (the FP32-RHS form runs the tiled kernel, whose tile is fixed)
+  if (e == cudaSuccess && autotune && prec == BSSN_FP64) {
     e = other_all(pl, 0, 0, pl->cap);
-    if (e == cudaSuccess && prec == BSSN_FP32_RHS) e = other_all(pl, 1, 0, pl->cap);
     if (e == cudaSuccess) e = other_all(pl, 2, 0, pl->cap);
     if (e == cudaSuccess) e = cudaStreamSynchronize(pl->cap);
   }
-  if (e == cudaSuccess && autotune) {
+  if (e == cudaSuccess && autotune && prec == BSSN_FP64) {
     std::map<int, int> rep;  // class -> representative patch (largest)
     for (int b = 0; b < nblocks; ++b) {
       const int c = size_class(blocks[b].grid);

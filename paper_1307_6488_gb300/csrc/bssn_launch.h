@@ -2,6 +2,7 @@
 // per finite-difference order instantiates them).
 #pragma once
 #include "bssn_common.cuh"
+#include "bssn_stage32_types.h"
 
 namespace bssn {
 
@@ -49,6 +50,23 @@ template <int P>
 cudaError_t launch_d1tab32(const Layout32& L32, const bssn_grid_t& G, const float* u, float* tables,
                            cudaStream_t s);
 cudaError_t launch_to_f32t(const Layout& L, const Layout32& L32, const double* u, float* f, cudaStream_t s);
+// The same kernels over many patches (bssn_batch.cu): the table entry of a
+// patch (maps, layouts, weights with its spacing, buffers), the stage of the
+// patches p0 .. p0+np-1 of one spacing whose tiles start at tbase, and the
+// conversion and tables over all patches (grid-stride, `grid` blocks).
+template <int P>
+bool make_patch32(Patch32* D, const bssn_grid_t& G, double eps, double* const buf[4], float* f32, float* tab);
+template <int P>
+cudaError_t stage32_batch_init();  // raises the kernel's shared-memory limit (not during a capture)
+template <int P>
+cudaError_t launch_stage32_batch(const Patch32* dev, const long long* tile0, int p0, int np, long long tbase,
+                                 long long ntiles, const Coef32& C, const Gauge& gz, const RK& rk, int in, int out,
+                                 cudaStream_t s);
+template <int P>
+cudaError_t launch_d1tab32_batch(const Patch32* dev, const long long* ext0, int np, long long total, int grid,
+                                 cudaStream_t s);
+cudaError_t launch_to_f32t_batch(const Patch32* dev, const long long* pad0, int np, long long total, int which,
+                                 int grid, cudaStream_t s);
 // Reads and clears the device word in which the tiled stage kernel records
 // a bounded wait that gave up (the caller synchronizes first).
 template <int P>

@@ -96,6 +96,51 @@ cudaError_t launch_stage32<BSSN_ORDER>(const Layout& L, const Layout32& L32, con
 }
 
 template <>
+bool make_patch32<BSSN_ORDER>(Patch32* D, const bssn_grid_t& G, double eps, double* const buf[4], float* f32,
+                              float* tab) {
+  using T = Tile32<BSSN_ORDER>;
+  D->L = make_layout(G);
+  D->L32 = make_layout32(G);
+  D->C = make_coef32<BSSN_ORDER>(G, eps);
+  for (int i = 0; i < 4; ++i) D->buf[i] = buf[i];
+  D->f32 = f32;
+  D->tab = tab;
+  D->ntx = (G.nx + T32X - 1) / T32X;
+  D->nty = (G.ny + T32Y - 1) / T32Y;
+  const Layout32& L32 = D->L32;
+  return map32(&D->M.x, f32, L32, NV, T::SXW, T32Y, T32Z) &&
+         map32(&D->M.y, f32, L32, NV, T32X, T32Y + 2 * T::R, T32Z) &&
+         map32(&D->M.z, f32, L32, NV, T32X, T32Y, T32Z + 2 * T::R) &&
+         map32(&D->M.ty, tab, L32, T32_NTAB, T32X, T32Y + 2 * T::H, T32Z) &&
+         map32(&D->M.tz, tab, L32, T32_NTAB, T32X, T32Y, T32Z + 2 * T::H);
+}
+
+static std::atomic<unsigned long long> g_smem_done_batch;
+
+template <>
+cudaError_t stage32_batch_init<BSSN_ORDER>() {
+  return allow_smem(k_stage32t_batch<BSSN_ORDER>, Tile32<BSSN_ORDER>::SMEM, g_smem_done_batch);
+}
+
+template <>
+cudaError_t launch_stage32_batch<BSSN_ORDER>(const Patch32* dev, const long long* tile0, int p0, int np,
+                                             long long tbase, long long ntiles, const Coef32& C, const Gauge& gz,
+                                             const RK& rk, int in, int out, cudaStream_t s) {
+  using T = Tile32<BSSN_ORDER>;
+  if (ntiles <= 0) return cudaSuccess;
+  k_stage32t_batch<BSSN_ORDER><<<(unsigned int)ntiles, T32N, T::SMEM, s>>>(dev, tile0, p0, np, tbase, C, gz, rk, in,
+                                                                           out);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_d1tab32_batch<BSSN_ORDER>(const Patch32* dev, const long long* ext0, int np, long long total,
+                                             int grid, cudaStream_t s) {
+  k_d1tab32_batch<BSSN_ORDER><<<(unsigned int)grid, 256, 0, s>>>(dev, ext0, np, total);
+  return cudaGetLastError();
+}
+
+template <>
 cudaError_t launch_d1tab32<BSSN_ORDER>(const Layout32& L32, const bssn_grid_t& G, const float* u, float* tables,
                                        cudaStream_t s) {
   constexpr int H = FD<BSSN_ORDER>::H;
@@ -123,6 +168,12 @@ cudaError_t bounds_take_stage32<BSSN_ORDER>(unsigned long long* out) {
 cudaError_t launch_to_f32t(const Layout& L, const Layout32& L32, const double* u, float* f, cudaStream_t s) {
   const long long n = (L.nx + 2LL * L.g) * (L.ny + 2LL * L.g) * (L.nz + 2LL * L.g);
   k_to_f32t<<<(unsigned int)((n + 255) / 256), 256, 0, s>>>(L, L32, u, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32t_batch(const Patch32* dev, const long long* pad0, int np, long long total, int which,
+                                 int grid, cudaStream_t s) {
+  k_to_f32t_batch<<<(unsigned int)grid, 256, 0, s>>>(dev, pad0, np, total, which);
   return cudaGetLastError();
 }
 #endif

@@ -49,6 +49,7 @@
 #include "bssn_common.cuh"
 #include "bssn_cvt.cuh"
 #include "bssn_point.cuh"
+#include "bssn_stage32_types.h"
 #include "bssn_tc.cuh"
 
 namespace bssn {
@@ -88,16 +89,6 @@ struct Tile32 {
                 "TMA destinations must stay 128-byte aligned");
 };
 
-// Weights of the tiled kernel, spacing folded in where it is constant.
-struct Coef32 {
-  float c1[3][5];  // W1[a] / h_d
-  float c2[3][5];  // W2[a] / h_d^2
-  float ko[3][6];  // eps KOSCALE KOW[a] / h_d  (0 when the caller wants no dissipation)
-  float sig[6];    // (w_a + w_-a) / 2 of the upwind weights
-  float tau[6];    // (w_a - w_-a) / 2
-  float ih[3];     // 1 / h_d
-};
-
 template <int P>
 Coef32 make_coef32(const bssn_grid_t& G, double eps) {
   using F = FD<P>;
@@ -120,12 +111,6 @@ Coef32 make_coef32(const bssn_grid_t& G, double eps) {
   }
   return C;
 }
-
-// Tensor maps of one launch (each fixes one box shape).
-struct Stage32Maps {
-  CUtensorMap x, y, z;  // state copy: boxes {24, 4, 4, 1}, {8, 4 + 2r, 4, 1}, {8, 4, 4 + 2r, 1}
-  CUtensorMap ty, tz;   // tables:     boxes {8, 4 + p, 4, 1}, {8, 4, 4 + p, 1}
-};
 
 __device__ __forceinline__ void prefetch_tmap(const void* p) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(p) : "memory");
@@ -174,10 +159,12 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 
 // MODE 0: RK stage (right-hand side + dissipation, then the update).
 // MODE 1: right-hand side (+ advection, no dissipation: pass eps = 0) into out.
+// The work of one block: tile b of a grid cut into ntx x nty x ... tiles.
+// The single-grid kernel and the batched-patch kernel below both run it.
 template <int P, int MODE>
-__global__ void __launch_bounds__(T32N, T32_MIN_BLOCKS)
-    k_stage32t(Layout L, Layout32 L32, Coef32 C, Gauge gz, RK rk, Stage32Ptrs S,
-               const __grid_constant__ Stage32Maps M, int ntx, int nty) {
+__device__ __forceinline__ void stage32_tile(const Layout& L, const Layout32& L32, const Coef32& C, const Gauge& gz,
+                                             const RK& rk, const Stage32Ptrs& S, const Stage32Maps& M, int b,
+                                             int ntx, int nty) {
   using T = Tile32<P>;
   constexpr int R = T::R, H = T::H;
   extern __shared__ __align__(128) unsigned char sm_raw[];
@@ -190,7 +177,6 @@ __global__ void __launch_bounds__(T32N, T32_MIN_BLOCKS)
 
   const int t = threadIdx.x;
   const int tx = t & (T32X - 1), ty = (t / T32X) & (T32Y - 1), tz = t / (T32X * T32Y);
-  const int b = blockIdx.x;
   const int x0 = (b % ntx) * T32X, y0 = ((b / ntx) % nty) * T32Y, z0 = (b / (ntx * nty)) * T32Z;
 
   if (t == 0) {
@@ -503,14 +489,52 @@ __global__ void __launch_bounds__(T32N, T32_MIN_BLOCKS)
       tc::mbar_wait(&full[v % T32_NBUF], (uint32_t)(v / T32_NBUF) & 1u, STAGE32_WAIT_NS);
 }
 
+template <int P, int MODE>
+__global__ void __launch_bounds__(T32N, T32_MIN_BLOCKS)
+    k_stage32t(Layout L, Layout32 L32, Coef32 C, Gauge gz, RK rk, Stage32Ptrs S,
+               const __grid_constant__ Stage32Maps M, int ntx, int nty) {
+  stage32_tile<P, MODE>(L, L32, C, gz, rk, S, M, (int)blockIdx.x, ntx, nty);
+}
+
+// index of the patch whose first entry (start[], ascending) is the last one <= t
+__device__ __forceinline__ int patch_of(const long long* __restrict__ start, int n, long long t) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// RK4 stage of many patches that share one spacing (one level) in one
+// launch: block -> (patch, tile) through the patches' first tiles; the
+// patch's maps, layouts and buffers come from its entry of the device table
+// (the maps stay in global memory, where the TMA unit reads them), the
+// weights from the launch parameters, where the arithmetic reads them as
+// constant operands.
+template <int P>
+__global__ void __launch_bounds__(T32N, T32_MIN_BLOCKS)
+    k_stage32t_batch(const Patch32* __restrict__ PP, const long long* __restrict__ tile0, int p0, int np,
+                     long long tbase, Coef32 C, Gauge gz, RK rk, int in, int out) {
+  const long long tb = tbase + blockIdx.x;
+  const int pb = p0 + patch_of(tile0 + p0, np, tb);
+  const Patch32& D = PP[pb];
+  Stage32Ptrs S;
+  S.ys64 = D.buf[in];
+  S.ys32 = D.f32;
+  S.y0 = D.buf[0];
+  S.acc = D.buf[3];
+  S.out = D.buf[out];
+  S.out32 = nullptr;
+  stage32_tile<P, 0>(D.L, D.L32, C, gz, rk, S, D.M, (int)(tb - D.tile0), D.ntx, D.nty);
+}
+
 // ---------------------------------------------------------------- helpers
-// FP64 state (Layout) -> single-precision copy (Layout32), every padded point.
-static __global__ void __launch_bounds__(256) k_to_f32t(Layout L, Layout32 L32, const double* __restrict__ u,
-                                                        float* __restrict__ f) {
+// FP64 state (Layout) -> single-precision copy (Layout32), padded point lin.
+__device__ __forceinline__ void to_f32t_point(const Layout& L, const Layout32& L32, const double* __restrict__ u,
+                                              float* __restrict__ f, long long lin) {
   const long long ex = L.nx + 2LL * L.g, ey = L.ny + 2LL * L.g, ez = L.nz + 2LL * L.g;
-  const long long n = ex * ey * ez;
-  const long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (lin >= n) return;
+  if (lin < 0 || lin >= ex * ey * ez) return;
   const int i = (int)(lin % ex) - L.g;
   const long long r = lin / ex;
   const int j = (int)(r % ey) - L.g;
@@ -522,15 +546,31 @@ static __global__ void __launch_bounds__(256) k_to_f32t(Layout L, Layout32 L32, 
   for (int v = 0; v < NV; ++v) f[v * L32.vs + q] = f64_to_f32_rn(__ldg(u + v * L.vs + p));
 }
 
+static __global__ void __launch_bounds__(256) k_to_f32t(Layout L, Layout32 L32, const double* __restrict__ u,
+                                                        float* __restrict__ f) {
+  to_f32t_point(L, L32, u, f, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
+
+// the same for every padded point of buffer `which` of all patches
+static __global__ void __launch_bounds__(256) k_to_f32t_batch(const Patch32* __restrict__ PP,
+                                                              const long long* __restrict__ pad0, int np,
+                                                              long long total, int which) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const Patch32& D = PP[patch_of(pad0, np, t)];
+    to_f32t_point(D.L, D.L32, D.buf[which], D.f32, t - D.pad0);
+  }
+}
+
 // D_x u and D_y u of the 11 mixed variables in Layout32 (tables 0..10: D_x,
-// 11..21: D_y), over interior x, y and z widened by p/2 (D_y: interior y).
+// 11..21: D_y), over interior x, y and z widened by p/2 (D_y: interior y);
+// table point lin.
 template <int P>
-__global__ void __launch_bounds__(256) k_d1tab32(Layout32 L, Coef32 C, const float* __restrict__ u,
-                                                 float* __restrict__ tab) {
+__device__ __forceinline__ void d1tab32_point(const Layout32& L, const Coef32& C, const float* __restrict__ u,
+                                              float* __restrict__ tab, long long lin) {
   constexpr int H = FD<P>::H;
   const long long ex = L.nx, ey = L.ny + 2 * H, ez = L.nz + 2 * H;
-  const long long lin = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (lin >= ex * ey * ez) return;
+  if (lin < 0 || lin >= ex * ey * ez) return;
   const int i = (int)(lin % ex);
   const long long r = lin / ex;
   const int j = (int)(r % ey) - H;
@@ -551,6 +591,23 @@ __global__ void __launch_bounds__(256) k_d1tab32(Layout32 L, Coef32 C, const flo
       for (int a = 2; a <= H; ++a) ry = fmaf(C.c1[1][a], __ldg(v + p + a * L.sy) - __ldg(v + p - a * L.sy), ry);
       tab[(NM + m) * L.vs + p] = ry;
     }
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_d1tab32(Layout32 L, Coef32 C, const float* __restrict__ u,
+                                                 float* __restrict__ tab) {
+  d1tab32_point<P>(L, C, u, tab, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
+
+// the same for all patches (each with its own spacing)
+template <int P>
+__global__ void __launch_bounds__(256) k_d1tab32_batch(const Patch32* __restrict__ PP,
+                                                       const long long* __restrict__ ext0, int np, long long total) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const Patch32& D = PP[patch_of(ext0, np, t)];
+    d1tab32_point<P>(D.L32, D.C, D.f32, D.tab, t - D.ext0);
   }
 }
 

@@ -51,12 +51,7 @@ def step_single(u, g, h, p, prec, dt):
     return B.download(s, grid)
 
 
-# two single-precision evaluations of the same step, differing in rounding
-# order only, relative to the step's change per tensor field
-FP32_ORDER_TOL = 1e-4
-
-
-@pytest.mark.parametrize("order,prec", [(4, B.FP64), (8, B.FP64), (4, B.FP32_RHS)])
+@pytest.mark.parametrize("order,prec", [(4, B.FP64), (8, B.FP64), (4, B.FP32_RHS), (8, B.FP32_RHS)])
 @pytest.mark.parametrize("autotune", [0, 1])
 def test_batch_step_matches_single_grid(order, prec, autotune):
     torch = need_gpu()
@@ -75,7 +70,9 @@ def test_batch_step_matches_single_grid(order, prec, autotune):
         pts, tiles, shapes = B.plan_info(plan, len(blocks))
         assert pts == sum(np.prod(n) for (n, _, _, _) in patches)
         assert np.all((shapes >= 0) & (shapes < 7))
-        if autotune == 0:
+        if prec == B.FP32_RHS:
+            assert np.all(shapes == 6)  # the tiled kernel's fixed 8 x 4 x 4 tiles
+        elif autotune == 0:
             assert np.all(shapes == 0)
         for step in range(2):
             B.batch_step(plan, dt)
@@ -83,13 +80,13 @@ def test_batch_step_matches_single_grid(order, prec, autotune):
         for (n, g, h, u), (grid, st, _) in zip(patches, keep):
             want = step_single(step_single(u, g, h, p, prec, dt), g, h, p, prec, dt)
             got = B.download(st, grid)
+            if prec == B.FP32_RHS:
+                # the same tiled kernel, tables and conversions as the single
+                # grid: bit for bit
+                np.testing.assert_array_equal(got, want)
+                continue
             err = rel_err_tensor(got - u, want - u, g)
-            # FP32-RHS: the patches' per-point gather and the single grid's
-            # tiled kernel evaluate the same single-precision arithmetic in a
-            # different order (upwinding from paired sums), so they agree to
-            # single-precision rounding, not bit for bit
-            tol = RHS_TOL if prec == B.FP64 else FP32_ORDER_TOL
-            assert np.max(err) < tol, (n, dict(zip(inputs.VARS, err)))
+            assert np.max(err) < RHS_TOL, (n, dict(zip(inputs.VARS, err)))
     finally:
         B.plan_destroy(plan)
 
