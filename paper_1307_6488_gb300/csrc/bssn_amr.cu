@@ -528,6 +528,13 @@ struct Level {
   DevList<RadEntry> rad;
   double* pbuf = nullptr;       // 5 x 24 x pro.n
   double h[3];
+  // FP32-RHS form: the tiled kernel's table of the level's patches (same
+  // order as ids; the padded-point and table-point offsets are d_pad0 and
+  // d_ext0) and the level's weights
+  Patch32* dev32 = nullptr;
+  long long* d_tile32 = nullptr;
+  long long ntiles32 = 0;
+  Coef32 C32{};
 };
 
 }  // namespace
@@ -541,6 +548,7 @@ struct bssn_amr {
   long long N[3] = {0, 0, 0};
   double v_gauge = 1.0;
   std::vector<PatchDev> host;
+  std::vector<Patch32> host32;  // FP32-RHS form: tiled-kernel entry per patch (input order)
   PatchDev* all = nullptr;
   std::vector<Level> lev;
   double* X1 = nullptr;         // separable prolongation scratch, shared by the levels
@@ -770,19 +778,27 @@ void diffs_level(bssn_amr* A, Level& L, int which, cudaStream_t s) {
 }
 
 cudaError_t compute_stage(bssn_amr* A, Level& L, const RK& rk, int in, int out, cudaStream_t s) {
-  const bool f64 = A->prec == BSSN_FP64;
-  if (!f64) {
-    const unsigned int g = (unsigned int)std::max<long long>(
-        1, std::min<long long>(A->grid_other, (L.npad + 255) / 256));
-    kb_to_f32<<<g, 256, 0, s>>>(L.dev, L.d_pad0, (int)L.ids.size(), L.npad, in);
-    ++A->nodes;
+  if (A->prec == BSSN_FP32_RHS) {
+    // the single grids' TMA-tiled kernel over the level's patches (one spacing)
+    const int n = (int)L.ids.size();
+    const int g1 = (int)std::max<long long>(1, std::min<long long>(A->grid_other, (L.npad + 255) / 256));
+    const int g2 = (int)std::max<long long>(1, std::min<long long>(A->grid_other, (L.next + 255) / 256));
+    cudaError_t e = launch_to_f32t_batch(L.dev32, L.d_pad0, n, L.npad, in, g1, s);
+    if (e == cudaSuccess)
+      e = A->order == 4 ? launch_d1tab32_batch<4>(L.dev32, L.d_ext0, n, L.next, g2, s)
+                        : launch_d1tab32_batch<8>(L.dev32, L.d_ext0, n, L.next, g2, s);
+    if (e == cudaSuccess)
+      e = A->order == 4 ? launch_stage32_batch<4>(L.dev32, L.d_tile32, 0, n, 0, L.ntiles32, L.C32, A->gz, rk, in, out, s)
+                        : launch_stage32_batch<8>(L.dev32, L.d_tile32, 0, n, 0, L.ntiles32, L.C32, A->gz, rk, in, out, s);
+    A->nodes += 3;
+    return e;
   }
   if (A->order == 4) {
-    if (f64) { diffs_level<4, double>(A, L, in, s); stage_level<4, double>(A, L, rk, in, out, s); }
-    else { diffs_level<4, float>(A, L, in, s); stage_level<4, float>(A, L, rk, in, out, s); }
+    diffs_level<4, double>(A, L, in, s);
+    stage_level<4, double>(A, L, rk, in, out, s);
   } else {
-    if (f64) { diffs_level<8, double>(A, L, in, s); stage_level<8, double>(A, L, rk, in, out, s); }
-    else { diffs_level<8, float>(A, L, in, s); stage_level<8, float>(A, L, rk, in, out, s); }
+    diffs_level<8, double>(A, L, in, s);
+    stage_level<8, double>(A, L, rk, in, out, s);
   }
   return cudaGetLastError();
 }
@@ -908,6 +924,7 @@ bssn_status_t bssn_amr_create(bssn_amr_t** out, const bssn_amr_patch_t* patches,
   // host geometry and per-patch storage
   std::vector<HostPatch> H(npatches);
   A->host.resize(npatches);
+  if (prec == BSSN_FP32_RHS) A->host32.resize(npatches);
   cudaError_t e = cudaSuccess;
   for (int b = 0; b < npatches && e == cudaSuccess; ++b) {
     const bssn_amr_patch_t& P = patches[b];
@@ -944,16 +961,27 @@ bssn_status_t bssn_amr_create(bssn_amr_t** out, const bssn_amr_patch_t* patches,
       if (D.buf[k] && k != 3) e = cudaMemcpy(D.buf[k], P.state, nd * sizeof(double), cudaMemcpyDeviceToDevice);
     if (e == cudaSuccess) e = cudaMemset(D.buf[3], 0, nd * sizeof(double));
     const int Hh = A->order / 2;
-    const size_t tab = (size_t)NM * Hh * P.var_stride;
-    const size_t esz = prec == BSSN_FP64 ? sizeof(double) : sizeof(float);
-    if (e == cudaSuccess) e = amr_alloc(A, 2 * tab * esz, &p);
     if (e != cudaSuccess) break;
-    D.dX = p;
-    D.dY = (char*)p + tab * esz;
-    if (prec == BSSN_FP32_RHS) {
-      e = amr_alloc(A, nd * sizeof(float), &p);
+    if (prec == BSSN_FP64) {
+      const size_t tab = (size_t)NM * Hh * P.var_stride;
+      e = amr_alloc(A, 2 * tab * sizeof(double), &p);
       if (e != cudaSuccess) break;
-      D.f32 = (float*)p;
+      D.dX = p;
+      D.dY = (char*)p + tab * sizeof(double);
+    } else {
+      // single-precision copy and D_x / D_y tables in Layout32 (tiled kernel)
+      const Layout32 L32 = make_layout32(G);
+      e = amr_alloc(A, (size_t)(NV + 2 * NM) * L32.vs * sizeof(float), &p);
+      if (e != cudaSuccess) break;
+      Patch32& Q = A->host32[b];
+      std::memset((void*)&Q, 0, sizeof(Q));
+      float* f32 = (float*)p;
+      const bool ok = A->order == 4 ? make_patch32<4>(&Q, G, params->ko_eps, D.buf, f32, f32 + (size_t)NV * L32.vs)
+                                    : make_patch32<8>(&Q, G, params->ko_eps, D.buf, f32, f32 + (size_t)NV * L32.vs);
+      if (!ok) {
+        e = cudaErrorInvalidValue;
+        break;
+      }
     }
     if (A->order == 4) {
       D.c64 = make_coef<4, double>(G, params->ko_eps);
@@ -1063,7 +1091,35 @@ bssn_status_t bssn_amr_create(bssn_amr_t** out, const bssn_amr_patch_t* patches,
       L.d_pad0 = (long long*)p;
       e = cudaMemcpy(p, p0.data(), sizeof(long long) * nl, cudaMemcpyHostToDevice);
     }
+    if (e == cudaSuccess && prec == BSSN_FP32_RHS) {
+      // the tiled kernel's entries in level order, 8 x 4 x 4 tiles
+      std::vector<Patch32> t32(nl);
+      std::vector<long long> q0(nl);
+      long long nq = 0;
+      for (int i = 0; i < nl; ++i) {
+        Patch32 Q = A->host32[L.ids[i]];
+        Q.tile0 = q0[i] = nq;
+        nq += (long long)Q.ntx * Q.nty * ((Q.L.nz + 3) / 4);
+        Q.pad0 = p0[i];
+        Q.ext0 = e0[i];
+        t32[i] = Q;
+      }
+      L.ntiles32 = nq;
+      L.C32 = t32[0].C;
+      e = amr_alloc(A, sizeof(Patch32) * nl, &p);
+      if (e == cudaSuccess) {
+        L.dev32 = (Patch32*)p;
+        e = cudaMemcpy(p, t32.data(), sizeof(Patch32) * nl, cudaMemcpyHostToDevice);
+      }
+      if (e == cudaSuccess) e = amr_alloc(A, sizeof(long long) * nl, &p);
+      if (e == cudaSuccess) {
+        L.d_tile32 = (long long*)p;
+        e = cudaMemcpy(p, q0.data(), sizeof(long long) * nl, cudaMemcpyHostToDevice);
+      }
+    }
   }
+  if (e == cudaSuccess && nested && prec == BSSN_FP32_RHS)
+    e = A->order == 4 ? stage32_batch_init<4>() : stage32_batch_init<8>();
   if (e == cudaSuccess && nested) e = cudaStreamCreateWithFlags(&A->cap, cudaStreamNonBlocking);
   int dev = 0, sms = 0, occ = 1;
   if (e == cudaSuccess && nested) e = cudaGetDevice(&dev);

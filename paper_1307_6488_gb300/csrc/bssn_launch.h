@@ -55,7 +55,7 @@ cudaError_t launch_to_f32t(const Layout& L, const Layout32& L32, const double* u
 // patches p0 .. p0+np-1 of one spacing whose tiles start at tbase, and the
 // conversion and tables over all patches (grid-stride, `grid` blocks).
 template <int P>
-bool make_patch32(Patch32* D, const bssn_grid_t& G, double eps, double* const buf[4], float* f32, float* tab);
+bool make_patch32(Patch32* D, const bssn_grid_t& G, double eps, double* const buf[6], float* f32, float* tab);
 template <int P>
 cudaError_t stage32_batch_init();  // raises the kernel's shared-memory limit (not during a capture)
 template <int P>

@@ -96,13 +96,13 @@ cudaError_t launch_stage32<BSSN_ORDER>(const Layout& L, const Layout32& L32, con
 }
 
 template <>
-bool make_patch32<BSSN_ORDER>(Patch32* D, const bssn_grid_t& G, double eps, double* const buf[4], float* f32,
+bool make_patch32<BSSN_ORDER>(Patch32* D, const bssn_grid_t& G, double eps, double* const buf[6], float* f32,
                               float* tab) {
   using T = Tile32<BSSN_ORDER>;
   D->L = make_layout(G);
   D->L32 = make_layout32(G);
   D->C = make_coef32<BSSN_ORDER>(G, eps);
-  for (int i = 0; i < 4; ++i) D->buf[i] = buf[i];
+  for (int i = 0; i < 6; ++i) D->buf[i] = buf[i];
   D->f32 = f32;
   D->tab = tab;
   D->ntx = (G.nx + T32X - 1) / T32X;

@@ -32,7 +32,8 @@ struct Patch32 {
   Layout L;        // double-precision state layout
   Layout32 L32;    // single-precision copy and tables
   Coef32 C;        // weights with this patch's spacing and dissipation
-  double* buf[4];  // 0: state (y0, result), 1, 2: stage inputs, 3: accumulator
+  double* buf[6];  // 0: state (y0, result), 1, 2: stage inputs, 3: accumulator; a
+                   // refined hierarchy's parents also 4: third stage input, 5: y0 kept
   float* f32;      // single-precision copy of the current stage input
   float* tab;      // D_x then D_y tables of the mixed variables
   int ntx, nty;    // tiles along x and y
