@@ -148,11 +148,24 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
 // Every wait is bounded; a role that times out sets the error word and the
 // CTA-wide abort flag, the others leave their loops, in-flight copies and
 // MMAs are waited for (bounded) and TMEM is freed.
-constexpr int CONV_THREADS = 576;
-constexpr int EPI_WARPS = 16;
+// Resident convolution CTAs per SM. One (the default) holds all of TMEM,
+// four slabs and 16 epilogue warps. Two (each with half of TMEM, two slabs
+// and 8 epilogue warps, so that one CTA's barrier hand-offs overlap the
+// other's MMAs) measured slower: 0.25 against 0.19-0.20 ms for a 64^3
+// single-sample forward pass.
+#ifndef CONV_CTAS_PER_SM
+#define CONV_CTAS_PER_SM 1
+#endif
+constexpr int CONV_CTAS = CONV_CTAS_PER_SM;
+constexpr int EPI_WARPS = CONV_CTAS == 2 ? 8 : 16;
+constexpr int CONV_THREADS = 32 * (EPI_WARPS + 2);
 constexpr int WG_THREADS = 192;
-constexpr int SLABS = 4;
-constexpr int KMAX = 16;  // accumulator blocks per tile at T = 1 (512 TMEM columns)
+constexpr int SLABS = CONV_CTAS == 2 ? 2 : 4;
+constexpr int KMAX = CONV_CTAS == 2 ? 8 : 16;  // accumulator blocks per tile at T = 1 (this CTA's TMEM columns / 32)
+// dynamic shared memory per CTA: at most what CONV_CTAS CTAs per SM can have,
+// at least enough that no further CTA fits beside them (the TMEM would not)
+constexpr int CONV_SMEM_MAX = CONV_CTAS == 2 ? 115712 : 232448;
+constexpr int CONV_SMEM_MIN = CONV_CTAS == 2 ? 79872 : 118784;
 
 struct ConvPlan {
   int R;              // output rows per unit
@@ -177,7 +190,7 @@ __device__ __forceinline__ void store_chunk(const Geom& G, __nv_bfloat16* buf, i
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(CONV_THREADS, 1)
+__global__ void __launch_bounds__(CONV_THREADS, CONV_CTAS)
     k_conv_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW, Geom G, ConvPlan P,
               const float* __restrict__ bias, float* __restrict__ zout, __nv_bfloat16* __restrict__ act_out,
               const float* __restrict__ zprev, int gelu, unsigned int* err) {
@@ -359,15 +372,22 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
       (void)tc::warp_wait(drain, 0, 100000000ull);
     }
   } else {
-    // ---- epilogue (warps 0-15): lanes 32 (warp % 4) .. +31, channels 8 cq .. 8 cq + 7
-    const int cq = warp >> 2;
-    const uint32_t lane_base = taddr + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(8 * cq);
-    float bq[8];
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 and the
+    // 8-channel chunks cq0 + i EPI_WARPS/4 (i < CPW) of the 4
+    constexpr int CPW = 16 / EPI_WARPS;
+    const int cq0 = warp >> 2;
+    const uint32_t lane_base = taddr + ((uint32_t)((warp & 3) * 32) << 16);
+    float bq[CPW][8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) bq[c] = MODE == 0 ? __ldg(bias + 8 * cq + c) : 0.f;
+    for (int i = 0; i < CPW; ++i)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) bq[i][c] = MODE == 0 ? __ldg(bias + 8 * (cq0 + i * (EPI_WARPS / 4)) + c) : 0.f;
     // every block starts zeroed and empty
     for (int j = 0; j < P.T; ++j)
-      for (int b = 0; b < P.K; ++b) tc::tmem_st8_zero(lane_base + (uint32_t)j * tile_cols + (uint32_t)(32 * b));
+      for (int b = 0; b < P.K; ++b)
+#pragma unroll
+        for (int i = 0; i < CPW; ++i)
+          tc::tmem_st8_zero(lane_base + (uint32_t)j * tile_cols + (uint32_t)(32 * b + 8 * (cq0 + i * (EPI_WARPS / 4))));
     tc::tmem_wait_st();
     tc::fence_before_sync();
     __syncwarp();
@@ -392,44 +412,53 @@ __global__ void __launch_bounds__(CONV_THREADS, 1)
         tc::fence_after_sync();
         const int z = z0 + q;
         for (int j = 0; q < len && j < P.T; ++j) {
-          const uint32_t col = lane_base + (uint32_t)j * tile_cols + (uint32_t)(32 * b);
-          float acc[8];
-          tc::tmem_ld8(col, acc);
-          tc::tmem_st8_zero(col);
+          float acc[CPW][8];
+#pragma unroll
+          for (int i = 0; i < CPW; ++i) {
+            const uint32_t col = lane_base + (uint32_t)j * tile_cols +
+                                 (uint32_t)(32 * b + 8 * (cq0 + i * (EPI_WARPS / 4)));
+            tc::tmem_ld8(col, acc[i]);
+            tc::tmem_st8_zero(col);
+          }
           const int e = XS + 128 * j + 32 * (warp & 3) + lane;
           const int row = e / XS, x = e - row * XS;
           const int y = yb * P.R + row - 1;
           if (x >= G.X || row > P.R || y >= G.Y) continue;
           const long long pt = (((long long)s * G.Z + z) * G.Y + y) * G.X + x;
-          __align__(16) __nv_bfloat16 hv[8];
-          if (MODE == 0) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) acc[c] += bq[c];
-            if (zout) {
-              float4* zo = (float4*)(zout + pt * CH + 8 * cq);
-              zo[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-              zo[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-            }
-            if (act_out) {
+          for (int i = 0; i < CPW; ++i) {
+            const int cq = cq0 + i * (EPI_WARPS / 4);
+            float* a = acc[i];
+            __align__(16) __nv_bfloat16 hv[8];
+            if (MODE == 0) {
 #pragma unroll
-              for (int c = 0; c < 8; ++c) hv[c] = __float2bfloat16_rn(gelu ? gelu_f(acc[c]) : acc[c]);
+              for (int c = 0; c < 8; ++c) a[c] += bq[i][c];
+              if (zout) {
+                float4* zo = (float4*)(zout + pt * CH + 8 * cq);
+                zo[0] = make_float4(a[0], a[1], a[2], a[3]);
+                zo[1] = make_float4(a[4], a[5], a[6], a[7]);
+              }
+              if (act_out) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) hv[c] = __float2bfloat16_rn(gelu ? gelu_f(a[c]) : a[c]);
+                store_chunk(G, act_out, s, z, y, x, cq, hv);
+              }
+            } else {
+              if (zprev) {
+                const float4* zp = (const float4*)(zprev + pt * CH + 8 * cq);
+#pragma unroll
+                for (int q4 = 0; q4 < 2; ++q4) {
+                  const float4 v = __ldg(zp + q4);
+                  a[4 * q4] *= gelu_grad_f(v.x);
+                  a[4 * q4 + 1] *= gelu_grad_f(v.y);
+                  a[4 * q4 + 2] *= gelu_grad_f(v.z);
+                  a[4 * q4 + 3] *= gelu_grad_f(v.w);
+                }
+              }
+#pragma unroll
+              for (int c = 0; c < 8; ++c) hv[c] = __float2bfloat16_rn(a[c]);
               store_chunk(G, act_out, s, z, y, x, cq, hv);
             }
-          } else {
-            if (zprev) {
-              const float4* zp = (const float4*)(zprev + pt * CH + 8 * cq);
-#pragma unroll
-              for (int q4 = 0; q4 < 2; ++q4) {
-                const float4 v = __ldg(zp + q4);
-                acc[4 * q4] *= gelu_grad_f(v.x);
-                acc[4 * q4 + 1] *= gelu_grad_f(v.y);
-                acc[4 * q4 + 2] *= gelu_grad_f(v.z);
-                acc[4 * q4 + 3] *= gelu_grad_f(v.w);
-              }
-            }
-#pragma unroll
-            for (int c = 0; c < 8; ++c) hv[c] = __float2bfloat16_rn(acc[c]);
-            store_chunk(G, act_out, s, z, y, x, cq, hv);
           }
         }
         // zeros written, then the block goes back to the MMA warp
@@ -1069,13 +1098,11 @@ bool make_conv_plan(int X, int R, ConvPlan* out) {
   P.tail_bytes = over > 0 ? (over * 16 + 127) / 128 * 128 : 0;
   P.slab_off = NTAP * W_TAP_BYTES + 128;
   P.bar_off = P.slab_off + SLABS * P.slab_stride + P.tail_bytes;
-  // at least half the SM's shared memory: one CTA per SM, the only one that
-  // can hold the 512 TMEM columns
-  P.smem = std::max(1024 + P.bar_off + 512, 118784);
+  P.smem = std::max(1024 + P.bar_off + 512, CONV_SMEM_MIN);
   int cols = 32;
   while (cols < P.T * P.K * 32) cols *= 2;
   P.tmem_cols = cols;
-  if (P.smem > 232448) return false;
+  if (P.smem > CONV_SMEM_MAX) return false;
   *out = P;
   return true;
 }
@@ -1104,7 +1131,8 @@ int conv_units(const bssn_corrector* c, const Geom& G, ConvPlan* P) {
     Q.nyb = (G.Y + R - 1) / R;
     for (int L = 1; L <= Q.K && L <= G.Z; ++L) {
       const long long units = (long long)G.S * Q.nyb * ((G.Z + L - 1) / L);
-      const double cost = (double)((units + c->sms - 1) / c->sms) * Q.T * (L + 2);
+      const long long slots = (long long)c->sms * CONV_CTAS;
+      const double cost = (double)((units + slots - 1) / slots) * Q.T * (L + 2);
       if (cost < best || (cost == best && units < best_units)) {
         best = cost;
         best_units = units;
@@ -1116,7 +1144,8 @@ int conv_units(const bssn_corrector* c, const Geom& G, ConvPlan* P) {
   if (best == 1e300) return 0;
   P->nzs = (G.Z + P->L - 1) / P->L;
   const long long units = (long long)G.S * P->nyb * P->nzs;
-  return (int)(units < c->sms ? units : c->sms);
+  const long long slots = (long long)c->sms * CONV_CTAS;
+  return (int)(units < slots ? units : slots);
 }
 
 // one layer forward on act[l] (sample count in G) -> z[l] and act[l+1]
