@@ -1,5 +1,5 @@
-"""The compile-time bounds-check mode (SURVEY's substitute for a sanitizer,
-which this pool does not offer): the library builds with -DBSSN_BOUNDS_CHECK
+"""The compile-time bounds-check mode (a substitute for a memory sanitizer):
+the library builds with -DBSSN_BOUNDS_CHECK
 into libbssn_check.so, reports the mode, and counts nothing until a kernel
 runs. The GPU half (tests/test_gpu_bounds.py) runs parity cases on that
 build and requires zero recorded violations."""
