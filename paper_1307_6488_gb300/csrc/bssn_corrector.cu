@@ -13,12 +13,13 @@
 //     operand of each of the 9 in-plane taps is that slab seen through a
 //     descriptor shifted by the tap's entry offset, and each slab serves the
 //     three output planes it neighbours (k_conv_tc below);
-//   weight gradient ("wgrad") - M = 4 taps x 32 input channels, N = 32 output
-//     channels, K = points (one x-row of 64 points per step), from
-//     channels-first copies of the activation (three copies pre-shifted by
-//     dx = -1, 0, +1 so that every TMA box starts 16-byte aligned) and of the
-//     output gradient (128-byte swizzle); each CTA reduces a range of rows
-//     and writes a partial, summed afterwards in a fixed order.
+//   weight gradient ("wgrad") - M = 3 dx taps x 32 input channels (+ 32
+//     discarded rows), N = 32 output channels, K = points (one x-row per
+//     step), from channels-first copies of the activation (three copies
+//     pre-shifted by dx = -1, 0, +1 so that every TMA box starts 16-byte
+//     aligned) and of the output gradient; each CTA streams a range of rows,
+//     keeps all 27 taps' sums in TMEM, and writes a partial, summed
+//     afterwards in a fixed order (k_wgrad_rows below).
 // Activations are zero outside the box (zero padding); the backward pass is
 // its exact adjoint.
 #include <cuda.h>
@@ -45,21 +46,8 @@ constexpr int CH = 32;
 constexpr int NL = 5;
 constexpr int NTAP = 27;
 constexpr int W_TAP_BYTES = CH * CH * 2;  // 2 KB per tap
-constexpr int WG_STAGES = 4;
-constexpr int XOFF = 8;                   // interior column of the channels-first copies
+constexpr int XOFF = 8;  // interior column of the channels-first copies
 constexpr int LAYER_PARAMS = NTAP * CH * CH + CH;
-// weight-gradient tiles for x-rows of XW (32 or 64) points: one channel row is
-// XW * 2 bytes, swizzled with the span that matches it (64 B or 128 B)
-template <int XW>
-struct WG {
-  static constexpr int ROWB = XW * 2;
-  static constexpr int A_BYTES = 4 * CH * ROWB;  // 4 taps x 32 input channels
-  static constexpr int B_BYTES = CH * ROWB;      // 32 output channels
-  static constexpr int SMEM = 1024 + WG_STAGES * (A_BYTES + B_BYTES) + 256;
-  static constexpr uint32_t SBO = 8 * ROWB;      // one 8-row swizzle atom
-  static constexpr int KSTEPS = XW / 16;         // MMAs (K = 16) per row
-  static constexpr tc::Swizzle SWZ = XW == 64 ? tc::SWZ_128B : tc::SWZ_64B;
-};
 
 struct Geom {
   int S, Z, Y, X;  // samples and interior points per axis
@@ -475,46 +463,78 @@ __global__ void __launch_bounds__(CONV_THREADS, CONV_CTAS)
 }
 
 // ---------------------------------------------------------------- wgrad
-// D[(q, ci)][co] = sum over this CTA's rows of sum_x act(p + off_{tap q}, ci) g(p, co),
-// tap q = min(4 * group + q, 26); one K step = one x-row of 64 points.
-// Warp-specialised: warp 4 streams rows through the TMA ring,
-// warp 5 issues the MMAs without waiting on them, warps 0-3 read the single
-// accumulator out at the end.
+// dW[t][co][ci] = sum over points p of act(p + off_t, ci) g(p, co): per CTA a
+// range of output x-rows (s, z, y), all 27 taps at once.
+//   For output row (s, z, y) the activation rows (s, z + dz, y + dy) of the
+//   three dx-shifted channels-first copies are needed, 27 boxes of
+//   32 channels x XW points. Consecutive rows of one plane share 18 of them,
+//   so the rows stream through a ring of 4 "row triples" (entry e: padded
+//   activation row y', its 3 dz planes x 3 dx copies), one new triple per
+//   output row and three at the start of a plane. Output row r uses the
+//   entries e(r) - 2, e(r) - 1, e(r) (dy = -1, 0, +1).
+//   MMA: per (dz, dy) group one M = 128 operand: the three dx boxes of that
+//   entry and plane are adjacent in shared memory (rows: dx-major, then ci),
+//   the fourth 32-row block is whatever follows and its results are
+//   discarded; N = 32 output channels from the output-gradient row; K = the
+//   row's XW points. Nine accumulators of 32 TMEM columns sum over the rows.
+//   warp 4 (one lane) streams triples and gradient rows; warp 5 (whole warp,
+//   one elected lane) issues 9 x XW/16 MMAs per row, frees each gradient
+//   slot after its row and each triple after the last row that reads it;
+//   warps 0-2 write the 27 taps' partial sums at the end (warp 3's lanes
+//   hold the discarded rows).
+constexpr int WR_Y = 4;    // row triples in the ring
+constexpr int WR_B = 4;    // gradient rows in flight
 template <int XW>
-__global__ void __launch_bounds__(WG_THREADS, 2)
-    k_wgrad_tc(const __grid_constant__ CUtensorMap tmXm, const __grid_constant__ CUtensorMap tmX0,
-               const __grid_constant__ CUtensorMap tmXp, const __grid_constant__ CUtensorMap tmG, Geom G,
-               int rows_per_cta, float* __restrict__ partial, unsigned int* err) {
+struct WR {
+  static constexpr int BOX = CH * XW * 2;                // one box: 32 channels x XW points
+  static constexpr int A_BYTES = WR_Y * 9 * BOX + BOX;   // ring + one box of pad (the 4th block of the last group)
+  static constexpr int ONES = 4 * BOX;                   // 128 rows of 1.0: the bias gradient's A operand
+  static constexpr int SMEM = 1024 + A_BYTES + WR_B * BOX + ONES + 256;
+  static constexpr uint32_t SBO = 8 * XW * 2;            // one 8-row swizzle atom
+  static constexpr int KSTEPS = XW / 16;
+  static constexpr tc::Swizzle SWZ = XW == 64 ? tc::SWZ_128B : tc::SWZ_64B;
+};
+
+template <int XW>
+__global__ void __launch_bounds__(WG_THREADS, 1)
+    k_wgrad_rows(const __grid_constant__ CUtensorMap tmXm, const __grid_constant__ CUtensorMap tmX0,
+                 const __grid_constant__ CUtensorMap tmXp, const __grid_constant__ CUtensorMap tmG, Geom G,
+                 int rows_per_cta, float* __restrict__ partial, unsigned int* err) {
+  using W = WR<XW>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* Ast = base;
-  using W = WG<XW>;
-  uint8_t* Bst = base + WG_STAGES * W::A_BYTES;
-  uint64_t* bars = (uint64_t*)(Bst + WG_STAGES * W::B_BYTES);
-  uint64_t* full = bars;
-  uint64_t* empty = bars + WG_STAGES;
-  uint64_t* done = bars + 2 * WG_STAGES;
+  uint8_t* Ast = base;                     // [entry slot][dz][dx] boxes
+  uint8_t* Bst = base + W::A_BYTES;        // [WR_B] gradient rows
+  uint8_t* Ones = Bst + WR_B * W::BOX;     // 128 x XW ones (any swizzle leaves them as they are)
+  uint64_t* bars = (uint64_t*)(Ones + W::ONES);
+  uint64_t* rfull = bars;                  // [WR_B] row r's new triples and gradient row landed
+  uint64_t* bempty = rfull + WR_B;         // [WR_B] gradient slot free
+  uint64_t* yempty = bempty + WR_B;        // [WR_Y] triple slot free
+  uint64_t* done = yempty + WR_Y;
   uint32_t* tslot = (uint32_t*)(done + 1);
   __shared__ volatile int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // the 7 tap groups of one row chunk are neighbouring CTAs, so they run
-  // together and share the chunk's rows in L2
-  const int group = blockIdx.x;
   const long long total_rows = (long long)G.S * G.Z * G.Y;
-  const long long r0 = (long long)blockIdx.y * rows_per_cta;
+  const long long r0 = (long long)blockIdx.x * rows_per_cta;
   const int nrows = (int)(r0 >= total_rows ? 0 : (total_rows - r0 < rows_per_cta ? total_rows - r0 : rows_per_cta));
+  // plane (s, z) of a row, and whether row r starts a new window
+  auto plane_of = [&](long long R) { return R / G.Y; };
+  auto fresh = [&](int k) { return k == 0 || plane_of(r0 + k) != plane_of(r0 + k - 1); };
 
+  for (int i = tid; i < W::ONES / 4; i += blockDim.x) ((uint32_t*)Ones)[i] = 0x3F803F80u;  // BF16 1.0 pairs
+  tc::fence_proxy_async();
   if (tid == 0) {
     abort_flag = 0;
-    for (int i = 0; i < WG_STAGES; ++i) {
-      tc::mbar_init(&full[i], 1);
-      tc::mbar_init(&empty[i], 1);
+    for (int i = 0; i < WR_B; ++i) {
+      tc::mbar_init(&rfull[i], 1);
+      tc::mbar_init(&bempty[i], 1);
     }
+    for (int i = 0; i < WR_Y; ++i) tc::mbar_init(&yempty[i], 1);
     tc::mbar_init(done, 1);
     tc::mbar_fence_init();
   }
-  if (warp == 0) tc::tmem_alloc(tslot, 32);
+  if (warp == 0) tc::tmem_alloc(tslot, 512);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -522,55 +542,90 @@ __global__ void __launch_bounds__(WG_THREADS, 2)
   constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, 32);
 
   if (warp == 4) {
-    // ---- TMA producer: one x-row of activations (4 taps) and gradient per step
+    // ---- TMA producer
     if (lane == 0 && nrows > 0) {
+      const CUtensorMap* tmx[3] = {&tmXm, &tmX0, &tmXp};
+      int e = -1;  // last triple issued
       int issued = 0;
-      for (int k = 0; k < nrows; ++k) {
-        const int slot = k % WG_STAGES;
-        if (k >= WG_STAGES && !tc::mbar_wait_or_abort(&empty[slot], ((k / WG_STAGES) - 1) & 1, &abort_flag)) {
-          if (!abort_flag) atomicOr(err, 4u);
-          abort_flag = 1;
-          break;
-        }
+      bool ok = true;
+      for (int k = 0; ok && k < nrows; ++k) {
         const long long R = r0 + k;
         const int y = (int)(R % G.Y);
         const long long rz = R / G.Y;
         const int z = (int)(rz % G.Z);
         const int s = (int)(rz / G.Z);
-        tc::mbar_expect_tx(&full[slot], W::A_BYTES + W::B_BYTES);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int tap = min(4 * group + q, NTAP - 1);
-          const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-          const CUtensorMap* tm = dx < 0 ? &tmXm : (dx == 0 ? &tmX0 : &tmXp);
-          tc::tma_load_4d(Ast + slot * W::A_BYTES + q * (CH * W::ROWB), tm, XOFF, y + 1 + dy,
-                          s * (G.Z + 2) + z + 1 + dz, 0, &full[slot]);
+        const int bs = k % WR_B;
+        if (k >= WR_B && !tc::mbar_wait_or_abort(&bempty[bs], ((k / WR_B) - 1) & 1, &abort_flag)) {
+          ok = false;
+          break;
         }
-        tc::tma_load_4d(Bst + slot * W::B_BYTES, &tmG, XOFF, y + 1, s * (G.Z + 2) + z + 1, 0, &full[slot]);
+        // the triples this row adds: padded rows y, y+1, y+2 at a plane start, else y+2
+        const int first = fresh(k) ? 0 : 2;
+        const int nnew = 3 - first;
+        for (int t = first; ok && t < 3; ++t) {
+          const int ee = e + 1 + (t - first);
+          if (ee >= WR_Y && !tc::mbar_wait_or_abort(&yempty[ee % WR_Y], ((ee / WR_Y) - 1) & 1, &abort_flag)) ok = false;
+        }
+        if (!ok) break;
+        tc::mbar_expect_tx(&rfull[bs], (uint32_t)((nnew * 9 + 1) * W::BOX));
+        for (int t = first; t < 3; ++t) {
+          ++e;
+          uint8_t* slot = Ast + (e % WR_Y) * 9 * W::BOX;
+          // padded row y + t holds activation row y - 1 + t (dy = t - 1)
+#pragma unroll
+          for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx)
+              tc::tma_load_4d(slot + (dz * 3 + dx) * W::BOX, tmx[dx], XOFF, y + t, s * (G.Z + 2) + z + dz, 0,
+                              &rfull[bs]);
+        }
+        tc::tma_load_4d(Bst + bs * W::BOX, &tmG, XOFF, y + 1, s * (G.Z + 2) + z + 1, 0, &rfull[bs]);
         issued = k + 1;
       }
-      // the last use of every slot has landed before the CTA leaves
-      for (int k = issued > WG_STAGES ? issued - WG_STAGES : 0; k < issued; ++k)
-        (void)tc::mbar_wait(&full[k % WG_STAGES], (k / WG_STAGES) & 1, 100000000ull);
+      if (!ok) {
+        if (!abort_flag) atomicOr(err, 4u);
+        abort_flag = 1;
+      }
+      // every copy has landed before the CTA leaves
+      for (int k = issued > WR_B ? issued - WR_B : 0; k < issued; ++k)
+        (void)tc::mbar_wait(&rfull[k % WR_B], (k / WR_B) & 1, 100000000ull);
     }
   } else if (warp == 5) {
-    // ---- MMA issuer: never waits for an MMA, only for data; the whole warp
-    // runs the loop on warp-uniform descriptors, one elected lane issues
+    // ---- MMA issuer (warp-uniform, one elected lane issues)
     if (nrows > 0) {
       bool ok = true;
+      int e = -1;
       for (int k = 0; k < nrows; ++k) {
-        const int slot = k % WG_STAGES;
-        if (!tc::warp_wait_or_abort(&full[slot], (k / WG_STAGES) & 1, &abort_flag)) {
+        const int bs = k % WR_B;
+        e += fresh(k) ? 3 : 1;
+        if (!tc::warp_wait_or_abort(&rfull[bs], (k / WR_B) & 1, &abort_flag)) {
           ok = false;
           break;
         }
         tc::fence_after_sync();
-        const uint64_t ad = tc::smem_desc(tc::smem_u32(Ast + slot * W::A_BYTES), 16, W::SBO, W::SWZ);
-        const uint64_t bd = tc::smem_desc(tc::smem_u32(Bst + slot * W::B_BYTES), 16, W::SBO, W::SWZ);
+        const uint64_t bd = tc::smem_desc(tc::smem_u32(Bst + bs * W::BOX), 16, W::SBO, W::SWZ);
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+          const int ent = e - 2 + dy;
+#pragma unroll
+          for (int dz = 0; dz < 3; ++dz) {
+            const uint64_t ad =
+                tc::smem_desc(tc::smem_u32(Ast + ((ent % WR_Y) * 9 + dz * 3) * W::BOX), 16, W::SBO, W::SWZ);
+            const uint32_t d = taddr + (uint32_t)((dz * 3 + dy) * 32);
+#pragma unroll
+            for (int j = 0; j < W::KSTEPS; ++j)
+              tc::mma_bf16_elect(d, ad + 2 * j, bd + 2 * j, IDESC, (k > 0 || j > 0) ? 1u : 0u);
+          }
+        }
+        // bias gradient: ones x gradient row, every TMEM lane gets the row's sums
+        const uint64_t od = tc::smem_desc(tc::smem_u32(Ones), 16, W::SBO, W::SWZ);
 #pragma unroll
         for (int j = 0; j < W::KSTEPS; ++j)
-          tc::mma_bf16_elect(taddr, ad + 2 * j, bd + 2 * j, IDESC, (k > 0 || j > 0) ? 1u : 0u);
-        tc::mma_commit_elect(&empty[slot]);
+          tc::mma_bf16_elect(taddr + 9 * 32, od + 2 * j, bd + 2 * j, IDESC, (k > 0 || j > 0) ? 1u : 0u);
+        tc::mma_commit_elect(&bempty[bs]);
+        // triples no later row reads: the oldest one, or all three before a new plane
+        const int keep_from = (k + 1 < nrows && !fresh(k + 1)) ? e - 1 : e + 1;
+        for (int q = e - 2; q < keep_from; ++q) tc::mma_commit_elect(&yempty[q % WR_Y]);
       }
       if (!ok && lane == 0) {
         if (!abort_flag) atomicOr(err, 4u);
@@ -580,7 +635,8 @@ __global__ void __launch_bounds__(WG_THREADS, 2)
       tc::mma_commit_elect(done);
     }
   }
-  // ---- epilogue (warps 0-3; the other two warps only meet the barriers)
+  // ---- epilogue (warps 0-2: TMEM lanes 32 w .. = input channels of dx = w - 1;
+  // warp 3: the bias gradient, columns 288 .. 319 of any lane)
   bool ok = false;
   if (warp < 4 && nrows > 0) {
     ok = tc::mbar_wait(done, 0);
@@ -589,33 +645,65 @@ __global__ void __launch_bounds__(WG_THREADS, 2)
     ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
   }
   tc::fence_after_sync();
-  if (warp < 4) {
-    float* out = partial + (((long long)group * gridDim.y + blockIdx.y) * 128 + warp * 32 + lane) * CH;
-    if (ok) {
+  if (warp < 3) {
+    for (int g = 0; g < 9; ++g) {
+      const int dz = g / 3, dy = g % 3, t = dz * 9 + dy * 3 + warp;
+      // partial[b][t][co][ci]: lane = ci, so each co is one coalesced 128-byte row
+      float* out = partial + ((long long)blockIdx.x * NTAP + t) * CH * CH + lane;
       float acc[32];
-      tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16), acc);
+      if (ok) {
+        tc::tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * 32), acc);
+      } else {
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        ((float4*)out)[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        for (int co = 0; co < 32; ++co) acc[co] = 0.f;
+      }
+#pragma unroll
+      for (int co = 0; co < 32; ++co) out[co * CH] = acc[co];
+    }
+  } else if (warp == 3) {
+    float acc[32];
+    if (ok) {
+      tc::tmem_ld32(taddr + ((uint32_t)(3 * 32) << 16) + (uint32_t)(9 * 32), acc);
     } else {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) ((float4*)out)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int co = 0; co < 32; ++co) acc[co] = 0.f;
     }
+    // after the gridDim.x x 27 x 32 x 32 weight partials: gridDim.x x 32 bias partials
+    float* out = partial + (long long)gridDim.x * NTAP * CH * CH + (long long)blockIdx.x * CH;
+    if (lane == 0)
+#pragma unroll
+      for (int co = 0; co < 32; ++co) out[co] = acc[co];
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(taddr, 32);
+  if (warp == 0) tc::tmem_dealloc(taddr, 512);
 }
 
-// dW[t][co][ci] = sum_b partial[group][b][(q, ci)][co] with t = 4 group + q < 27.
-__global__ void k_wgrad_reduce(const float* __restrict__ partial, int nb, float* __restrict__ dW) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // over 27*32*32
-  if (idx >= NTAP * CH * CH) return;
-  const int t = idx / (CH * CH), co = (idx / CH) % CH, ci = idx % CH;
-  const int group = t / 4, q = t % 4;
+// dW[t][co][ci] = sum_b partial[b][t][co][ci] and db[co] = sum_b
+// bias_partial[b][co] (db follows dW in the layer's parameters), in a fixed
+// order: a block of 8 warps takes 32 consecutive outputs (one per lane,
+// coalesced), warp w sums the partials b = w, w + 8, ... in double precision,
+// then the 8 warp sums are added in warp order.
+__global__ void __launch_bounds__(256) k_wgrad_reduce(const float* __restrict__ partial, int nb,
+                                                      float* __restrict__ dW) {
+  __shared__ double part[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int idx = blockIdx.x * 32 + lane;  // over 27*32*32 + 32
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += partial[(((long long)group * nb + b) * 128 + q * 32 + ci) * CH + co];
-  dW[idx] = (float)s;
+  if (idx < NTAP * CH * CH) {
+    for (int b = w; b < nb; b += 8) s += partial[(long long)b * NTAP * CH * CH + idx];
+  } else if (idx < NTAP * CH * CH + CH) {
+    const float* bp = partial + (long long)nb * NTAP * CH * CH + (idx - NTAP * CH * CH);
+    for (int b = w; b < nb; b += 8) s += bp[(long long)b * CH];
+  }
+  part[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && idx < NTAP * CH * CH + CH) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += part[q][lane];
+    dW[idx] = (float)t;
+  }
 }
 
 // Channels-last padded BF16 -> channels-first copy, interior at column XOFF,
@@ -646,65 +734,6 @@ __global__ void k_to_channels_first(Geom G, const __nv_bfloat16* __restrict__ in
 #pragma unroll
     for (int c = 0; c < CH; ++c) out[(long long)c * rows * xp + i] = v[c];
   }
-}
-
-// Bias gradient: db[c] = sum over interior points of g[c] (g padded BF16), fixed order.
-// Bias gradient db[c] = sum over points of g[., c], in two deterministic
-// passes: per-block partials (each thread sums whole 32-channel rows, then the
-// warp and the block reduce), then one warp sums the BIAS_BLOCKS partials.
-constexpr int BIAS_BLOCKS = 304;
-__global__ void __launch_bounds__(256) k_bias_partial(Geom G, const __nv_bfloat16* __restrict__ g,
-                                                      double* __restrict__ part) {
-  float acc[CH];
-#pragma unroll
-  for (int c = 0; c < CH; ++c) acc[c] = 0.f;
-  const long long pts = (long long)G.S * G.Z * G.Y * G.X;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < pts; i += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(i % G.X);
-    const long long r = i / G.X;
-    const int y = (int)(r % G.Y);
-    const long long r2 = r / G.Y;
-    const int z = (int)(r2 % G.Z), s = (int)(r2 / G.Z);
-    const uint4* src = (const uint4*)g + chunk_off(G, s, z + 1, 0, y + 1, x + 1);
-    const long long cs = chunk_stride(G);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint4 v = __ldg(src + q * cs);
-      const __nv_bfloat162* h = (const __nv_bfloat162*)&v;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float2 f = __bfloat1622float2(h[j]);
-        acc[8 * q + 2 * j] += f.x;
-        acc[8 * q + 2 * j + 1] += f.y;
-      }
-    }
-  }
-  __shared__ double sh[8][CH];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // warp transpose-reduce: lane c ends with the warp's sum of channel c
-  double mine = 0.0;
-#pragma unroll
-  for (int c = 0; c < CH; ++c) {
-    double v = acc[c];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == c) mine = v;
-  }
-  sh[warp][lane] = mine;
-  __syncthreads();
-  if (threadIdx.x < CH) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w][threadIdx.x];
-    part[blockIdx.x * CH + threadIdx.x] = t;
-  }
-}
-
-__global__ void k_bias_final(const double* __restrict__ part, int nb, float* __restrict__ db) {
-  const int c = threadIdx.x;
-  if (c >= CH) return;
-  double t = 0.0;
-  for (int b = 0; b < nb; ++b) t += part[b * CH + c];
-  db[c] = (float)t;
 }
 
 // Unpadded BF16 [pts][32] -> interior of a padded buffer.
@@ -1043,7 +1072,6 @@ struct bssn_corrector {
   float* target = nullptr;       // unpadded FP32 targets
   float* partial = nullptr;      // wgrad partials
   double* lpart = nullptr;       // loss partials
-  double* bpart = nullptr;       // bias-gradient partials [BIAS_BLOCKS][32]
   float* params = nullptr;       // FP32 master [NL][LAYER_PARAMS]
   float* grads = nullptr;
   float* adam_m = nullptr;
@@ -1194,7 +1222,6 @@ cudaError_t network_backward(bssn_corrector* c, const Geom& G, cudaStream_t s) {
   const int rpc = (int)((rows + nb - 1) / nb);
   for (int l = NL - 1; l >= 0 && e == cudaSuccess; --l) {
     float* gW = c->grads + (size_t)l * LAYER_PARAMS;
-    float* gb = gW + NTAP * CH * CH;
     // channels-first copies of the layer input and of the gradient
     for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
       k_to_channels_first<<<1024, 256, 0, s>>>(G, c->act[l], c->cf[d], d - 1, c->xp);
@@ -1210,20 +1237,14 @@ cudaError_t network_backward(bssn_corrector* c, const Geom& G, cudaStream_t s) {
     if (!map_cf(&tg, c->cfg, G, c->xp)) return cudaErrorInvalidValue;
     if (e == cudaSuccess) {
       if (G.X == 64)
-        k_wgrad_tc<64><<<dim3(7, nb), WG_THREADS, WG<64>::SMEM, s>>>(tm[0], tm[1], tm[2], tg, G, rpc, c->partial,
-                                                                       c->err);
+        k_wgrad_rows<64><<<nb, WG_THREADS, WR<64>::SMEM, s>>>(tm[0], tm[1], tm[2], tg, G, rpc, c->partial, c->err);
       else
-        k_wgrad_tc<32><<<dim3(7, nb), WG_THREADS, WG<32>::SMEM, s>>>(tm[0], tm[1], tm[2], tg, G, rpc, c->partial,
-                                                                       c->err);
+        k_wgrad_rows<32><<<nb, WG_THREADS, WR<32>::SMEM, s>>>(tm[0], tm[1], tm[2], tg, G, rpc, c->partial, c->err);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-      k_wgrad_reduce<<<(NTAP * CH * CH + 255) / 256, 256, 0, s>>>(c->partial, nb, gW);
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) {
-      k_bias_partial<<<BIAS_BLOCKS, 256, 0, s>>>(G, c->g[cur], c->bpart);
-      k_bias_final<<<1, 32, 0, s>>>(c->bpart, BIAS_BLOCKS, gb);
+      // weight and bias gradients (the bias follows the weights in gW)
+      k_wgrad_reduce<<<(NTAP * CH * CH + CH + 31) / 32, 256, 0, s>>>(c->partial, nb, gW);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess && l > 0) {
@@ -1291,8 +1312,15 @@ bssn_status_t bssn_corrector_create(bssn_corrector_t** out, int n, int max_batch
   c->xp = n + 16;
   c->pts = (long long)max_batch * n * n * n;
   c->pad_pts = (long long)max_batch * (n + 2) * (n + 2) * (n + 2);
-  const long long rows = (long long)max_batch * n * n;
-  c->wg_blocks = (int)(rows < 128 ? rows : 128);
+  // one weight-gradient CTA per SM (each streams a range of rows)
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms < 1)
+      sms = 128;
+    const long long rows = (long long)max_batch * n * n;
+    c->wg_blocks = (int)(rows < sms ? rows : sms);
+  }
   cudaError_t e = cudaSuccess;
   void* p = nullptr;
   for (int l = 0; l < NL && e == cudaSuccess; ++l) {
@@ -1314,12 +1342,10 @@ bssn_status_t bssn_corrector_create(bssn_corrector_t** out, int n, int max_batch
   c->cfg = (__nv_bfloat16*)p;
   if (e == cudaSuccess) e = calloc_dev(c, c->pts * CH * 4, &p);
   c->target = (float*)p;
-  if (e == cudaSuccess) e = calloc_dev(c, (size_t)7 * c->wg_blocks * 128 * CH * 4, &p);
+  if (e == cudaSuccess) e = calloc_dev(c, (size_t)c->wg_blocks * (NTAP * CH * CH + CH) * 4, &p);
   c->partial = (float*)p;
   if (e == cudaSuccess) e = calloc_dev(c, 256 * sizeof(double), &p);
   c->lpart = (double*)p;
-  if (e == cudaSuccess) e = calloc_dev(c, (size_t)BIAS_BLOCKS * CH * sizeof(double), &p);
-  c->bpart = (double*)p;
   const size_t np = (size_t)NL * LAYER_PARAMS;
   if (e == cudaSuccess) e = calloc_dev(c, np * 4, &p);
   c->params = (float*)p;
@@ -1344,16 +1370,16 @@ bssn_status_t bssn_corrector_create(bssn_corrector_t** out, int n, int max_batch
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->conv_smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_wgrad_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, WG<64>::SMEM);
+    e = cudaFuncSetAttribute(k_wgrad_rows<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, WR<64>::SMEM);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_wgrad_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, WG<32>::SMEM);
+    e = cudaFuncSetAttribute(k_wgrad_rows<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, WR<32>::SMEM);
   // ask for the full shared-memory carveout for the tensor-core kernels
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_tc<0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_tc<1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_wgrad_tc<64>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    e = cudaFuncSetAttribute(k_wgrad_rows<64>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_wgrad_tc<32>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    e = cudaFuncSetAttribute(k_wgrad_rows<32>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess) {
     int dev = 0;
     e = cudaGetDevice(&dev);
