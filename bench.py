@@ -1224,7 +1224,7 @@ def main():
                     help="skip the FP32-RHS 256^3 throughput and 96^3 100-step accuracy runs")
     ap.add_argument("--learned-pairs", type=int, default=2000,
                     help="training pairs for the learned form (20 per fine trajectory)")
-    ap.add_argument("--learned-epochs", type=int, default=5)
+    ap.add_argument("--learned-epochs", type=int, default=10)
     ap.add_argument("--corrector-only", action="store_true",
                     help="only the learned corrector's kernels (training steps and forward passes, 64^3): for ncu")
     ap.add_argument("--profile", action="store_true",
