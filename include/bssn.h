@@ -517,7 +517,9 @@ bssn_status_t bssn_corrector_params(bssn_corrector_t* c, float* host, int write)
 /* Copy layer `layer`'s (0..4) pre-activation output of the last forward pass,
  * S samples, to out (DEVICE FP32 [S][n^3][32]). Synchronizes. After
  * bssn_corrector_forward_raw the last layer's output is only in that call's
- * own out buffer (layer 4 here then holds the last training or apply pass). */
+ * own out buffer (layer 4 here then holds the last training or apply pass).
+ * bssn_corrector_apply and bssn_corrector_infer_async keep no hidden-layer
+ * pre-activations: after them layers 0..3 hold those of an earlier pass. */
 bssn_status_t bssn_corrector_layer_output(bssn_corrector_t* c, int layer, int S, float* out);
 /* Copy the gradient of the last loss evaluation to the HOST array (packed). */
 bssn_status_t bssn_corrector_grads(bssn_corrector_t* c, float* host);
@@ -534,6 +536,19 @@ bssn_status_t bssn_corrector_set_step_scale(bssn_corrector_t* c, const double* s
  * [S][n][n][n][32] channels last): out (DEVICE FP32 [S][n^3][32]).
  * Returns BSSN_ERR_TIMEOUT if a bounded device wait gave up. Synchronizes. */
 bssn_status_t bssn_corrector_forward_raw(bssn_corrector_t* c, int S, const void* x_bf16, float* out, void* stream);
+/* Inference for serving: the forward pass of bssn_corrector_forward_raw
+ * (same arguments, bit-identical out) enqueued on stream without
+ * synchronizing, and without keeping the hidden layers' pre-activations
+ * (bssn_corrector_layer_output is then undefined for layers 0..3). x_bf16
+ * and out must stay valid until the stream reaches the call. A bounded device
+ * wait that gives up is latched on the device and reported by the next
+ * bssn_corrector_sync; any other call on c clears the latch when it starts.
+ * Returns BSSN_ERR_CUDA if a launch failed. */
+bssn_status_t bssn_corrector_infer_async(bssn_corrector_t* c, int S, const void* x_bf16, float* out, void* stream);
+/* Wait for the work enqueued on stream, then report (and clear) the device
+ * error latch: BSSN_ERR_TIMEOUT if a wait of an earlier
+ * bssn_corrector_infer_async gave up. Synchronizes. */
+bssn_status_t bssn_corrector_sync(bssn_corrector_t* c, void* stream);
 /* Mean squared error over the first 24 output channels against target
  * (DEVICE FP32 [S][n^3][32]) and its gradient (read with
  * bssn_corrector_grads); *loss is a HOST double. Synchronizes. */

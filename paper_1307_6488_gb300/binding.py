@@ -284,13 +284,16 @@ def _corr_lib():
         L.bssn_corrector_grads.argtypes = [vp, vp]
         L.bssn_corrector_set_scales.argtypes = [vp, vp, vp, vp]
         L.bssn_corrector_forward_raw.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+        L.bssn_corrector_infer_async.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+        L.bssn_corrector_sync.argtypes = [vp, vp]
         L.bssn_corrector_loss_grad_raw.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.POINTER(ctypes.c_double), vp]
         L.bssn_corrector_train_step.argtypes = [vp, ctypes.POINTER(Grid), ctypes.c_int, vp, vp, ctypes.c_float,
                                                 ctypes.POINTER(ctypes.c_double), vp]
         L.bssn_corrector_apply.argtypes = [vp, ctypes.POINTER(Grid), vp, vp]
         L.bssn_corrector_layer_output.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
         for n in ("bssn_corrector_create", "bssn_corrector_destroy", "bssn_corrector_params", "bssn_corrector_grads",
-                  "bssn_corrector_set_scales", "bssn_corrector_forward_raw", "bssn_corrector_loss_grad_raw",
+                  "bssn_corrector_set_scales", "bssn_corrector_forward_raw", "bssn_corrector_infer_async",
+                  "bssn_corrector_sync", "bssn_corrector_loss_grad_raw",
                   "bssn_corrector_train_step", "bssn_corrector_apply", "bssn_corrector_layer_output"):
             getattr(L, n).restype = ctypes.c_int
         L._corr_typed = True
@@ -345,6 +348,16 @@ def corrector_set_step_scale(c, step_scale):
 def corrector_forward_raw(c, S, x_bf16, out, stream=None):
     _check(_corr_lib().bssn_corrector_forward_raw(c, S, _ptr(x_bf16), _ptr(out), _stream(stream)),
            "corrector_forward_raw")
+
+
+def corrector_infer_async(c, S, x_bf16, out, stream=None):
+    """Enqueue an inference pass; returns without waiting (see corrector_sync)."""
+    _check(_corr_lib().bssn_corrector_infer_async(c, S, _ptr(x_bf16), _ptr(out), _stream(stream)),
+           "corrector_infer_async")
+
+
+def corrector_sync(c, stream=None):
+    _check(_corr_lib().bssn_corrector_sync(c, _stream(stream)), "corrector_sync")
 
 
 def corrector_loss_grad_raw(c, S, x_bf16, target, stream=None):

@@ -1203,12 +1203,16 @@ cudaError_t layer_forward(bssn_corrector* c, const Geom& G, int l, float* zout, 
 }
 
 // the whole network; the last layer writes its output to `last` if given
-// (the caller's buffer, same [S][n^3][32] layout), else to z[NL-1]
-cudaError_t network_forward(bssn_corrector* c, const Geom& G, cudaStream_t s, float* last = nullptr) {
+// (the caller's buffer, same [S][n^3][32] layout), else to z[NL-1]. The
+// hidden layers' pre-activations go to z[l] only with keep_pre (the backward
+// pass reads them); inference writes just the activations.
+cudaError_t network_forward(bssn_corrector* c, const Geom& G, cudaStream_t s, float* last = nullptr,
+                            bool keep_pre = true) {
   cudaError_t e = cudaSuccess;
-  for (int l = 0; l < NL && e == cudaSuccess; ++l)
-    e = layer_forward(c, G, l, l == NL - 1 && last ? last : c->z[l], l < NL - 1 ? c->act[l + 1] : nullptr,
-                      l < NL - 1 ? 1 : 0, s);
+  for (int l = 0; l < NL && e == cudaSuccess; ++l) {
+    float* zout = l == NL - 1 ? (last ? last : c->z[l]) : (keep_pre ? c->z[l] : nullptr);
+    e = layer_forward(c, G, l, zout, l < NL - 1 ? c->act[l + 1] : nullptr, l < NL - 1 ? 1 : 0, s);
+  }
   return e;
 }
 
@@ -1500,6 +1504,28 @@ bssn_status_t bssn_corrector_forward_raw(bssn_corrector_t* c, int S, const void*
   return status_of(c, e, s);
 }
 
+bssn_status_t bssn_corrector_infer_async(bssn_corrector_t* c, int S, const void* x_bf16, float* out, void* stream) {
+  if (!c || !x_bf16 || !out || S < 1 || S > c->max_batch) return BSSN_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Geom G = geom_for(c, S);
+  k_pad_copy<<<1024, 256, 0, s>>>(G, (const __nv_bfloat16*)x_bf16, c->act[0]);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = network_forward(c, G, s, out, false);
+  if (e != cudaSuccess) return e == cudaErrorInvalidValue ? BSSN_ERR_UNSUPPORTED : BSSN_ERR_CUDA;
+  return BSSN_OK;
+}
+
+bssn_status_t bssn_corrector_sync(bssn_corrector_t* c, void* stream) {
+  if (!c) return BSSN_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned int err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, c->err, sizeof(err), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(err), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return BSSN_ERR_CUDA;
+  return err ? BSSN_ERR_TIMEOUT : BSSN_OK;
+}
+
 bssn_status_t bssn_corrector_loss_grad_raw(bssn_corrector_t* c, int S, const void* x_bf16, const float* target,
                                            double* loss, void* stream) {
   if (!c || !x_bf16 || !target || !loss || S < 1 || S > c->max_batch) return BSSN_ERR_INVALID_ARG;
@@ -1599,7 +1625,7 @@ bssn_status_t bssn_corrector_apply(bssn_corrector_t* c, const bssn_grid_t* grid,
     k_pack_state<<<512, 256, 0, s>>>(G, L, 0, state, c->coef, c->act[0]);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = network_forward(c, G, s);
+  if (e == cudaSuccess) e = network_forward(c, G, s, nullptr, false);
   if (e == cudaSuccess) {
     k_apply<<<512, 256, 0, s>>>(G, L, c->z[NL - 1], c->coef, state);
     e = cudaGetLastError();

@@ -59,6 +59,14 @@ constexpr int T32X = 8, T32Y = 4, T32Z = 4, T32N = T32X * T32Y * T32Z;
 #ifndef T32_MIN_BLOCKS
 #define T32_MIN_BLOCKS 3
 #endif
+// variable before whose stencils the update's operands are prefetched into
+// L2 (-1: before the variable loop). Two thirds of the way through the loop
+// the lines arrive in time and are still there when the update reads them;
+// prefetched at the start, a 128^3 stage streams more than the L2 holds
+// before they are used (1.35 -> 1.28 ms per stage).
+#ifndef T32_PF_AT
+#define T32_PF_AT 16
+#endif
 #ifndef T32_NBUF_DEF
 #define T32_NBUF_DEF 3
 #endif
@@ -157,6 +165,27 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// The update's double-precision operands (y0; acc from stage 1 on; ys for
+// RK3) of the tile's rows: one prefetch per 64-byte row end, spread over the
+// block's threads, so that they are in L2 when the update reads them.
+__device__ __forceinline__ void prefetch_update_rows(const Layout& L, const RK& rk, const Stage32Ptrs& S, int x0,
+                                                     int y0, int z0, int t) {
+  const double* acc_in = (rk.method == 4 && rk.stage > 0) ? S.acc : nullptr;
+  const double* ys_in = rk.method == 3 ? S.ys64 : nullptr;
+  const int rows = T32Y * T32Z;
+  const int xe = min(x0 + T32X, L.nx) - 1;
+  for (int q = t; q < 3 * NV * rows; q += T32N) {
+    const int which = q / (NV * rows);
+    const double* base = which == 0 ? S.y0 : (which == 1 ? acc_in : ys_in);
+    const int v = (q / rows) % NV, row = q % rows;
+    const int jj = y0 + (row % T32Y), kk = z0 + row / T32Y;
+    if (!base || jj >= L.ny || kk >= L.nz) continue;
+    const double* r0 = base + v * L.vs + L.off0 + jj * L.sy + kk * L.sz;
+    prefetch_l2(r0 + x0);
+    prefetch_l2(r0 + xe);
+  }
+}
+
 // MODE 0: RK stage (right-hand side + dissipation, then the update).
 // MODE 1: right-hand side (+ advection, no dissipation: pass eps = 0) into out.
 // The work of one block: tile b of a grid cut into ntx x nty x ... tiles.
@@ -198,24 +227,8 @@ __device__ __forceinline__ void stage32_tile(const Layout& L, const Layout32& L3
   }
   __syncthreads();
 
-  // the epilogue's double-precision operands (y0; acc from stage 1 on; ys
-  // for RK3) of the tile's rows move into L2 while the stencils run
-  if (MODE == 0) {
-    const double* acc_in = (rk.method == 4 && rk.stage > 0) ? S.acc : nullptr;
-    const double* ys_in = rk.method == 3 ? S.ys64 : nullptr;
-    const int rows = T32Y * T32Z;
-    const int xe = min(x0 + T32X, L.nx) - 1;
-    for (int q = t; q < 3 * NV * rows; q += T32N) {
-      const int which = q / (NV * rows);
-      const double* base = which == 0 ? S.y0 : (which == 1 ? acc_in : ys_in);
-      const int v = (q / rows) % NV, row = q % rows;
-      const int jj = y0 + (row % T32Y), kk = z0 + row / T32Y;
-      if (!base || jj >= L.ny || kk >= L.nz) continue;
-      const double* r0 = base + v * L.vs + L.off0 + jj * L.sy + kk * L.sz;
-      prefetch_l2(r0 + x0);
-      prefetch_l2(r0 + xe);
-    }
-  }
+  // the update's operands move into L2 while the stencils run
+  if (MODE == 0 && T32_PF_AT < 0) prefetch_update_rows(L, rk, S, x0, y0, z0, t);
 
   const int i = x0 + tx, j = y0 + ty, k = z0 + tz;
   const bool valid = i < L.nx && j < L.ny && k < L.nz;
@@ -284,6 +297,7 @@ __device__ __forceinline__ void stage32_tile(const Layout& L, const Layout32& L3
       break;
     }
     consumed = v + 1;
+    if (MODE == 0 && v == T32_PF_AT) prefetch_update_rows(L, rk, S, x0, y0, z0, t);
     const float* slot = sm + s * T::SLOT;
     const float* SX = slot + T::O_X;
     const float* SY = slot + T::O_Y;

@@ -126,6 +126,37 @@ def test_first_layer_at_64_cubed():
         B.corrector_destroy(c)
 
 
+@pytest.mark.parametrize("n,S", [(32, 2), (64, 1)])
+def test_async_inference_is_the_forward_pass(n, S):
+    """The serving call (enqueued without a host wait, no hidden
+    pre-activations stored) gives the synchronous forward pass's output bit
+    for bit, and queued calls on one stream each see their own input."""
+    torch = need_gpu()
+    c = B.corrector_create(n, S, seed=5)
+    try:
+        B.corrector_params(c, seeded_params(41))
+        rng = np.random.default_rng(42 + n)
+        xs = []
+        for _ in range(2):
+            x = np.zeros((S, n, n, n, CH))
+            x[..., :24] = bf16_round(rng.standard_normal((S, n, n, n, 24)))
+            xs.append(to_bf16_tensor(x))
+        want = []
+        for x in xs:
+            o = torch.empty((S * n ** 3, CH), dtype=torch.float32, device="cuda")
+            B.corrector_forward_raw(c, S, x, o)
+            want.append(o)
+        got = [torch.full_like(w, float("nan")) for w in want]
+        for x, o in zip(xs, got):
+            B.corrector_infer_async(c, S, x, o)
+        B.corrector_sync(c)
+        for g, w in zip(got, want):
+            assert torch.equal(g, w)
+        assert not torch.equal(got[0], got[1])
+    finally:
+        B.corrector_destroy(c)
+
+
 def test_loss_and_gradient_match_oracle(net32):
     torch = need_gpu()
     n, S = 32, 1
