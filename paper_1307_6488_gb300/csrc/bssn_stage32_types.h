@@ -16,6 +16,9 @@ struct Coef32 {
   float sig[6];    // (w_a + w_-a) / 2 of the upwind weights
   float tau[6];    // (w_a - w_-a) / 2
   float ih[3];     // 1 / h_d
+  // the same weights as (y, z) pairs for packed single-precision operations
+  float2 c1yz[5], c2yz[5];  // (c1[1][a], c1[2][a]), (c2[1][a], c2[2][a])
+  float2 tau2[6];           // (tau[a], tau[a])
 };
 
 // Tensor maps of one grid (each fixes one box shape).
