@@ -58,9 +58,9 @@ FP64_PIPE_BUSY = {"src_sha": "1bd173c68c3b6f9f", "pct_of_active_cycles": 82.57,
                   "dmul_per_point": 101187584 / 64 ** 3}
 # The same for the tiled FP32-RHS stage kernel k_stage32t<8,0> as
 # bssn_rk4_step runs it (writing the next stage's single-precision input too;
-# one launch at 64^3: 224.9 MB read + 112.8 MB written, 1.29 kB per point,
+# one launch at 64^3: 208.9 MB read + 112.1 MB written, 1.22 kB per point,
 # profiles/k_stage32t_fp32_bl64.md), scaled to 128^3 by the point count.
-TRAFFIC_F32 = {"src_sha": "4660eee38171c24b", "bytes_per_launch_128": (224896512 + 112758784) * 128 ** 3 / 64 ** 3}
+TRAFFIC_F32 = {"src_sha": "c9578cbd115078fd", "bytes_per_launch_128": (208853760 + 112123392) * 128 ** 3 / 64 ** 3}
 N_SM = 152
 FP64_FMA_PER_CLK_SM = 2
 
