@@ -975,11 +975,27 @@ def run_gpu(args):
             e1.record(stream)
             B.corrector_sync(corr)
             ms_fwd = e0.elapsed_time(e1) / args.steps
+            # the same pass waited for after each call, and the training
+            # forward pass (hidden pre-activations stored) waited for likewise
+            e0.record(stream)
+            for _ in range(args.steps):
+                B.corrector_infer_async(corr, 1, xs[0], out)
+                B.corrector_sync(corr)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_fwd_wait = e0.elapsed_time(e1) / args.steps
+            e0.record(stream)
+            for _ in range(args.steps):
+                B.corrector_forward_raw(corr, 1, xs[0], out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_fwd_raw = e0.elapsed_time(e1) / args.steps
         finally:
             B.corrector_destroy(corr)
         if rank == 0:
             print(json.dumps({"corrector_only": f"{nc}^3", "batch": S, "ms_per_train_step": ms_train,
-                              "ms_per_forward_1_sample": ms_fwd}))
+                              "ms_per_forward_1_sample": ms_fwd, "ms_per_forward_waited": ms_fwd_wait,
+                              "ms_per_forward_raw_waited": ms_fwd_raw}))
         return
 
     if args.cfd_only:

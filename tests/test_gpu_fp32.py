@@ -218,11 +218,14 @@ def test_full_size_sampled(n, prec):
     the benchmark's launch configuration, checked at 4096 sampled points
     against the oracle's right-hand side: FP64 per variable at 1e-12; the
     FP32-RHS form per tensor field at 2e-3. That bound is wider than the
-    3e-4 of the smooth-data tests above: with the punctures on the grid
-    (W ~ 0.03 at the nearest points), single-precision rounding of the
-    stencil inputs, differentiated twice (1/h^2 = 256), reaches ~1e-3 of
-    the tensor's largest right-hand side (measured 8.8e-4 at 128^3, 5.8e-4
-    at 256^3)."""
+    3e-4 of the smooth-data tests above because at t = 0 the right-hand
+    sides of trK and At_ij are small (the Laplacian and trace-free Hessian
+    of a nearly flat lapse) next to the single-precision rounding of O(1)
+    fields differenced twice, which is absolute, ~eps32/h^2: relative to
+    those small tensors it reaches ~1e-3 (measured 8.8e-4 at 128^3, for
+    trK at a point with W = 0.91, far from the punctures; 5.8e-4 at 256^3).
+    test_full_size_error_is_rounding_of_second_differences checks that
+    reading against an absolute bound."""
     torch = need_gpu()
     g = 5
     u, h = inputs.brill_lindquist(n, g, lo=-8.0, hi=8.0)
@@ -254,3 +257,49 @@ def test_full_size_sampled(n, prec):
         err = np.max(np.abs(gi - want), axis=0) / np.maximum(scale, 1e-300)
         worst = sorted(zip(err, inputs.VARS), reverse=True)[:6]
         assert np.max(err) < 2e-3, worst
+
+
+@pytest.mark.slow
+def test_full_size_error_is_rounding_of_second_differences():
+    """The reading behind the 2e-3 bound of test_full_size_sampled, made
+    checkable. A second difference of an O(1) field whose values are rounded
+    to single precision, formed with single-precision sums, carries an
+    absolute error of about eps32 * (sum of |weights| ~ 6.5) / h^2 per axis
+    (the input rounding and that of the paired sums, each of that size);
+    over three axes and the few O(1) factors of the algebra this stays below
+    64 eps32 / h^2. That is an absolute bound on every right-hand side
+    (times dt/6, its weight in the stage-0 accumulator). Relative to a
+    tensor's largest right-hand side it is large only where that right-hand
+    side is small: at t = 0 (K = 0, At = 0) those of trK and At_ij are the
+    Laplacian and trace-free Hessian of a nearly flat lapse, ~1e-4..4e-4 of
+    dt/6 at 128^3, so the relative error there reaches ~1e-3 far from the
+    punctures. The oracle's right-hand side of the state rounded to single
+    precision sits about halfway (the input rounding is half of it)."""
+    torch = need_gpu()
+    n, g = 128, 5
+    u, h = inputs.brill_lindquist(n, g, lo=-8.0, hi=8.0)
+    inputs.smooth_perturbation(u, g, 1e-3, 4243 + n, h)
+    assert np.max(np.abs(u)) < 1.5  # O(1) fields: the bound below is in these units
+    p = B.make_params(fd_order=8)
+    grid = grid_for(u, g, h)
+    y0 = B.upload(u, grid)
+    acc = B.alloc_state(grid)
+    ynext = B.alloc_state(grid)
+    work = B.alloc_work(grid, p, B.FP32_RHS)
+    dt = 0.25 * h
+    B.rk4_stage(grid, p, B.FP32_RHS, 0, dt, y0, y0, acc, ynext, work)
+    torch.cuda.synchronize()
+    del ynext, work
+    rng = np.random.default_rng(n + B.FP32_RHS)
+    lin = np.unique(rng.integers(0, n ** 3, 4096))
+    gi = interior(B.download(acc, grid), g).reshape(24, -1)[:, lin].T
+    eps32 = 2.0 ** -24
+    bound = dt / 6 * 64 * eps32 / h ** 2
+    errs = []
+    for state in (u, u.astype(np.float32).astype(np.float64)):
+        want = dt / 6 * oracle.rhs_points(state, g, h, oracle_params(p), lin, ko=True)
+        errs.append(np.max(np.abs(gi - want), axis=0))  # per variable
+    exact, rounded = errs
+    assert np.all(exact < bound), dict(zip(inputs.VARS, exact / bound))
+    k = inputs.VARS.index("trK")
+    assert rounded[k] < 0.8 * exact[k], (exact[k], rounded[k])
