@@ -591,6 +591,15 @@ bssn_status_t bssn_corrector_apply(bssn_corrector_t* c, const bssn_grid_t* grid,
 bssn_status_t bssn_constraints(const bssn_grid_t* grid, const bssn_params_t* params, const double* state,
                                double* ham, double* mom, double* gcon, double* out_l2, double* out_max,
                                void* work, unsigned long long work_bytes, void* stream);
+/* The Hamiltonian constraint H alone (the monitor of the learned step's
+ * fallback): the values of bssn_constraints' H, bit for bit, without the
+ * derivatives only the momentum and Gamma constraints need. ham (DEVICE,
+ * nullable) receives the pointwise values; *out_l2 and *out_max (HOST) the
+ * root-mean-square and maximum modulus over interior points. Same work
+ * buffer, synchronization and BSSN_ERR_NONFINITE rule as bssn_constraints. */
+bssn_status_t bssn_hamiltonian(const bssn_grid_t* grid, const bssn_params_t* params, const double* state,
+                               double* ham, double* out_l2, double* out_max, void* work,
+                               unsigned long long work_bytes, void* stream);
 
 /* Algebraic constraints of the conformal decomposition, FP64, at interior
  * points of `state` (DEVICE; ghosts not needed): det(gt_ij) - 1 and the

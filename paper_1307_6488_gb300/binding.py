@@ -91,10 +91,11 @@ def lib():
     L.bssn_rk4_step.argtypes = [G, P, ctypes.c_int, ctypes.c_double, ctypes.c_int, _p, _p, _p, _p, ull, _p]
     L.bssn_constraints.argtypes = [G, P, _p, _p, _p, _p, _p, _p, _p, ull, _p]
     L.bssn_algebraic_constraints.argtypes = [G, P, _p, _p, _p, _p, ull, _p]
+    L.bssn_hamiltonian.argtypes = [G, P, _p, _p, _p, _p, _p, ull, _p]
     L.bssn_probe_fp_rates.argtypes = [_p]
     for name in ("bssn_fill_ghosts", "bssn_rhs", "bssn_ko_dissipation", "bssn_rk4_stage", "bssn_rk4_step",
                  "bssn_diff_tables", "bssn_rk4_stage_fused",
-                 "bssn_constraints", "bssn_algebraic_constraints", "bssn_probe_fp_rates"):
+                 "bssn_constraints", "bssn_hamiltonian", "bssn_algebraic_constraints", "bssn_probe_fp_rates"):
         getattr(L, name).restype = ctypes.c_int
     _L = L
     return L
@@ -514,6 +515,19 @@ def constraints(grid, params, state, work, ham=None, mom=None, gcon=None, stream
     if s not in (OK, ERR_NONFINITE):
         raise BssnError(s, "constraints")
     return l2, mx, s
+
+
+def hamiltonian(grid, params, state, work, ham=None, stream=None):
+    """Hamiltonian constraint alone: returns (l2, max, status); status is OK
+    or ERR_NONFINITE."""
+    l2 = np.zeros(1)
+    mx = np.zeros(1)
+    s = lib().bssn_hamiltonian(ctypes.byref(grid), ctypes.byref(params), _ptr(state), _ptr(ham),
+                               l2.ctypes.data_as(_p), mx.ctypes.data_as(_p), _ptr(work), _nbytes(work),
+                               _stream(stream))
+    if s not in (OK, ERR_NONFINITE):
+        raise BssnError(s, "hamiltonian")
+    return float(l2[0]), float(mx[0]), s
 
 
 def algebraic_constraints(grid, params, state, work, stream=None):

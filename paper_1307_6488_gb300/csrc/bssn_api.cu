@@ -726,9 +726,14 @@ bssn_status_t bssn_psi4(const bssn_grid_t* grid, const bssn_params_t* params, co
   return latch(e);
 }
 
-bssn_status_t bssn_constraints(const bssn_grid_t* grid, const bssn_params_t* params, const double* state, double* ham,
+}  // extern "C"
+
+namespace {
+// The differential constraints, all seven or (ham_only) the Hamiltonian
+// alone; out_l2 / out_max receive 7 values either way.
+bssn_status_t constraints_impl(const bssn_grid_t* grid, const bssn_params_t* params, const double* state, double* ham,
                                double* mom, double* gcon, double* out_l2, double* out_max, void* work,
-                               unsigned long long work_bytes, void* stream) {
+                               unsigned long long work_bytes, void* stream, bool ham_only) {
   if (!grid_ok(grid) || !params_ok(grid, params)) return BSSN_ERR_INVALID_ARG;
   if (!aligned16(state) || !aligned16(work) || !out_l2 || !out_max) return BSSN_ERR_INVALID_ARG;
   if ((ham && !aligned16(ham)) || (mom && !aligned16(mom)) || (gcon && !aligned16(gcon))) return BSSN_ERR_INVALID_ARG;
@@ -741,10 +746,10 @@ bssn_status_t bssn_constraints(const bssn_grid_t* grid, const bssn_params_t* par
   if (e == cudaSuccess) {
     if (params->fd_order == 4)
       e = launch_constraints<4>(L, make_coef<4, double>(*grid, 0.0), state, w.dX64, w.dY64, ham, mom, gcon, w.part,
-                                w.flag, s);
+                                w.flag, ham_only, s);
     else
       e = launch_constraints<8>(L, make_coef<8, double>(*grid, 0.0), state, w.dX64, w.dY64, ham, mom, gcon, w.part,
-                                w.flag, s);
+                                w.flag, ham_only, s);
   }
   if (e == cudaSuccess) {
     k_reduce_partials<<<1, 256, 0, s>>>(w.part, con_blocks(L), w.finals);
@@ -762,6 +767,29 @@ bssn_status_t bssn_constraints(const bssn_grid_t* grid, const bssn_params_t* par
   unsigned int flag;
   std::memcpy(&flag, &host[14], sizeof(flag));
   return flag ? BSSN_ERR_NONFINITE : BSSN_OK;
+}
+}  // namespace
+
+extern "C" {
+
+bssn_status_t bssn_constraints(const bssn_grid_t* grid, const bssn_params_t* params, const double* state, double* ham,
+                               double* mom, double* gcon, double* out_l2, double* out_max, void* work,
+                               unsigned long long work_bytes, void* stream) {
+  return constraints_impl(grid, params, state, ham, mom, gcon, out_l2, out_max, work, work_bytes, stream, false);
+}
+
+bssn_status_t bssn_hamiltonian(const bssn_grid_t* grid, const bssn_params_t* params, const double* state, double* ham,
+                               double* out_l2, double* out_max, void* work, unsigned long long work_bytes,
+                               void* stream) {
+  if (!out_l2 || !out_max) return BSSN_ERR_INVALID_ARG;
+  double l2[7], mx[7];
+  const bssn_status_t st =
+      constraints_impl(grid, params, state, ham, nullptr, nullptr, l2, mx, work, work_bytes, stream, true);
+  if (st == BSSN_OK || st == BSSN_ERR_NONFINITE) {
+    *out_l2 = l2[0];
+    *out_max = mx[0];
+  }
+  return st;
 }
 
 bssn_status_t bssn_algebraic_constraints(const bssn_grid_t* grid, const bssn_params_t* params, const double* state,

@@ -609,8 +609,11 @@ __global__ void __launch_bounds__(256) k_ko(Layout L, Coef<R> C, const double* _
 
 // ------------------------------------------------------------------ constraints
 // Per-block partial results: 7 sums of squares, 7 maxima, written to
-// part[blockIdx.x * 14 + q]. Always double precision.
-template <int P>
+// part[blockIdx.x * 14 + q]. Always double precision. With HONLY the
+// Hamiltonian constraint alone (the momentum and Gamma slots stay 0, and
+// the derivatives only they need are not formed); its values are the same
+// bits as in the full evaluation.
+template <int P, bool HONLY>
 __global__ void __launch_bounds__(128, STAGE_F64_MIN_BLOCKS) k_constraints(Layout L, Coef<double> C, const double* __restrict__ u,
                                                      const double* __restrict__ dX, const double* __restrict__ dY,
                                                      double* ham, double* mom, double* gcon, double* part,
@@ -637,14 +640,17 @@ __global__ void __launch_bounds__(128, STAGE_F64_MIN_BLOCKS) k_constraints(Layou
 #pragma unroll
     for (int d = 0; d < 3; ++d)
 #pragma unroll
-      for (int s = 0; s < 6; ++s) dAt[d][s] = d1_direct<H>(u + (V_AT11 + s) * L.vs, p, st[d], C.c1[d]);
+      for (int s = 0; s < 6; ++s) dAt[d][s] = HONLY ? 0.0 : d1_direct<H>(u + (V_AT11 + s) * L.vs, p, st[d], C.c1[d]);
     const double iW = 1.0 / Q.u[V_W];
     constraints_point<double>(Q, dAt, iW, c);
+    if (HONLY)
+#pragma unroll
+      for (int q = 1; q < 7; ++q) c[q] = 0.0;
     if (ham) ham[p] = c[0];
-    if (mom)
+    if (mom && !HONLY)
 #pragma unroll
       for (int a = 0; a < 3; ++a) mom[a * L.vs + p] = c[1 + a];
-    if (gcon)
+    if (gcon && !HONLY)
 #pragma unroll
       for (int a = 0; a < 3; ++a) gcon[a * L.vs + p] = c[4 + a];
 #pragma unroll

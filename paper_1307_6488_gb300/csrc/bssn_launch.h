@@ -34,7 +34,7 @@ cudaError_t launch_ko(const Layout& L, const bssn_grid_t& G, double eps, bssn_pr
 template <int P>
 cudaError_t launch_constraints(const Layout& L, const Coef<double>& C, const double* u, const double* dX,
                                const double* dY, double* ham, double* mom, double* gcon, double* part,
-                               unsigned int* flag, cudaStream_t s);
+                               unsigned int* flag, bool ham_only, cudaStream_t s);
 
 template <int P>
 cudaError_t launch_psi4(const Layout& L, const Coef<double>& C, const double* u, const double* dX, const double* dY,

@@ -59,9 +59,14 @@ cudaError_t launch_ko<BSSN_ORDER>(const Layout& L, const bssn_grid_t& G, double 
 template <>
 cudaError_t launch_constraints<BSSN_ORDER>(const Layout& L, const Coef<double>& C, const double* u,
                                            const double* dX, const double* dY, double* ham, double* mom,
-                                           double* gcon, double* part, unsigned int* flag, cudaStream_t s) {
-  k_constraints<BSSN_ORDER><<<(unsigned int)con_blocks(L), CON_THREADS, 0, s>>>(L, C, u, dX, dY, ham, mom, gcon,
-                                                                               part, flag);
+                                           double* gcon, double* part, unsigned int* flag, bool ham_only,
+                                           cudaStream_t s) {
+  if (ham_only)
+    k_constraints<BSSN_ORDER, true><<<(unsigned int)con_blocks(L), CON_THREADS, 0, s>>>(L, C, u, dX, dY, ham,
+                                                                                        nullptr, nullptr, part, flag);
+  else
+    k_constraints<BSSN_ORDER, false><<<(unsigned int)con_blocks(L), CON_THREADS, 0, s>>>(L, C, u, dX, dY, ham, mom,
+                                                                                         gcon, part, flag);
   return cudaGetLastError();
 }
 

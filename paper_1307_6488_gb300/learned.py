@@ -98,8 +98,8 @@ class Stepper:
         B.fill_ghosts(self.p.gf, self.p.bc, self.src_f if self.p.bc == 1 else None, fine)
 
     def ham_l2(self, state):
-        l2, mx, st = B.constraints(self.p.gc, self.p.params, state, self.work_con)
-        return float(l2[0]) if st == B.OK else float("inf")
+        l2, mx, st = B.hamiltonian(self.p.gc, self.p.params, state, self.work_con)
+        return l2 if st == B.OK else float("inf")
 
 
 def trajectory_pairs(stepper, nsteps, measure=None):

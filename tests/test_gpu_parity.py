@@ -230,6 +230,33 @@ def test_constraints_parity(order):
     np.testing.assert_allclose(mx, wmx, rtol=1e-12)
 
 
+@pytest.mark.parametrize("order", [4, 8])
+def test_hamiltonian_alone_is_the_same_bits(order):
+    """The Hamiltonian-only evaluation (the learned step's monitor) gives the
+    full evaluation's H field and norms bit for bit, and its H against the
+    oracle; a non-positive W at an interior point is still flagged."""
+    torch = need_gpu()
+    g = order // 2 + 1
+    u = perturbed_bl(15, 11, 9, g, 0.15, seed=32)
+    p = B.make_params(fd_order=order)
+    grid = grid_for(u, g, 0.15)
+    d = B.upload(u, grid)
+    work = B.alloc_work(grid, p)
+    ham = B.alloc_state(grid)
+    ham1 = B.alloc_state(grid)
+    l2, mx, st = B.constraints(grid, p, d, work, ham=ham)
+    h2, hm, hst = B.hamiltonian(grid, p, d, work, ham=ham1)
+    torch.cuda.synchronize()
+    assert st == hst == B.OK
+    assert h2 == l2[0] and hm == mx[0]
+    gi = interior(B.download(ham, grid, 1), g)
+    assert np.array_equal(interior(B.download(ham1, grid, 1), g), gi)
+    wl2, wmx, wst, (wham, _, _) = oracle.constraints(u, g, 0.15, order, fields=True)
+    assert rel_err(B.download(ham1, grid, 1), wham[None], g)[0] < RHS_TOL
+    u[IDX["W"], g + 1, g + 5, g + 2] = -0.25
+    assert B.hamiltonian(grid, p, B.upload(u, grid), work)[2] == B.ERR_NONFINITE
+
+
 def test_constraints_nonfinite_status():
     torch = need_gpu()
     g = 3
