@@ -907,6 +907,35 @@ def run_gpu(args):
             B.corrector_sync(corr)
             ms_forward = e0.elapsed_time(e1) / reps
             mma96 = B.probe_mma_rate(96)
+            # the same network on coarse steps in the FP32-RHS form (FP64
+            # state, Hamiltonian check and fallback in FP64; the fine
+            # reference and the plain fine timing stay FP64)
+            acc32 = {}
+            for name in ("bl_m0.45_0.55_d2.7", "bl_m0.35_0.65_d3.5"):
+                kind, kw = held[name]
+                acc32[name] = LR.evaluate(LR.Stepper(LR.Problem(kind, nc, **kw), prec=B.FP32_RHS,
+                                                     fine_prec=B.FP64), corr, 8)
+            st32 = LR.Stepper(LR.Problem("bl", nc, masses=(0.45, 0.55), separation=2.7), prec=B.FP32_RHS,
+                              fine_prec=B.FP64)
+            y32 = st32.src_c.clone()
+            fb32 = 0
+            for _ in range(args.warmup):
+                fb32 += LR.learned_step(st32, corr, y32, scratch=scratch)[0]
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                fb32 += LR.learned_step(st32, corr, y32, scratch=scratch)[0]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_learned32 = e0.elapsed_time(e1) / args.steps
+            c32 = st32.src_c.clone()
+            e0.record(stream)
+            for _ in range(args.steps):
+                st32.coarse_step(c32)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_coarse32 = e0.elapsed_time(e1) / args.steps
+            del st32, y32, c32
         finally:
             B.corrector_destroy(corr)
         torch.cuda.empty_cache()
@@ -919,6 +948,13 @@ def run_gpu(args):
                 "speedup_vs_plain_fine": ms_fine2 / ms_learned,
                 "ms_learned_step": ms_learned, "ms_two_fine_steps": ms_fine2, "ms_plain_coarse_step": ms_coarse,
                 "fallbacks_in_timed_steps": int(fb),
+                "on_fp32_rhs_coarse_steps": {
+                    "value": 2 * nf3 / (ms_learned32 * 1e-3), "unit": "fine-grid-equivalent point updates/s",
+                    "speedup_vs_plain_fine": ms_fine2 / ms_learned32, "ms_learned_step": ms_learned32,
+                    "ms_plain_coarse_step": ms_coarse32, "fallbacks_in_timed_steps": int(fb32),
+                    "accuracy_8_coarse_steps": acc32,
+                    "note": "the network trained above, applied after coarse RK4 steps in the FP32-RHS form; "
+                            "errors against the FP64 fine method"},
                 "network_forward_ms_64cubed": ms_forward,
                 "network_roofline": {"bound": "tensor", "achieved": conv_tflops,
                                      "peak": MEASURED.get("bf16_tflops", 1922.5), "unit": "TFLOP/s",
