@@ -48,12 +48,12 @@ except (OSError, ValueError):
 # MB written per launch, 6.56 kB per point at 4 blocks/SM, rows traversed in
 # bricks) and scaled to 128^3 by the point count, since the traffic is per
 # point (state, tables and the per-thread stack).
-TRAFFIC = {"src_sha": "1bd173c68c3b6f9f", "bytes_per_launch_128": (921128448 + 797547008) * 128 ** 3 / 64 ** 3}
+TRAFFIC = {"src_sha": "64481867ccf4c0a5", "bytes_per_launch_128": (920577024 + 797818880) * 128 ** 3 / 64 ** 3}
 # FP64 pipe utilisation of the same launch (sm__pipe_fp64_cycles_active,
 # percent of peak over active cycles) and the FP64 instructions it executed
 # per interior point (smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul}
 # _pred_on.sum / 64^3), for the same source.
-FP64_PIPE_BUSY = {"src_sha": "1bd173c68c3b6f9f", "pct_of_active_cycles": 82.57,
+FP64_PIPE_BUSY = {"src_sha": "64481867ccf4c0a5", "pct_of_active_cycles": 82.56,
                   "dfma_per_point": 636223488 / 64 ** 3, "dadd_per_point": 409468928 / 64 ** 3,
                   "dmul_per_point": 101187584 / 64 ** 3}
 # The same for the tiled FP32-RHS stage kernel k_stage32t<8,0> as

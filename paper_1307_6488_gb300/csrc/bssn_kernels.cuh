@@ -197,7 +197,10 @@ __device__ __forceinline__ bool negative_bits(float x) { return __float_as_int(x
 
 // Gather every derivative of the right-hand side at point p.
 // ko_out (if WITH_KO) receives the Kreiss-Oliger term of every variable.
-template <int P, bool WITH_KO, bool WITH_ADV, typename R>
+// With NMIX < NM only the first NMIX variables with second derivatives get
+// their derivatives (7: W and gt_ij, all the Hamiltonian constraint needs);
+// the lapse's and shift's are then left zero.
+template <int P, bool WITH_KO, bool WITH_ADV, typename R, int NMIX = NM>
 __device__ __forceinline__ void gather(const Layout& L, const Coef<R>& C, const R* __restrict__ u,
                                        const R* __restrict__ dX, const R* __restrict__ dY, long long p,
                                        PointIn<R>& Q, R* ko_out) {
@@ -207,10 +210,24 @@ __device__ __forceinline__ void gather(const Layout& L, const Coef<R>& C, const 
   const long long st[3] = {1, L.sy, L.sz};
 #pragma unroll
   for (int v = 0; v < NV; ++v) Q.u[v] = __ldg(u + v * vs + p);
+  if (NMIX < NM) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      Q.da[d] = R(0);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Q.db[d][i] = R(0);
+    }
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+      Q.dda[s] = R(0);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Q.ddb[i][s] = R(0);
+    }
+  }
 
   // ---- the 11 variables with second derivatives
 #pragma unroll 1
-  for (int m = 0; m < NM; ++m) {
+  for (int m = 0; m < NMIX; ++m) {
     const int var = mvar(m);
     const R* v = u + var * vs;
     const R* tx = dX + (long long)m * H * vs;
@@ -634,7 +651,7 @@ __global__ void __launch_bounds__(128, STAGE_F64_MIN_BLOCKS) k_constraints(Layou
   // no early return here: every thread takes part in the block reduction
   if (lin < L.npts && in_range(p - FD<P>::R * L.sz, p + FD<P>::R * L.sz, padded_points(L))) {
     PointIn<double> Q;
-    gather<P, false, false, double>(L, C, u, dX, dY, p, Q, nullptr);
+    gather<P, false, false, double, HONLY ? 7 : NM>(L, C, u, dX, dY, p, Q, nullptr);
     double dAt[3][6];
     const long long st[3] = {1, L.sy, L.sz};
 #pragma unroll

@@ -258,5 +258,13 @@ def test_trained_corrector_beats_the_plain_coarse_method():
             assert r["fallbacks"] == 0, r
             assert r["err_learned"] < 0.5 * r["err_plain"], r
             assert abs(r["ham_learned"] - r["ham_fine"]) < 0.1 * r["ham_fine"], r
+            # the same network after coarse steps in the FP32-RHS form (FP64
+            # state, check and fine reference): the FP32 right-hand side's
+            # error is far below the coarse truncation error it corrects
+            st32 = LR.Stepper(LR.Problem("bl", N, **kw), prec=B.FP32_RHS, fine_prec=B.FP64)
+            r32 = LR.evaluate(st32, c, 8)
+            assert r32["fallbacks"] == 0, r32
+            assert abs(r32["err_learned"] - r["err_learned"]) < 0.02 * r["err_learned"], (r, r32)
+            assert abs(r32["err_plain"] - r["err_plain"]) < 0.02 * r["err_plain"], (r, r32)
     finally:
         B.corrector_destroy(c)
