@@ -174,8 +174,8 @@ def test_add_difference_is_elementwise(setup):
 
 def test_fallback_is_closer_to_the_fine_method_than_a_plain_step():
     """On the smooth gauge wave the fallback step must land closer to the
-    restricted fine solution than the plain coarse step does (the plain
-    fine method is the judge of the error), and closer than restricting the
+    restricted fine solution than the plain coarse step does (errors are
+    measured against the plain fine method), and closer than restricting the
     fine steps of the prolonged state outright. It cannot reach the fine
     method itself: the fine steps start from an interpolated state whose
     interpolation error their second derivatives amplify."""
