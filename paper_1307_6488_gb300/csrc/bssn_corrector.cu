@@ -1082,6 +1082,11 @@ struct bssn_corrector {
   unsigned int* err = nullptr;
   int wg_blocks = 0, rows_per_cta = 0;
   int sms = 0;        // streaming multiprocessors (one conv CTA each)
+  // convolution plans by sample count (the grid is fixed per network), so
+  // that the search over (rows, planes) pairs runs once, not on every layer
+  // launch
+  ConvPlan plan[65];
+  int plan_grid[65] = {};  // 0: not planned yet
   int conv_smem = 0;  // the most dynamic shared memory a convolution plan of this grid asks for
   long long adam_t = 0;
 };
@@ -1150,7 +1155,7 @@ int conv_smem_max(int X, int Y) {
 // planes). A unit issues T tiles x (L + 2) input planes of MMAs, so R and L
 // are picked to make ceil(units / SMs) T (L + 2) smallest (then the fewest
 // units). Returns the grid size, 0 if no plan fits.
-int conv_units(const bssn_corrector* c, const Geom& G, ConvPlan* P) {
+int conv_units_search(const bssn_corrector* c, const Geom& G, ConvPlan* P) {
   double best = 1e300;
   long long best_units = 0;
   for (int R = 1; R <= G.Y; ++R) {
@@ -1174,6 +1179,13 @@ int conv_units(const bssn_corrector* c, const Geom& G, ConvPlan* P) {
   const long long units = (long long)G.S * P->nyb * P->nzs;
   const long long slots = (long long)c->sms * CONV_CTAS;
   return (int)(units < slots ? units : slots);
+}
+
+int conv_units(bssn_corrector* c, const Geom& G, ConvPlan* P) {
+  if (G.S < 1 || G.S > 64) return conv_units_search(c, G, P);
+  if (!c->plan_grid[G.S]) c->plan_grid[G.S] = conv_units_search(c, G, &c->plan[G.S]);
+  *P = c->plan[G.S];
+  return c->plan_grid[G.S];
 }
 
 // one layer forward on act[l] (sample count in G) -> z[l] and act[l+1]
