@@ -56,11 +56,14 @@ TRAFFIC = {"src_sha": "64481867ccf4c0a5", "bytes_per_launch_128": (920577024 + 7
 FP64_PIPE_BUSY = {"src_sha": "64481867ccf4c0a5", "pct_of_active_cycles": 82.56,
                   "dfma_per_point": 636223488 / 64 ** 3, "dadd_per_point": 409468928 / 64 ** 3,
                   "dmul_per_point": 101187584 / 64 ** 3}
-# The same for the tiled FP32-RHS stage kernel k_stage32t<8,0> as
-# bssn_rk4_step runs it (writing the next stage's single-precision input too;
-# one launch at 64^3: 208.9 MB read + 112.1 MB written, 1.22 kB per point,
-# profiles/k_stage32t_fp32_bl64.md), scaled to 128^3 by the point count.
-TRAFFIC_F32 = {"src_sha": "c9578cbd115078fd", "bytes_per_launch_128": (208853760 + 112123392) * 128 ** 3 / 64 ** 3}
+# The same for the tiled FP32-RHS stage kernel k_stage32t<8,0> as the bench
+# times it (per-stage calls; the roofline's 864 B per point is the average of
+# the four stages): the mean of the four stages' launches at 64^3, 1043.6 MB
+# read and written in all, 0.995 kB per point and launch
+# (profiles/k_stage32t_fp32_bl64.md), scaled to 128^3 by the point count.
+TRAFFIC_F32 = {"src_sha": "c9578cbd115078fd",
+               "bytes_per_launch_128": (150967552 + 75629568 + 206530560 + 83616512 + 206648064 + 83771904 +
+                                        197803520 + 38672384) / 4 * 128 ** 3 / 64 ** 3}
 N_SM = 152
 FP64_FMA_PER_CLK_SM = 2
 
