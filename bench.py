@@ -103,6 +103,30 @@ def kernel32_src_sha():
 N_FIRST, N_SECOND, N_MIXED, N_ADV, N_ADV_SUM = 45, 33, 33, 72, 48
 
 
+def stage_bytes(prec, stage, order=8, whole_step=False):
+    """Algorithmic DRAM bytes per interior point of one fused RK4 stage
+    (0..3): every array the stage must read or write once. Both forms read
+    the stage input and y0, read the accumulator from stage 1 on, write it
+    up to stage 2 and write the next state; FP64 reads the first-difference
+    tables (x and y differences of the 11 variables with mixed derivatives,
+    order/2 doubles each), FP32-RHS reads the single-precision input, its
+    D_x / D_y tables (22 floats) and W in double precision instead of the
+    double-precision input; inside bssn_rk4_step the FP32-RHS stages 0..2
+    also write the next stage's single-precision input."""
+    nv = 24
+    common = nv * 8 * (1 + (stage > 0) + (stage < 3) + 1)  # y0, acc read, acc written, ynext
+    if prec == "fp64":
+        return nv * 8 + 2 * 11 * (order // 2) * 8 + common
+    b = nv * 4 + 22 * 4 + 8 + common
+    if whole_step and stage < 3:
+        b += nv * 4
+    return b
+
+
+def mean_stage_bytes(prec, order=8):
+    return sum(stage_bytes(prec, s, order) for s in range(4)) / 4
+
+
 def executed_fp64(stage_ms, pts, sm_mhz, per_clk, sha):
     """FP64 instructions the fused stage kernel executes per point (ncu
     counts for this source, else None) and their issue rate per SM clock as a
@@ -1202,11 +1226,12 @@ def run_gpu(args):
                      "peak_probe_sm_mhz": rates["sm_mhz_fp64_fma"],
                      "frac_of_probe": achieved / peak_probe,
                      # the HBM side of the same kernel: algorithmic bytes per point and stage,
-                     # averaged over the four stages: ys 192, difference tables 704, y0 192,
-                     # acc read 144 and written 144, ynext 192
-                     "hbm": {"bytes_per_point_stage": 1568,
-                             "achieved_gbs": 1568 * pts / (f64["stage_ms"] * 1e-3) / 1e9,
-                             "frac": (1568 * pts / (f64["stage_ms"] * 1e-3) / 1e9 / MEASURED["hbm_gbs"])
+                     # averaged over the four stages (stage_bytes): ys 192, difference tables
+                     # 704, y0 192, acc read 144 and written 144, ynext 192
+                     "hbm": {"bytes_per_point_stage": mean_stage_bytes("fp64"),
+                             "achieved_gbs": mean_stage_bytes("fp64") * pts / (f64["stage_ms"] * 1e-3) / 1e9,
+                             "frac": (mean_stage_bytes("fp64") * pts / (f64["stage_ms"] * 1e-3) / 1e9 /
+                                      MEASURED["hbm_gbs"])
                              if MEASURED.get("hbm_gbs") else None},
                      "fp64_pipe_busy_ncu": FP64_PIPE_BUSY if FP64_PIPE_BUSY["src_sha"] == sha else None,
                      # what the kernel executes (ncu instruction counts of the same source): FP64
@@ -1239,9 +1264,10 @@ def run_gpu(args):
                          # algorithmic bytes of the stage kernel per point and stage, averaged over
                          # the four stages: FP32 stencil input 96, FP32 tables 88, FP64 W 8, y0 192,
                          # acc read 144 and written 144, ynext 192
-                         "hbm": {"bytes_per_point_stage": 864,
-                                 "achieved_gbs": 864 * pts / (f32["stage_ms"] * 1e-3) / 1e9,
-                                 "frac": (864 * pts / (f32["stage_ms"] * 1e-3) / 1e9 / MEASURED["hbm_gbs"])
+                         "hbm": {"bytes_per_point_stage": mean_stage_bytes("fp32"),
+                                 "achieved_gbs": mean_stage_bytes("fp32") * pts / (f32["stage_ms"] * 1e-3) / 1e9,
+                                 "frac": (mean_stage_bytes("fp32") * pts / (f32["stage_ms"] * 1e-3) / 1e9 /
+                                          MEASURED["hbm_gbs"])
                                  if MEASURED.get("hbm_gbs") else None,
                                  "traffic": TRAFFIC_F32["bytes_per_launch_128"]
                                  if TRAFFIC_F32["src_sha"] == kernel32_src_sha() and n == N else None},

@@ -3,7 +3,8 @@ stage. The oracle counts the operations of its own literal code with a
 counting scalar (add/sub/mul/div = 1, no fused operations). These tests pin
 that counter to counts derived by hand from the stencil definitions it
 evaluates, pin the composition of the per-point total the benchmark uses,
-and set it beside the paper's own figure for the right-hand side."""
+and set it beside the paper's own figure for the right-hand side. The
+last test pins the HBM side: the algorithmic bytes per point and stage."""
 import os
 import sys
 
@@ -77,3 +78,28 @@ def test_rhs_count_beside_the_paper():
     import bench
     rhs = bench.algorithmic_flops(8)["rhs"]
     assert abs(rhs / 7900 - 1) < 0.05, rhs
+
+
+def test_stage_bytes_model():
+    """The HBM side of the rooflines: the algorithmic bytes per interior
+    point of one fused RK4 stage, counted array by array from what the stage
+    must touch once (RK4 in the y0 / accumulator form: stage 0 writes the
+    accumulator without reading it, stage 3 reads it without writing it),
+    and their four-stage means, which the benchmark divides by the stage
+    time."""
+    import bench
+    d, f = 8, 4  # bytes of a double and of a float
+    nv, nm, H = 24, 11, 4  # variables, variables with mixed derivatives, 8th-order pairs
+    rk = [nv * d * (2 + (s > 0) + (s < 3)) for s in range(4)]  # y0, ynext, acc read, acc written
+    assert rk == [576, 768, 768, 576]
+    fp64 = [nv * d + 2 * nm * H * d + x for x in rk]  # stage input, x/y difference tables
+    fp32 = [nv * f + 2 * nm * f + d + x for x in rk]  # single-precision input, D_x/D_y tables, W
+    for s in range(4):
+        assert bench.stage_bytes("fp64", s) == fp64[s]
+        assert bench.stage_bytes("fp32", s) == fp32[s]
+        # inside bssn_rk4_step stages 0..2 also write the next single-precision input
+        assert bench.stage_bytes("fp32", s, whole_step=True) == fp32[s] + (nv * f if s < 3 else 0)
+    assert bench.mean_stage_bytes("fp64") == 1568
+    assert bench.mean_stage_bytes("fp32") == 864
+    # 4th order: half the difference-table pairs
+    assert bench.stage_bytes("fp64", 1, order=4) == fp64[1] - 2 * nm * 2 * d
