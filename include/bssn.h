@@ -540,7 +540,10 @@ bssn_status_t bssn_corrector_forward_raw(bssn_corrector_t* c, int S, const void*
  * (same arguments, bit-identical out) enqueued on stream without
  * synchronizing, and without keeping the hidden layers' pre-activations
  * (bssn_corrector_layer_output is then undefined for layers 0..3). x_bf16
- * and out must stay valid until the stream reaches the call. A bounded device
+ * and out must stay valid until the stream reaches the call. Every call on
+ * one network uses the network's own activation buffers, so calls on the
+ * same network must be ordered (one stream, or events between streams);
+ * concurrent serving needs one network per stream. A bounded device
  * wait that gives up is latched on the device and reported by the next
  * bssn_corrector_sync; any other call on c clears the latch when it starts.
  * Returns BSSN_ERR_CUDA if a launch failed. */
