@@ -1,5 +1,6 @@
 """Pins for the corrector oracle (not GPU): the convolution against a
-direct numpy evaluation of its definition, GELU against its closed form and
+direct numpy evaluation of its definition and, for one channel, against
+scipy's 3-D cross-correlation, GELU against its closed form and
 the standard normal CDF, and the whole network's gradient against central
 finite differences."""
 import math
@@ -87,3 +88,21 @@ def test_network_gradient_finite_differences():
         lm, _, _ = oracle.corrector_loss(pp, ch, x, t, want_grad=False)
         fd = (lp - lm) / (2 * h)
         assert abs(fd - grad[i]) <= 1e-6 * max(abs(fd), 1e-3), (i, fd, grad[i])
+
+
+def test_conv_single_channel_is_scipy_correlation():
+    """One input and one output channel: the oracle's convolution is the
+    library's 3-D cross-correlation with zero padding (scipy.ndimage), tap
+    (dz, dy, dx) weighting x(z + dz, y + dy, x + dx). A flipped or
+    transposed kernel, or a wrong tap order, fails here (the kernel below
+    has no symmetry)."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((1, 5, 6, 7, 1))
+    w = rng.standard_normal((3, 3, 3))  # w[dz + 1, dy + 1, dx + 1]
+    W = w.reshape(27, 1, 1)
+    want = ndimage.correlate(x[0, ..., 0], w, mode="constant", cval=0.0)
+    got = oracle.conv3d_fwd(x, W, None)[0, ..., 0]
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+    # and it is not the convolution (the flipped kernel)
+    assert not np.allclose(got, ndimage.convolve(x[0, ..., 0], w, mode="constant", cval=0.0))
